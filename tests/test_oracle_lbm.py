@@ -1,0 +1,334 @@
+"""Pins of the oracle's lattice Boltzmann step (oracle/lbm.py).
+
+Each test checks the oracle against something other than its own formula:
+textbook lattice identities, the polynomial definition of the MRT moments,
+closed forms of the equilibrium moments, exact stencil identities of the
+Shan-Chen sum, the Guo forcing / BGK special cases, exact conservation laws,
+and physical steady states (Maxwell coexistence, flat normal pressure at g = 0,
+hydrostatic balance) that a dropped term, a wrong sign or a transposed operand
+would break.
+"""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+
+from oracle import eos, lbm
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+A, B, R = 0.25, 4.0, 1.0
+RHO_C, T_C, P_C = eos.critical_point(A, B, R)
+
+
+def golden():
+    vals = {}
+    for line in open(GOLDEN):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+def column(ny, Tr, nx=1, liquid_rows=None, width=5.0):
+    """Tanh liquid-below-vapour column at Maxwell densities (synthetic initial state)."""
+    rv, rl, ps = eos.maxwell(Tr * T_C, A, B, R)
+    y0 = (ny / 2 if liquid_rows is None else liquid_rows) - 0.5
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    rho0 = 0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2.0 * (y - y0) / width)
+    return rho0, rv, rl, ps, y0
+
+
+# ------------------------------------------------------------ lattice constants
+def test_lattice_weights_match_paper_and_are_isotropic():
+    g = golden()
+    assert lbm.W[0] == pytest.approx(g["w0"], rel=1e-15)
+    assert np.allclose(lbm.W[1:5], g["w1"], rtol=1e-15)
+    assert np.allclose(lbm.W[5:], g["w5"], rtol=1e-15)
+    assert lbm.CS2 == pytest.approx(g["cs2"], rel=1e-15)
+    assert lbm.W_SC[1] == pytest.approx(g["wsc1"]) and lbm.W_SC[5] == pytest.approx(g["wsc2"])
+    c = lbm.C.astype(float)
+    w = lbm.W
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose(w @ c, 0.0, atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), lbm.CS2 * np.eye(2), atol=1e-16)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, c, c, c), 0.0, atol=1e-16)
+    d = np.eye(2)
+    iso4 = lbm.CS2**2 * (
+        np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d) + np.einsum("ad,bc->abcd", d, d)
+    )
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c), iso4, atol=1e-16)
+    # the Shan-Chen weights give sum_i w(|c_i|^2) c_ia c_ib = delta_ab
+    assert np.allclose(np.einsum("i,ia,ib->ab", lbm.W_SC, c, c), np.eye(2), atol=1e-16)
+    for i in range(9):
+        assert (lbm.C[lbm.OPP[i]] == -lbm.C[i]).all()
+
+
+def test_mrt_rows_are_the_gram_schmidt_polynomials():
+    """Rows of Eq. MatrixMRT are the Lallemand-Luo polynomials of c (independent definition)."""
+    cx = lbm.C[:, 0].astype(float)
+    cy = lbm.C[:, 1].astype(float)
+    c2 = cx**2 + cy**2
+    rows = [
+        np.ones(9),
+        3 * c2 - 4,
+        (9 * c2**2 - 21 * c2 + 8) / 2,
+        cx,
+        (3 * c2 - 5) * cx,
+        cy,
+        (3 * c2 - 5) * cy,
+        cx**2 - cy**2,
+        cx * cy,
+    ]
+    np.testing.assert_array_equal(lbm.M, np.array(rows))
+
+
+def test_mrt_orthogonality_and_inverse():
+    np.testing.assert_allclose(lbm.M @ lbm.M.T, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]), atol=0)
+    # Gauss-Jordan inverse equals the transpose shortcut M^T diag(1/|row|^2)
+    shortcut = lbm.M.T @ np.diag(1.0 / np.array([9, 36, 36, 6, 12, 6, 12, 4, 4], dtype=float))
+    np.testing.assert_allclose(lbm.MINV, shortcut, rtol=0, atol=2e-16)
+    np.testing.assert_allclose(lbm.MINV @ lbm.M, np.eye(9), rtol=0, atol=1e-15)
+
+
+def test_equilibrium_moments_closed_form():
+    """M f_eq of Eq. EquilibriumDistribution equals the textbook moment equilibria."""
+    rng = np.random.default_rng(1)
+    rho = rng.uniform(0.02, 0.4, 50)
+    ux = rng.uniform(-0.1, 0.1, 50)
+    uy = rng.uniform(-0.1, 0.1, 50)
+    feq = lbm.equilibrium(rho, ux, uy)
+    m = lbm.M @ feq
+    u2 = ux**2 + uy**2
+    expect = np.array(
+        [rho, -2 * rho + 3 * rho * u2, rho - 3 * rho * u2, rho * ux, -rho * ux, rho * uy, -rho * uy,
+         rho * (ux**2 - uy**2), rho * ux * uy]
+    )
+    np.testing.assert_allclose(m, expect, rtol=1e-13, atol=1e-16)
+    # second moment: sum_i f_eq c_a c_b = rho cs^2 delta + rho u u
+    c = lbm.C.astype(float)
+    P = np.einsum("ia,ib,in->abn", c, c, feq)
+    np.testing.assert_allclose(P[0, 0], rho * lbm.CS2 + rho * ux * ux, rtol=1e-13)
+    np.testing.assert_allclose(P[0, 1], rho * ux * uy, rtol=1e-12, atol=1e-17)
+
+
+# ------------------------------------------------------------ streaming
+def test_stream_moves_packets_along_c_and_reflects_at_walls():
+    nx, ny = 5, 6
+    for i in range(9):
+        for (x0, y0) in [(2, 3), (0, 0), (4, 5), (0, 5), (4, 0)]:
+            fs = np.zeros((9, ny, nx))
+            fs[i, y0, x0] = 1.0
+            f = lbm.stream(fs)
+            cx, cy = lbm.C[i]
+            yt = y0 + cy
+            if 0 <= yt < ny:
+                # lands one link away, x periodic, same direction
+                assert f[i, yt, (x0 + cx) % nx] == 1.0
+            else:
+                # hits the wall half a link away and comes back reversed to the same node
+                assert f[lbm.OPP[i], y0, x0] == 1.0
+            assert f.sum() == 1.0
+
+
+def test_stream_is_a_permutation():
+    rng = np.random.default_rng(2)
+    fs = rng.random((9, 7, 3))
+    f = lbm.stream(fs)
+    np.testing.assert_array_equal(np.sort(fs.ravel()), np.sort(f.ravel()))
+
+
+# ------------------------------------------------------------ Shan-Chen force
+def test_shan_chen_uniform_linear_quadratic():
+    G = -1.0
+    ny, nx = 9, 16
+    psi = np.full((ny, nx), 0.7)
+    Fx, Fy = lbm.shan_chen_force(psi, G)
+    assert np.all(Fx == 0) and np.all(Fy == 0)
+    # linear in y: F = -G psi beta exactly on interior rows; zero on the two wall rows
+    beta = 0.013
+    psi = 0.4 + beta * np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    Fx, Fy = lbm.shan_chen_force(psi, G)
+    np.testing.assert_allclose(Fy[1:-1], -G * psi[1:-1] * beta, rtol=1e-13)
+    np.testing.assert_allclose(Fx, 0.0, atol=1e-16)
+    assert np.all(Fy[0] == 0) and np.all(Fy[-1] == 0)
+    # linear in x away from the periodic seam
+    psi = 0.4 + beta * np.arange(nx, dtype=float)[None, :] * np.ones((ny, 1))
+    Fx, Fy = lbm.shan_chen_force(psi, G)
+    np.testing.assert_allclose(Fx[1:-1, 1:-1], -G * psi[1:-1, 1:-1] * beta, rtol=1e-13)
+    # the stencil differentiates quadratics exactly: S = grad psi for psi = q (x^2 + 2 y^2)
+    q = 1e-3
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    psi = q * (X**2 + 2 * Y**2)
+    Sx, Sy = lbm.shan_chen_sum(psi)
+    np.testing.assert_allclose(Sx[1:-1, 1:-1], 2 * q * X[1:-1, 1:-1], rtol=1e-12)
+    np.testing.assert_allclose(Sy[1:-1, 1:-1], 4 * q * Y[1:-1, 1:-1], rtol=1e-12)
+
+
+# ------------------------------------------------------------ collision and forcing
+def _random_state(n, seed):
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.05, 0.35, n)
+    ux, uy = rng.uniform(-0.05, 0.05, (2, n))
+    Fx, Fy = rng.uniform(-1e-3, 1e-3, (2, n))
+    f = lbm.equilibrium(rho, ux, uy) + rng.uniform(-1e-3, 1e-3, (9, n))
+    return rng, rho, ux, uy, Fx, Fy, f
+
+
+def guo(ux, uy, Fx, Fy):
+    """Guo et al. (2002) forcing term without the (1 - 1/(2 tau)) prefactor:
+    w_i [ (c_i - u)/cs^2 + (c_i . u) c_i / cs^4 ] . F."""
+    c = lbm.C.astype(float)
+    out = np.empty((9,) + ux.shape)
+    for i in range(9):
+        cu = c[i, 0] * ux + c[i, 1] * uy
+        ax = (c[i, 0] - ux) / lbm.CS2 + cu * c[i, 0] / lbm.CS2**2
+        ay = (c[i, 1] - uy) / lbm.CS2 + cu * c[i, 1] / lbm.CS2**2
+        out[i] = lbm.W[i] * (ax * Fx + ay * Fy)
+    return out
+
+
+def test_li_source_without_sigma_is_guo_forcing():
+    """With sigma = 0, M^-1 S~ of Eq. LiFS is Guo's velocity-space forcing term."""
+    _, rho, ux, uy, Fx, Fy, _ = _random_state(40, 3)
+    p = lbm.Params(nx=1, ny=1, sigma=0.0)
+    S = lbm.li_source(ux, uy, Fx, Fy, np.zeros_like(ux), p)
+    np.testing.assert_allclose(lbm.MINV @ S, guo(ux, uy, Fx, Fy), rtol=1e-12, atol=1e-18)
+
+
+def test_mrt_with_equal_times_is_bgk_with_guo_forcing():
+    """All tau equal: Eq. OperatorMRT + Eq. LiFS reduce to BGK with Guo forcing."""
+    _, rho, ux, uy, Fx, Fy, f = _random_state(40, 4)
+    tau = 0.8
+    p = lbm.Params(nx=1, ny=1, sigma=0.0, tau_rho=tau, tau_e=tau, tau_varsigma=tau, tau_j=tau, tau_q=tau, tau_nu=tau)
+    feq = lbm.equilibrium(rho, ux, uy)
+    S = lbm.li_source(ux, uy, Fx, Fy, np.zeros_like(ux), p)
+    got = lbm.collide(f, feq, S, p)
+    want = f - (f - feq) / tau + (1 - 1 / (2 * tau)) * guo(ux, uy, Fx, Fy)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-17)
+
+
+def test_sigma_term_changes_only_e_and_epsilon():
+    """The sigma term of Eq. LiFS leaves mass and momentum alone; through (I - Lambda/2)
+    it shifts e by sigma r / tau_e and epsilon by -sigma r / tau_varsigma."""
+    _, rho, ux, uy, Fx, Fy, f = _random_state(30, 5)
+    ratio = np.random.default_rng(6).uniform(0, 1e-4, 30)
+    p = lbm.Params(nx=1, ny=1, sigma=1.385, tau_e=0.9, tau_varsigma=1.2, tau_q=1.1, tau_nu=0.7)
+    p0 = dataclasses.replace(p, sigma=0.0)
+    feq = lbm.equilibrium(rho, ux, uy)
+    d = lbm.collide(f, feq, lbm.li_source(ux, uy, Fx, Fy, ratio, p), p) - lbm.collide(
+        f, feq, lbm.li_source(ux, uy, Fx, Fy, ratio, p0), p0
+    )
+    dm = lbm.M @ d
+    np.testing.assert_allclose(dm[1], p.sigma * ratio / p.tau_e, rtol=1e-9)
+    np.testing.assert_allclose(dm[2], -p.sigma * ratio / p.tau_varsigma, rtol=1e-9)
+    np.testing.assert_allclose(dm[[0, 3, 4, 5, 6, 7, 8]], 0.0, atol=1e-15)
+
+
+def test_force_enters_momentum_once():
+    """Post-collision momentum is sum f c + F for any relaxation times
+    (j* = j - s_j (j - rho u) + (1 - s_j/2) F with rho u = j + F/2)."""
+    _, rho, ux, uy, Fx, Fy, f = _random_state(30, 7)
+    jx = lbm.C[:, 0] @ f
+    jy = lbm.C[:, 1] @ f
+    rho = f.sum(0)
+    ux = (jx + Fx / 2) / rho
+    uy = (jy + Fy / 2) / rho
+    p = lbm.Params(nx=1, ny=1, tau_j=0.7, tau_e=0.9, tau_q=1.3)
+    fs = lbm.collide(f, lbm.equilibrium(rho, ux, uy), lbm.li_source(ux, uy, Fx, Fy, np.zeros(30), p), p)
+    np.testing.assert_allclose(fs.sum(0), rho, rtol=1e-14)
+    np.testing.assert_allclose(lbm.C[:, 0] @ fs, jx + Fx, rtol=1e-12, atol=1e-17)
+    np.testing.assert_allclose(lbm.C[:, 1] @ fs, jy + Fy, rtol=1e-12, atol=1e-17)
+
+
+def test_uniform_rest_state_is_a_fixed_point():
+    rho0 = np.full((6, 4), 0.2)
+    p = lbm.Params(nx=4, ny=6, T=0.85 * T_C)
+    f0 = lbm.init_state(rho0)
+    f = lbm.run(f0, p, 5)
+    np.testing.assert_allclose(f, f0, rtol=1e-14, atol=0)
+
+
+def test_form_two_gravity_has_zero_net_force():
+    """Eq. Gravity_2 with the same-step domain mean gives zero total force (Sec. II)."""
+    rho0, *_ = column(40, 0.85, nx=3)
+    p = lbm.Params(nx=3, ny=40, T=0.85 * T_C, g=(0.0, -1e-4), form=2)
+    mac = lbm.macroscopic(lbm.run(lbm.init_state(rho0), p, 20), p)
+    assert abs(mac.Fg[1].sum()) < 1e-16 * mac.rho.size
+    assert abs(mac.Fg[1]).max() > 1e-6
+
+
+# ------------------------------------------------------------ invariants over many steps
+@pytest.fixture(scope="module")
+def config1_short():
+    """4 x 200 column, T = 0.85 T_c, g_y = -2e-5, form 1 (the FP64 workload), 2000 steps."""
+    rho0, rv, rl, ps, y0 = column(200, 0.85, nx=4, liquid_rows=100)
+    p = lbm.Params(nx=4, ny=200, T=0.85 * T_C, g=(0.0, -2e-5), form=1)
+    f0 = lbm.init_state(rho0)
+    return p, f0, lbm.run(f0, p, 2000)
+
+
+def test_mass_is_conserved(config1_short):
+    p, f0, f = config1_short
+    assert abs(lbm.mass(f) - lbm.mass(f0)) / lbm.mass(f0) < 1e-13
+
+
+def test_x_uniform_state_stays_bitwise_uniform(config1_short):
+    _, _, f = config1_short
+    assert np.all(f == f[:, :, :1])
+
+
+def test_gravity_forms_identical_at_zero_gravity():
+    rho0, *_ = column(30, 0.8, nx=2)
+    f0 = lbm.init_state(rho0)
+    p1 = lbm.Params(nx=2, ny=30, T=0.8 * T_C, g=(0.0, 0.0), form=1)
+    p2 = dataclasses.replace(p1, form=2)
+    np.testing.assert_array_equal(lbm.run(f0, p1, 50), lbm.run(f0, p2, 50))
+
+
+# ------------------------------------------------------------ physical steady states
+def steady(ny, Tr, g, form, sigma, steps):
+    rho0, rv, rl, ps, y0 = column(ny, Tr)
+    p = lbm.Params(nx=1, ny=ny, T=Tr * T_C, g=(0.0, g), form=form, sigma=sigma)
+    mac = lbm.macroscopic(lbm.run(lbm.init_state(rho0), p, steps), p)
+    return p, mac, rv, rl, ps, y0
+
+
+@pytest.mark.slow
+def test_coexistence_at_zero_gravity_matches_maxwell():
+    """sigma = 1.385 makes the flat-interface coexistence densities follow the
+    Maxwell rule (Sec. IV); without the sigma term the vapour density is far off."""
+    p, mac, rv, rl, ps, _ = steady(64, 0.85, 0.0, 1, 1.385, 8000)
+    rho = mac.rho[:, 0]
+    assert rho[16] == pytest.approx(rl, rel=5e-3)
+    assert rho[48] == pytest.approx(rv, rel=1e-2)
+    assert np.abs(mac.u[1]).max() < 1e-4
+    # flat normal pressure across the interface, Eq. GeneralPressureTensor with c = 1
+    pyy = lbm.normal_pressure(rho, p)[5:-5]
+    assert np.ptp(pyy) < 1e-3 * ps
+    peos = eos.p_eos(rho, p.T, A, B, R)[5:-5]
+    assert np.ptp(peos) > 1.0 * ps       # the EOS pressure alone is far from flat
+    # another sigma coefficient in the tensor would not give a flat profile
+    q = dataclasses.replace(p, sigma=1.385 * 0.8)
+    assert np.ptp(lbm.normal_pressure(rho, q)[5:-5]) > 20 * np.ptp(pyy)
+    p0, mac0, *_ = steady(64, 0.85, 0.0, 1, 0.0, 8000)
+    assert abs(mac0.rho[48, 0] / rv - 1) > 0.1
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("form", [1, 2])
+def test_hydrostatic_balance(form):
+    """dp_yy/dy = F_g,y in the bulk at steady state (Eq. Momentum_Balance_TS)."""
+    ny = 48
+    p, mac, rv, rl, ps, y0 = steady(ny, 0.85, -2e-5, form, 1.385, 6000)
+    rho = mac.rho[:, 0]
+    pyy = lbm.normal_pressure(rho, p)          # rows 1..ny-2
+    dp = 0.5 * (pyy[2:] - pyy[:-2])            # rows 2..ny-3
+    Fg = mac.Fg[1][2:-2, 0]
+    ys = np.arange(2, ny - 2)
+    bulk = (np.abs(ys - y0) > 12) & (ys > 6) & (ys < ny - 7)
+    err = np.abs(dp - Fg)[bulk].max()
+    assert err < 1e-2 * np.abs(Fg[bulk]).max()
+    # and the forcing really acts: the pressure difference across the bulk is the weight
+    assert np.abs(Fg[bulk]).max() > 1e-7
