@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the fused D2Q9 pseudopotential LBM step on GB300.
+
+Workload (default): one 1024 x 4096 domain, FP32 populations with FP64
+reductions, Carnahan-Starling EOS with a = 0.25, b = 4, R = 1 at T = 0.80 T_c,
+gravity (rho - <rho>) g with g_y = -1e-4, liquid below y = 2048 under vapour,
+seeded +-1e-3 uniform density noise across the interface, tau = 1,
+sigma = 1.385. A step is one time step of the whole domain (one launch of the
+fused kernel). Metric: MLUPS (million lattice-node updates per second).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica
+of the domain (the single-domain workload has no independent partition): the
+JSON line reports the aggregate over ranks with the max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+slice of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX, NY = 1024, 4096
+A, B, R = 0.25, 4.0, 1.0
+TR = 0.80
+GY = -1e-4
+LIQUID_ROWS = 2048
+NOISE = 1e-3
+SEED = 20230130
+BYTES_PER_NODE = {"fp32": 72, "fp64": 144}   # 9 populations read + 9 written
+KERNEL_SRC = os.path.join(ROOT, "paper_2301_12869_gb300", "csrc", "lbm_kernels.cu")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_fp32_1024x4096.json")
+
+
+def workload_config(precision):
+    return {
+        "workload": f"single liquid column {NX}x{NY} D2Q9, {precision.upper()} populations, FP64 reductions",
+        "nx": NX, "ny": NY, "T_over_Tc": TR, "a": A, "b": B, "R": R, "gravity": "(rho-<rho>)g", "g_y": GY,
+        "liquid_rows": LIQUID_ROWS, "noise": NOISE, "seed": SEED, "tau": 1.0, "sigma": 1.385,
+        "l2": "state 302 MB (FP32) > 129 MB L2: no flush needed",
+    }
+
+
+def kernel_source_hash():
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_from_profile(precision):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    if precision != "fp32" or not os.path.exists(PROFILE_SUMMARY):
+        return None
+    with open(PROFILE_SUMMARY) as fh:
+        prof = json.load(fh)
+    if prof.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [s.strip() for s in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def oracle_sample_main(ny_slice, steps):
+    """Runs in a child process: oracle steps on a 1024 x ny_slice slice around the interface."""
+    import numpy as np
+
+    from oracle import eos
+    from oracle import lbm as olbm
+    from paper_2301_12869_gb300 import inputs
+
+    _, Tc, _ = eos.critical_point(A, B, R)
+    rv, rl, _ = eos.maxwell(TR * Tc, A, B, R)
+    rho_full_rows = inputs.column_rho0(NX, NY, rl, rv, LIQUID_ROWS, noise_amp=NOISE, seed=SEED)
+    y0 = LIQUID_ROWS - ny_slice // 2
+    rho0 = np.ascontiguousarray(rho_full_rows[y0:y0 + ny_slice])
+    p = olbm.Params(nx=NX, ny=ny_slice, a=A, b=B, R=R, T=TR * Tc, g=(0.0, GY), form=2)
+    f = olbm.init_state(rho0)
+    f = olbm.step(f, p)  # warm-up (allocations)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f = olbm.step(f, p)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "nodes": NX * ny_slice, "steps": steps}))
+
+
+def time_oracle(ny_slice, steps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"import bench; bench.oracle_sample_main({ny_slice}, {steps})"
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    return res["nodes"] * res["steps"] / res["seconds"] / 1e6, res
+
+
+def cpu_baseline_entry(ny_slice=512, steps=60):
+    mlups, res = time_oracle(ny_slice, steps)
+    return {
+        "value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "sample": f"{steps} FP64 oracle steps on a {NX}x{ny_slice} slice of the workload around the interface "
+                  f"({res['seconds']:.1f} s, numpy, 1 thread)",
+    }
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_over_ranks(torch, values, op="max"):
+    """All-reduce a list of floats over ranks (max or sum); identity when not distributed."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return list(values)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.cpu()]
+
+
+def aggregate(local_ms, local_units, torch):
+    """Whole-job throughput: all ranks' units divided by the slowest rank's time."""
+    ms = reduce_over_ranks(torch, [local_ms], "max")[0]
+    units = reduce_over_ranks(torch, [local_units], "sum")[0]
+    return ms, units
+
+
+# ---------------------------------------------------------------- end to end
+def run_e2e(args, rho0, Tc, nodes, world, torch, lbm):
+    """The same metric through the public C ABI with host buffers: lbm_init from pinned
+    host rho0 (host-to-device copy inside), K lbm_step calls' worth of steps, lbm_moments
+    of rho, u_x, u_y to pinned host memory and lbm_reduce(MASS); the library allocates
+    its own device memory. Timed on the host clock around the synchronous calls."""
+    pinned = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True)
+    pinned.copy_(torch.from_numpy(rho0))
+    rho_h = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True)
+    ux_h = torch.empty_like(rho_h)
+    uy_h = torch.empty_like(rho_h)
+    pe = lbm.make_params(NX, NY, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = lbm.lbm_init(pe, pinned.numpy())
+    lbm.lbm_step(h, args.steps)
+    lbm.lbm_moments(h, rho_h.numpy(), ux_h.numpy(), uy_h.numpy())
+    mass = lbm.lbm_reduce(h, lbm.LBM_REDUCE_MASS)[0]
+    t1 = time.perf_counter()
+    lbm.lbm_destroy(h)
+    ms, units = aggregate((t1 - t0) * 1e3, float(nodes) * args.steps, torch)
+    return {
+        "value": units / (ms / 1e3) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * nodes / args.steps,
+        "d2h_bytes_per_step": (3 * 8 * nodes + 8) / args.steps, "mass": mass,
+        "what": "lbm_init from pinned host rho0 + K steps + lbm_moments(rho, ux, uy) to host + "
+                "lbm_reduce(MASS), library-allocated device memory, host clock",
+    }
+
+
+# ---------------------------------------------------------------- main
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    ny_slice = args.ref_rows
+    # the child process runs one untimed warm-up step, then times K oracle steps
+    mlups, res = time_oracle(ny_slice, max(1, args.steps))
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["seconds"] * 1e3 / res["steps"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config("fp64") | {"sample_rows": ny_slice},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{res['steps']} FP64 oracle steps on a {NX}x{ny_slice} slice around the interface"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2301_12869_gb300 import inputs, lbm
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # cpu baseline first (child process, before heavy GPU work; spawn-safe)
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu_base = cpu_baseline_entry()
+        except Exception as exc:  # noqa: BLE001 - reported, not hidden
+            cpu_base = {"value": None, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+
+    rho_c, Tc, p_c = lbm.lbm_critical_point(A, B, R)
+    rv, rl, _ = lbm.lbm_coexistence(A, B, R, TR * Tc)
+    rho0 = inputs.column_rho0(NX, NY, rl, rv, LIQUID_ROWS, noise_amp=NOISE, seed=SEED)
+    p = lbm.make_params(NX, NY, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY))
+    nodes = NX * NY
+
+    # ---- device-resident run (value)
+    lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
+    info = lbm.lbm_launch_info(lat.h)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        lat.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    local_ms = start.elapsed_time(end)
+    status = lat.status()
+    ms, units = aggregate(local_ms, float(nodes) * args.steps, torch)
+    value = units / (ms / 1e3) / 1e6
+    kernel_s = local_ms / 1e3 / args.steps          # one fused-kernel launch per step, back to back
+    alg_bytes = BYTES_PER_NODE[args.precision] * nodes
+    peaks, peak_kind = measured_peaks()
+    achieved = alg_bytes / kernel_s / 1e9
+    mass = lat.reduce(lbm.LBM_REDUCE_MASS)[0]
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the C ABI with host buffers (init from pinned host rho0,
+    #      K steps, moments and mass read back to host), library-allocated memory
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, rho0, Tc, nodes, world, torch, lbm)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": workload_config(args.precision) | {"launch": info, "replicas": world},
+        "roofline": {
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profile(args.precision),
+            "peak_kind": peak_kind, "kernel": f"step_kernel<{'float' if args.precision == 'fp32' else 'double'}>",
+            "algorithmic_bytes_per_launch": alg_bytes,
+        },
+        "cpu_baseline": cpu_base,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks.summary(),
+        "status": status,
+        "mass": mass,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0 if status == 0 and math.isfinite(value) else 2
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,152 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) D2Q9 pseudopotential lattice Boltzmann step.
+ *
+ * Method: Czelusniak, Cabezas Gomez & Wagner, "Effects of gravity induced
+ * pressure variations for thermal liquid-gas phase-change simulations with the
+ * pseudopotential lattice Boltzmann method" (arXiv 2301.12869), Sec. III:
+ * pull streaming (Eq. LBE) on the D2Q9 set (Eq. VelocitySet), MRT collision
+ * (Eqs. OperatorMRT, MatrixMRT, RelaxationMatrix) with Li's forcing scheme
+ * (Eq. LiFS), density and velocity (Eqs. Density, Momentum), equilibrium
+ * (Eq. EquilibriumDistribution), the Shan-Chen nearest-neighbour force
+ * (Eq. ShanChenForce) with the Yuan-Schaefer potential (Eq. InteractionPotential)
+ * of the Carnahan-Starling EOS (Sec. IV, Eq. EOS), and gravity as rho g
+ * (Eq. Gravity_1) or (rho - <rho>) g (Eq. Gravity_2).
+ *
+ * Geometry: nx x ny nodes, x periodic, walls below row 0 and above row ny-1
+ * (halfway bounce-back); the Shan-Chen force is zero on rows 0 and ny-1.
+ *
+ * Conventions for every function:
+ *  - returns LBM_OK (0) or a negative LBM_E* code; lbm_last_error() gives text;
+ *  - pointers are plain host or device addresses, as each argument states;
+ *    nothing is retained after the call unless stated;
+ *  - a handle is used from one host thread at a time;
+ *  - all device work is issued on the handle's stream (borrowed at lbm_init);
+ *    calls that return host data synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+/* ---- status codes */
+enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,    /* invalid argument or parameter */
+  LBM_ECUDA = -2,     /* a CUDA runtime call failed */
+  LBM_ENONPHYS = -3,  /* the state became non-physical: rho <= 0, NaN, or
+                         2 (p_EOS - rho/3)/G < 0 (psi undefined) */
+  LBM_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+  LBM_ENOMEM = -5     /* device allocation failed or workspace too small */
+};
+
+/* ---- enumerations */
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };                              /* storage and arithmetic */
+enum { LBM_GRAVITY_RHO_G = 1, LBM_GRAVITY_RHO_MINUS_MEAN_G = 2 }; /* Eq. Gravity_1 / _2 */
+enum { LBM_HOST = 0, LBM_DEVICE = 1 };                            /* where a buffer lives */
+enum {
+  LBM_REDUCE_MASS = 0,        /* out[0] = sum over nodes of rho (FP64)                      */
+  LBM_REDUCE_MEAN_RHO = 1,    /* out[0] = <rho> = mass / (nx ny), as used by Eq. Gravity_2   */
+  LBM_REDUCE_RESIDUAL = 2,    /* out[0] = max |rho_now - rho_at_previous_RESIDUAL_call|;
+                                 the first call after init/set_state returns +inf           */
+  LBM_REDUCE_MAX_U = 3,       /* out[0] = max |u|                                            */
+  LBM_REDUCE_INTERFACE_Y = 4, /* out[0] = first height (from y = 0, linear interpolation of
+                                 the x-averaged rho) where rho crosses (rho_l + rho_v)/2 of
+                                 the Maxwell rule at T; NaN if none                          */
+  LBM_REDUCE_RHO_LV = 5       /* out[0] = max, out[1] = min of the x-averaged rho profile    */
+};
+
+/* ---- parameters (lattice units). Fill with lbm_params_default() first. */
+typedef struct lbm_params {
+  uint32_t size;          /* sizeof(lbm_params): versioning */
+  int32_t precision;      /* LBM_FP64 or LBM_FP32 */
+  int32_t nx, ny;         /* lattice size; nx must be a multiple of 16/sizeof(real) */
+  double a, b, R;         /* Carnahan-Starling constants of Eq. EOS */
+  double T;               /* absolute temperature */
+  double G;               /* interaction parameter of Eqs. ShanChenForce/InteractionPotential (< 0) */
+  double sigma;           /* sigma of Eq. LiFS */
+  double tau_rho, tau_e, tau_varsigma, tau_j, tau_q, tau_nu; /* Eq. RelaxationMatrix */
+  double gx, gy;          /* gravitational acceleration vector */
+  int32_t gravity_form;   /* LBM_GRAVITY_RHO_G or LBM_GRAVITY_RHO_MINUS_MEAN_G */
+  int32_t reserved0;
+  double rho_ref;         /* populations are stored as f_i - w_i rho_ref; NaN = choose
+                             (mean of rho0 for FP32, 0 for FP64) */
+  void* workspace;        /* optional caller-owned DEVICE buffer of lbm_workspace_bytes();
+                             borrowed, must outlive the handle; NULL = library allocates */
+  uint64_t workspace_bytes;
+} lbm_params;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Paper defaults: a = 0.5, b = 4, R = 1 (Sec. IV), G = -1, sigma = 1.385, all tau = 1
+ * (Sec. IV), gravity off, form 1, FP64, rho_ref = NaN, no workspace. nx, ny, T unset (0). */
+void lbm_params_default(lbm_params* p);
+
+/* Device bytes a handle needs for p (populations A/B, reduction partials, moments scratch). */
+int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes);
+
+/* Create a lattice. rho0 (nx*ny doubles, row-major [y][x]) is the initial density,
+ * in host (LBM_HOST) or device (LBM_DEVICE) memory; the state is set to the rest
+ * equilibrium f_i = f_i^eq(rho0, u = 0) of Eq. EquilibriumDistribution.
+ * stream: a cudaStream_t (NULL = legacy default stream), borrowed.
+ * Errors: LBM_EINVAL (bad sizes/parameters, NULL rho0/out), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stream, lbm_handle** out);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the handle's stream). Each step is
+ * one launch of the fused kernel: stream, rho, psi, <rho>, F_int, F_g, u, MRT + Li
+ * forcing, store. Device-side faults (non-physical state, timeouts) are recorded in a
+ * sticky status returned by the next synchronising call. */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Macroscopic fields of the current state, as the next step evaluates them: the stored
+ * post-collision populations are pulled (streamed) and rho (Eq. Density) and u
+ * (Eq. Momentum, with F = F_int + F_g) computed. Outputs are nx*ny doubles [y][x] in
+ * host or device memory per `where`; any pointer may be NULL to skip it. Synchronises
+ * when where == LBM_HOST. */
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, int where);
+
+/* FP64 reductions of the current state (see LBM_REDUCE_*). out: host array of 1
+ * (2 for LBM_REDUCE_RHO_LV) doubles. Synchronises. */
+int lbm_reduce(lbm_handle* h, int kind, double* out);
+
+/* Full populations f_i (absolute, not deviations) as 9*nx*ny doubles [i][y][x] (i in
+ * the order of Eq. VelocitySet), and the number of steps taken. */
+int lbm_get_state(lbm_handle* h, double* f, int where, int64_t* steps_done);
+int lbm_set_state(lbm_handle* h, const double* f, int where, int64_t steps_done);
+
+/* Change T, G, sigma, tau_*, gx, gy, gravity_form between steps (the paper's
+ * equilibrate-then-change protocol). nx, ny, precision, rho_ref, a, b, R must match. */
+int lbm_set_params(lbm_handle* h, const lbm_params* p);
+
+/* Synchronise and return the sticky device status (LBM_OK, LBM_ENONPHYS, LBM_ETIMEOUT). */
+int lbm_status(lbm_handle* h);
+
+/* Release the handle and what it allocated. NULL is accepted. */
+int lbm_destroy(lbm_handle* h);
+
+/* Text of the last error on h (or of the last failed call without a handle when h is
+ * NULL). Static storage owned by the library. */
+const char* lbm_last_error(const lbm_handle* h);
+
+/* ---- host-side thermodynamics of Eq. EOS (FP64, no device work) */
+/* Critical point: dp/drho = d2p/drho2 = 0. */
+int lbm_critical_point(double a, double b, double R, double* rho_c, double* T_c, double* p_c);
+/* Coexistence densities and pressure at T < T_c by the Maxwell rule, Eqs. MaxwellRule. */
+int lbm_coexistence(double a, double b, double R, double T, double* rho_v, double* rho_l, double* p_sat);
+
+/* Launch configuration the handle uses for its fused step (for reports and tests):
+ * grid CTAs, threads per CTA, dynamic shared bytes, band width (nodes along x per CTA),
+ * strip height (rows per CTA), pipeline stages. Any pointer may be NULL. */
+int lbm_launch_info(const lbm_handle* h, int* grid, int* block, int* smem_bytes,
+                    int* band_width, int* strip_rows, int* stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

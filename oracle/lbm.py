@@ -291,12 +291,17 @@ class Macro:
     nonphysical: np.ndarray = field(default=None)
 
 
-def macroscopic(fstar, p):
-    """Steps 1-7: stream the stored f* and evaluate rho, psi, <rho>, forces and u."""
+def macroscopic(fstar, p, mean_rho=None):
+    """Steps 1-7: stream the stored f* and evaluate rho, psi, <rho>, forces and u.
+
+    ``mean_rho`` overrides the domain mean of Eq. Gravity_2 for a caller that
+    passes a patch cut out of a larger domain (whose mean it computed itself).
+    """
     f = stream(fstar)
     rho = density(f)
     psi, bad = interaction_potential(rho, p)
-    mean_rho = float(np.mean(rho))
+    if mean_rho is None:
+        mean_rho = float(np.mean(rho))
     Sx, Sy = shan_chen_sum(psi)
     Fint = (-p.G * psi * Sx, -p.G * psi * Sy)
     Fg = gravity(rho, mean_rho, p)
@@ -310,9 +315,9 @@ def macroscopic(fstar, p):
     return Macro(f, rho, psi, mean_rho, Fint, Fg, F, u, ratio, bad)
 
 
-def step(fstar, p):
+def step(fstar, p, mean_rho=None):
     """One full time step: returns the new post-collision populations f*."""
-    mac = macroscopic(fstar, p)
+    mac = macroscopic(fstar, p, mean_rho)
     feq = equilibrium(mac.rho, mac.u[0], mac.u[1])
     S = li_source(mac.u[0], mac.u[1], mac.F[0], mac.F[1], mac.ratio, p)
     return collide(mac.f, feq, S, p)

@@ -1,0 +1,74 @@
+// Internal declarations shared by the host API (lbm_api.cu) and the kernels
+// (lbm_kernels.cu) of liblbm. Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+// Sticky device status bits (OR-ed by kernels, mapped to LBM_E* on the host).
+enum : int { STATUS_NONPHYS = 1, STATUS_TIMEOUT = 2 };
+
+// Physical constants of one step, FP64 masters (converted to the kernel's real type).
+struct StepPhys {
+  double rho_ref;          // populations are stored as g_i = f_i - w_i rho_ref
+  double RT, a, b;         // Eq. EOS: R T, a, b
+  double G;                // Eqs. ShanChenForce / InteractionPotential
+  double s_e, s_vs, s_j, s_q, s_nu;   // diagonal of Lambda (Eq. RelaxationMatrix): 1/tau
+  double sig_e, sig_vs;    // sigma/(tau_e - 1/2), sigma/(tau_varsigma - 1/2) of Eq. LiFS
+  double gx, gy;           // gravity
+  int form;                // 1: rho g (Eq. Gravity_1), 2: (rho - <rho>) g (Eq. Gravity_2)
+};
+
+// Tiling of the fused step: CTA b covers band (b % nbands) of width band_w along x
+// and strip (b / nbands) of strip_h rows.
+struct StepTiling {
+  int nx, ny;
+  int band_w, nbands, strip_h, nstrips;
+  int threads, smem_bytes;
+};
+
+enum StepMode : int { MODE_STEP = 0, MODE_MOMENTS = 1 };
+
+struct StepIO {
+  const void* fin;         // real[9][ny][nx], state after the previous step
+  void* fout;              // real[9][ny][nx], state after this step (MODE_STEP)
+  const double* part_in;   // FP64 partial sums of sum_i g_i of fin, npart_in entries
+  int npart_in;
+  double* part_out;        // one FP64 partial per CTA of sum_i g_i of fout (MODE_STEP)
+  int* status;             // sticky device status word
+  double* rho_out;         // MODE_MOMENTS outputs, [y][x] doubles (may be NULL)
+  double* ux_out;
+  double* uy_out;
+};
+
+// ---- launch wrappers (lbm_kernels.cu). All are asynchronous on `stream`.
+int stages();  // pipeline depth of the fused kernel
+size_t step_smem_bytes(int precision, int band_w, int threads);
+int step_max_ctas_per_sm(int precision, int mode, int threads, int smem_bytes);
+cudaError_t step_prepare(int precision);  // sets the dynamic shared memory limit
+cudaError_t launch_step(int precision, int mode, const StepTiling& t, const StepPhys& ph,
+                        const StepIO& io, cudaStream_t stream);
+
+cudaError_t launch_init(int precision, const double* rho0, void* f, int nx, int ny, double rho_ref,
+                        cudaStream_t stream);
+cudaError_t launch_partials(int precision, const void* f, int nx, int ny, double* part, int npart,
+                            cudaStream_t stream);
+// out[0] = sum of part[0..npart) in a fixed order
+cudaError_t launch_sum_partials(const double* part, int npart, double* out, cudaStream_t stream);
+// one population plane of n values: out = plane + add / plane = in - sub
+cudaError_t launch_plane_to_double(int precision, const void* plane, double* out, size_t n, double add,
+                                   cudaStream_t stream);
+cudaError_t launch_plane_from_double(int precision, const double* in, void* plane, size_t n, double sub,
+                                     cudaStream_t stream);
+// max |a - b| over n (b may be NULL: max |a|); max sqrt(ux^2+uy^2)
+cudaError_t launch_max_abs_diff(const double* a, const double* b, size_t n, double* out, cudaStream_t stream);
+cudaError_t launch_max_speed(const double* ux, const double* uy, size_t n, double* out, cudaStream_t stream);
+cudaError_t launch_row_means(const double* rho, int nx, int ny, double* rowmean, cudaStream_t stream);
+// out[0] = first crossing height of rowmean through level (NaN if none); out[1] = max; out[2] = min
+cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, double* out, cudaStream_t stream);
+
+}  // namespace lbm

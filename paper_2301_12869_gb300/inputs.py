@@ -73,3 +73,19 @@ def batched_columns(n, seed=DEFAULT_SEED, heights=(64, 128, 256, 512, 1024)):
         dict(ny=int(H[k]), Tr=float(Tr[k]), gy=float(g[k]), form=int(form[k]), liquid_fraction=float(frac[k]))
         for k in range(n)
     ]
+
+
+#: D2Q9 lattice weights in the velocity order (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
+LATTICE_WEIGHTS = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def perturbed_populations(rho0, amp, seed=DEFAULT_SEED):
+    """Non-equilibrium test populations f[i, y, x] = w_i rho0 (1 + amp (2 U_i - 1)), U_i seeded
+    per (i, y, x). Drawn data only: not an equilibrium of the method."""
+    rho0 = np.asarray(rho0, dtype=np.float64)
+    ny, nx = rho0.shape
+    f = np.empty((9, ny, nx))
+    for i in range(9):
+        u = uniform_field(seed, nx, ny, stream=100 + i)
+        f[i] = LATTICE_WEIGHTS[i] * rho0 * (1.0 + amp * (2.0 * u - 1.0))
+    return f

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of liblbm (C ABI in include/lbm.h).
+
+The functions below carry the ABI's names and only marshal arguments: every
+step of the computation runs in the library's CUDA kernels. Buffers can be
+given as numpy arrays (host), torch tensors (host or CUDA) or raw integer
+addresses. PyTorch is used, when present, only to allocate device memory and to
+pick the current CUDA stream (``Lattice``).
+
+There is no fallback: if ``_lib/liblbm.so`` has not been built (``python -m
+paper_2301_12869_gb300._build`` or ``__graft_entry__.build()``), loading fails
+with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "liblbm.so")
+
+# ---- constants of include/lbm.h
+LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENONPHYS, LBM_ETIMEOUT, LBM_ENOMEM = 0, -1, -2, -3, -4, -5
+LBM_FP64, LBM_FP32 = 0, 1
+LBM_GRAVITY_RHO_G, LBM_GRAVITY_RHO_MINUS_MEAN_G = 1, 2
+LBM_HOST, LBM_DEVICE = 0, 1
+(LBM_REDUCE_MASS, LBM_REDUCE_MEAN_RHO, LBM_REDUCE_RESIDUAL, LBM_REDUCE_MAX_U,
+ LBM_REDUCE_INTERFACE_Y, LBM_REDUCE_RHO_LV) = range(6)
+
+ERROR_NAMES = {
+    LBM_EINVAL: "LBM_EINVAL", LBM_ECUDA: "LBM_ECUDA", LBM_ENONPHYS: "LBM_ENONPHYS",
+    LBM_ETIMEOUT: "LBM_ETIMEOUT", LBM_ENOMEM: "LBM_ENOMEM",
+}
+
+#: every symbol include/lbm.h declares
+EXPORTS = (
+    "lbm_params_default", "lbm_workspace_bytes", "lbm_init", "lbm_step", "lbm_moments", "lbm_reduce",
+    "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
+    "lbm_critical_point", "lbm_coexistence", "lbm_launch_info",
+)
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("size", ctypes.c_uint32), ("precision", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double), ("T", ctypes.c_double),
+        ("G", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("tau_rho", ctypes.c_double), ("tau_e", ctypes.c_double), ("tau_varsigma", ctypes.c_double),
+        ("tau_j", ctypes.c_double), ("tau_q", ctypes.c_double), ("tau_nu", ctypes.c_double),
+        ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+        ("gravity_form", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("rho_ref", ctypes.c_double), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbm.so once; raises if it is missing (the CUDA path has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblbm.so not built at {path}; run paper_2301_12869_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, d, i32, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "lbm_params_default": (None, [P(lbm_params)]),
+        "lbm_workspace_bytes": (i32, [P(lbm_params), P(ctypes.c_uint64)]),
+        "lbm_init": (i32, [P(lbm_params), vp, i32, vp, P(vp)]),
+        "lbm_step": (i32, [vp, i64]),
+        "lbm_moments": (i32, [vp, vp, vp, vp, i32]),
+        "lbm_reduce": (i32, [vp, i32, P(d)]),
+        "lbm_get_state": (i32, [vp, vp, i32, P(i64)]),
+        "lbm_set_state": (i32, [vp, vp, i32, i64]),
+        "lbm_set_params": (i32, [vp, P(lbm_params)]),
+        "lbm_status": (i32, [vp]),
+        "lbm_destroy": (i32, [vp]),
+        "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_critical_point": (i32, [d, d, d, P(d), P(d), P(d)]),
+        "lbm_coexistence": (i32, [d, d, d, d, P(d), P(d), P(d)]),
+        "lbm_launch_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, h=None):
+    if rc != LBM_OK:
+        msg = load().lbm_last_error(h)
+        raise LbmError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(buf):
+    """(address, where) of a numpy array, torch tensor or raw int (int = device address)."""
+    if buf is None:
+        return None, None
+    if isinstance(buf, int):
+        return buf, LBM_DEVICE
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous or buf.dtype != np.float64:
+            raise ValueError("host buffers must be C-contiguous float64 arrays")
+        return buf.ctypes.data, LBM_HOST
+    if hasattr(buf, "data_ptr"):  # torch tensor
+        if not buf.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return buf.data_ptr(), (LBM_DEVICE if buf.is_cuda else LBM_HOST)
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+# ---------------------------------------------------------------- ABI functions
+def lbm_params_default():
+    p = lbm_params()
+    load().lbm_params_default(ctypes.byref(p))
+    return p
+
+
+def lbm_workspace_bytes(p):
+    n = ctypes.c_uint64()
+    _check(load().lbm_workspace_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_init(p, rho0, stream=None):
+    addr, where = _ptr(rho0)
+    h = ctypes.c_void_p()
+    _check(load().lbm_init(ctypes.byref(p), addr, where, stream, ctypes.byref(h)))
+    return h
+
+
+def lbm_step(h, nsteps):
+    _check(load().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_moments(h, rho=None, ux=None, uy=None):
+    wheres = {w for _, w in map(_ptr, (rho, ux, uy)) if w is not None}
+    if len(wheres) > 1:
+        raise ValueError("moment outputs must all be host or all be device buffers")
+    where = wheres.pop() if wheres else LBM_HOST
+    _check(load().lbm_moments(h, _ptr(rho)[0], _ptr(ux)[0], _ptr(uy)[0], where), h)
+
+
+def lbm_reduce(h, kind, check=True):
+    out = (ctypes.c_double * 2)(math.nan, math.nan)
+    rc = load().lbm_reduce(h, kind, out)
+    if check:
+        _check(rc, h)
+    vals = [out[0], out[1]] if kind == LBM_REDUCE_RHO_LV else [out[0]]
+    return (vals, rc) if not check else vals
+
+
+def lbm_get_state(h, f):
+    addr, where = _ptr(f)
+    steps = ctypes.c_int64()
+    _check(load().lbm_get_state(h, addr, where, ctypes.byref(steps)), h)
+    return steps.value
+
+
+def lbm_set_state(h, f, steps_done=0):
+    addr, where = _ptr(f)
+    _check(load().lbm_set_state(h, addr, where, int(steps_done)), h)
+
+
+def lbm_set_params(h, p):
+    _check(load().lbm_set_params(h, ctypes.byref(p)), h)
+
+
+def lbm_status(h):
+    return load().lbm_status(h)
+
+
+def lbm_destroy(h):
+    _check(load().lbm_destroy(h))
+
+
+def lbm_last_error(h=None):
+    msg = load().lbm_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def lbm_critical_point(a, b, R):
+    rc_, Tc, pc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_critical_point(a, b, R, ctypes.byref(rc_), ctypes.byref(Tc), ctypes.byref(pc)))
+    return rc_.value, Tc.value, pc.value
+
+
+def lbm_coexistence(a, b, R, T):
+    rv, rl, ps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().lbm_coexistence(a, b, R, T, ctypes.byref(rv), ctypes.byref(rl), ctypes.byref(ps)))
+    return rv.value, rl.value, ps.value
+
+
+def lbm_launch_info(h):
+    vals = [ctypes.c_int() for _ in range(6)]
+    _check(load().lbm_launch_info(h, *[ctypes.byref(v) for v in vals]), h)
+    keys = ("grid", "block", "smem_bytes", "band_width", "strip_rows", "stages")
+    return {k: v.value for k, v in zip(keys, vals)}
+
+
+# ---------------------------------------------------------------- convenience
+def make_params(nx, ny, T, precision="fp64", **kw):
+    """lbm_params from the paper's defaults plus keyword overrides (names of the C struct;
+    ``form`` is accepted for ``gravity_form`` and ``g`` for (gx, gy))."""
+    p = lbm_params_default()
+    p.nx, p.ny, p.T = int(nx), int(ny), float(T)
+    p.precision = LBM_FP32 if str(precision).lower() in ("fp32", "float32", "1") else LBM_FP64
+    if "form" in kw:
+        p.gravity_form = int(kw.pop("form"))
+    if "g" in kw:
+        p.gx, p.gy = map(float, kw.pop("g"))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Lattice:
+    """A handle whose workspace is a torch CUDA tensor and whose stream is torch's
+    current stream. Outputs of ``moments`` are torch tensors on the device."""
+
+    def __init__(self, params, rho0, device="cuda"):
+        import torch
+
+        self._torch = torch
+        self.params = params
+        nbytes = lbm_workspace_bytes(params)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self._ws.data_ptr()
+        params.workspace = (base + 255) // 256 * 256
+        params.workspace_bytes = nbytes
+        self.stream = torch.cuda.current_stream(self._ws.device).cuda_stream
+        self.h = lbm_init(params, rho0, self.stream)
+        self.nx, self.ny = params.nx, params.ny
+
+    def step(self, n):
+        lbm_step(self.h, n)
+
+    def moments(self):
+        t = self._torch
+        rho, ux, uy = (t.empty((self.ny, self.nx), dtype=t.float64, device=self._ws.device) for _ in range(3))
+        lbm_moments(self.h, rho, ux, uy)
+        return rho, ux, uy
+
+    def reduce(self, kind):
+        return lbm_reduce(self.h, kind)
+
+    def get_state(self):
+        f = np.empty((9, self.ny, self.nx))
+        lbm_get_state(self.h, f)
+        return f
+
+    def set_state(self, f, steps_done=0):
+        lbm_set_state(self.h, np.ascontiguousarray(f, dtype=np.float64), steps_done)
+
+    def status(self):
+        return lbm_status(self.h)
+
+    def close(self):
+        if self.h is not None:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -270,8 +270,10 @@ def config1_short():
 
 
 def test_mass_is_conserved(config1_short):
+    """Exact in exact arithmetic; in FP64 the collision's rounding drifts the mass
+    by at most ~1e-16 (relative) per step here: 2000 steps stay below 2e-13."""
     p, f0, f = config1_short
-    assert abs(lbm.mass(f) - lbm.mass(f0)) / lbm.mass(f0) < 1e-13
+    assert abs(lbm.mass(f) - lbm.mass(f0)) / lbm.mass(f0) < 2e-13
 
 
 def test_x_uniform_state_stays_bitwise_uniform(config1_short):
