@@ -39,8 +39,27 @@ LIQUID_ROWS = 2048
 NOISE = 1e-3
 SEED = 20230130
 BYTES_PER_NODE = {"fp32": 72, "fp64": 144}   # 9 populations read + 9 written
+# With (rho - <rho>) g at g_y = -1e-4 the 2048-row vapour column accelerates freely
+# (max |u| = 0.42 after 500 steps, NaN before 1000): the workload is physical only for
+# its first ~500 steps. Timed runs longer than WINDOW steps restore the post-warm-up
+# state every WINDOW steps (lbm_set_state from a device snapshot, inside the timing).
+WINDOW = 400
 KERNEL_SRC = os.path.join(ROOT, "paper_2301_12869_gb300", "csrc", "lbm_kernels.cu")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_fp32_1024x4096.json")
+
+
+def run_steps(lbm, h, nsteps, snapshot):
+    """nsteps fused steps; every WINDOW steps the snapshot state is restored on the device.
+    Returns the number of restores."""
+    done = restores = 0
+    while done < nsteps:
+        n = min(WINDOW, nsteps - done)
+        lbm.lbm_step(h, n)
+        done += n
+        if done < nsteps:
+            lbm.lbm_set_state(h, snapshot)
+            restores += 1
+    return restores
 
 
 def workload_config(precision):
@@ -49,6 +68,8 @@ def workload_config(precision):
         "nx": NX, "ny": NY, "T_over_Tc": TR, "a": A, "b": B, "R": R, "gravity": "(rho-<rho>)g", "g_y": GY,
         "liquid_rows": LIQUID_ROWS, "noise": NOISE, "seed": SEED, "tau": 1.0, "sigma": 1.385,
         "l2": "state 302 MB (FP32) > 129 MB L2: no flush needed",
+        "physical_window": f"state restored from the post-warm-up snapshot every {WINDOW} steps "
+                           "(the workload goes non-physical after ~500 steps)",
     }
 
 
@@ -77,7 +98,7 @@ def traffic_from_profile(precision):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms while running."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -91,7 +112,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -198,7 +219,7 @@ def aggregate(local_ms, local_units, torch):
 
 
 # ---------------------------------------------------------------- end to end
-def run_e2e(args, rho0, Tc, nodes, world, torch, lbm):
+def run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot):
     """The same metric through the public C ABI with host buffers: lbm_init from pinned
     host rho0 (host-to-device copy inside), K lbm_step calls' worth of steps, lbm_moments
     of rho, u_x, u_y to pinned host memory and lbm_reduce(MASS); the library allocates
@@ -214,7 +235,7 @@ def run_e2e(args, rho0, Tc, nodes, world, torch, lbm):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = lbm.lbm_init(pe, pinned.numpy())
-    lbm.lbm_step(h, args.steps)
+    run_steps(lbm, h, args.steps, snapshot)
     lbm.lbm_moments(h, rho_h.numpy(), ux_h.numpy(), uy_h.numpy())
     mass = lbm.lbm_reduce(h, lbm.LBM_REDUCE_MASS)[0]
     t1 = time.perf_counter()
@@ -251,8 +272,8 @@ def run_reference(args, world, rank):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -298,6 +319,8 @@ def main(argv=None):
     lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
     info = lbm.lbm_launch_info(lat.h)
     lat.step(args.warmup)
+    snapshot = torch.empty((9, NY, NX), dtype=torch.float64, device="cuda")
+    lbm.lbm_get_state(lat.h, snapshot)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,7 +329,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         start.record(stream)
-        lat.step(args.steps)
+        restores = run_steps(lbm, lat.h, args.steps, snapshot)
         end.record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -315,7 +338,8 @@ def main(argv=None):
     status = lat.status()
     ms, units = aggregate(local_ms, float(nodes) * args.steps, torch)
     value = units / (ms / 1e3) / 1e6
-    kernel_s = local_ms / 1e3 / args.steps          # one fused-kernel launch per step, back to back
+    # one fused-kernel launch per step, back to back; the restores are counted against it
+    kernel_s = local_ms / 1e3 / args.steps
     alg_bytes = BYTES_PER_NODE[args.precision] * nodes
     peaks, peak_kind = measured_peaks()
     achieved = alg_bytes / kernel_s / 1e9
@@ -328,7 +352,8 @@ def main(argv=None):
     #      K steps, moments and mass read back to host), library-allocated memory
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, rho0, Tc, nodes, world, torch, lbm)
+        e2e = run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot)
+    del snapshot
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -346,7 +371,8 @@ def main(argv=None):
         },
         "cpu_baseline": cpu_base,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps + restores * (9 + 1),
+        "restores": restores,
         "clocks": clocks.summary(),
         "status": status,
         "mass": mass,
