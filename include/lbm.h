@@ -146,6 +146,33 @@ int lbm_coexistence(double a, double b, double R, double T, double* rho_v, doubl
 int lbm_launch_info(const lbm_handle* h, int* grid, int* block, int* smem_bytes,
                     int* band_width, int* strip_rows, int* stages);
 
+/* ---- one step without device allocation (this entry point has no counterpart in the paper)
+ *
+ * Some callers cannot call cudaMalloc: a host loop that must not stall other streams on
+ * the implicit device synchronisation an allocation can bring, a process whose device
+ * memory is reserved up front by another allocator, or a plug-in that may not create
+ * allocations of its own. lbm_step_noalloc runs one time step f_out = step(f_in) - the
+ * same fused kernel as lbm_step - on caller-owned device arrays and allocates nothing.
+ *
+ * f_in, f_out: distinct DEVICE arrays of 9*nx*ny reals (float for LBM_FP32, double for
+ *   LBM_FP64), layout [i][y][x] in the order of Eq. VelocitySet, holding the deviations
+ *   f_i - w_i rho_ref with rho_ref = p->rho_ref (NaN means 0). Caller-owned; read / written.
+ * p: as for lbm_init; p->workspace is ignored. stream: a cudaStream_t (NULL = default).
+ * Scratch: the FP64 partial mass sums that give <rho> (Eq. Gravity_2) and a status word
+ *   live in a file-scope __device__ array of 65 792 bytes inside liblbm, held by every
+ *   device that loads the library until the process exits. Its 4096 partial slots bound
+ *   the step's grid: lattices wider than 4096 x-bands (nx > 4 194 304 in FP32, 2 097 152 in
+ *   FP64) are rejected with LBM_EINVAL.
+ * Every call shares that array and leaves its own values there; the status word is
+ *   cleared at the start of each call. Calls that overlap on the GPU (several streams, or
+ *   host threads without ordering) race on it: serialise them.
+ * The first call on a device (per process) looks up the array's device address with
+ *   cudaGetSymbolAddress and sets the kernels' shared-memory limit; make that first call
+ *   before any stream capture.
+ * Synchronises `stream`. Returns LBM_OK, LBM_EINVAL, LBM_ECUDA, or the device status of
+ *   this step (LBM_ENONPHYS, LBM_ETIMEOUT); text in lbm_last_error(NULL). */
+int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

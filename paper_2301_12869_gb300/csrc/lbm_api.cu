@@ -284,6 +284,14 @@ int run_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
 
 }  // namespace
 
+// ---- wrappers for the other translation units (lbm_internal.h)
+namespace lbm {
+int validate_params(const lbm_params* p, char* err) { return validate(p, err); }
+StepPhys phys_from_params(const lbm_params& p, double rho_ref) { return phys_of(p, rho_ref); }
+int plan_step_tiling(const lbm_params& p, int nsm, StepTiling* t, char* err) { return plan_tiling(p, nsm, t, err); }
+void set_last_error(const char* msg) { set_err(g_err, "%s", msg); }
+}  // namespace lbm
+
 // ================================================================== public ABI
 extern "C" {
 

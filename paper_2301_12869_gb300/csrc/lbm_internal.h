@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm.h"
+
 namespace lbm {
 
 // Sticky device status bits (OR-ed by kernels, mapped to LBM_E* on the host).
@@ -70,5 +72,11 @@ cudaError_t launch_max_speed(const double* ux, const double* uy, size_t n, doubl
 cudaError_t launch_row_means(const double* rho, int nx, int ny, double* rowmean, cudaStream_t stream);
 // out[0] = first crossing height of rowmean through level (NaN if none); out[1] = max; out[2] = min
 cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, double* out, cudaStream_t stream);
+
+// ---- host helpers of lbm_api.cu shared with other entry points (same behaviour as lbm_init's)
+int validate_params(const lbm_params* p, char* err);  // err: 512 bytes
+StepPhys phys_from_params(const lbm_params& p, double rho_ref);
+int plan_step_tiling(const lbm_params& p, int nsm, StepTiling* t, char* err);
+void set_last_error(const char* msg);  // text returned by lbm_last_error(NULL)
 
 }  // namespace lbm

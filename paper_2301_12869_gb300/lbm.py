@@ -37,7 +37,7 @@ ERROR_NAMES = {
 EXPORTS = (
     "lbm_params_default", "lbm_workspace_bytes", "lbm_init", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
-    "lbm_critical_point", "lbm_coexistence", "lbm_launch_info",
+    "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
 )
 
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "lbm_critical_point": (i32, [d, d, d, P(d), P(d), P(d)]),
         "lbm_coexistence": (i32, [d, d, d, d, P(d), P(d), P(d)]),
         "lbm_launch_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]),
+        "lbm_step_noalloc": (i32, [P(lbm_params), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +210,12 @@ def lbm_launch_info(h):
     _check(load().lbm_launch_info(h, *[ctypes.byref(v) for v in vals]), h)
     keys = ("grid", "block", "smem_bytes", "band_width", "strip_rows", "stages")
     return {k: v.value for k, v in zip(keys, vals)}
+
+
+def lbm_step_noalloc(p, f_in, f_out, stream=None):
+    """One step f_out = step(f_in) on caller-owned device arrays of deviations
+    f_i - w_i rho_ref (real type of p.precision), with no device allocation."""
+    _check(load().lbm_step_noalloc(ctypes.byref(p), _ptr(f_in)[0], _ptr(f_out)[0], stream))
 
 
 # ---------------------------------------------------------------- convenience
