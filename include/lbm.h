@@ -146,6 +146,20 @@ int lbm_coexistence(double a, double b, double R, double T, double* rho_v, doubl
 int lbm_launch_info(const lbm_handle* h, int* grid, int* block, int* smem_bytes,
                     int* band_width, int* strip_rows, int* stages);
 
+/* Tile autotuner: times each tile variant of the fused kernel (band width and threads per
+ * CTA) for `steps` launches on this lattice - every candidate reads the current state and
+ * writes the spare buffer, so the state is unchanged - and keeps the fastest for later
+ * lbm_step / lbm_moments calls. variant, ms (mean time per step of the winner): may be NULL.
+ * Synchronises the handle's stream. */
+int lbm_autotune(lbm_handle* h, int steps, int* variant, double* ms);
+
+/* Number of tile variants of the fused kernel for a precision (LBM_EINVAL otherwise). */
+int lbm_tile_variants(int precision);
+
+/* Use tile variant `variant` (0 = default, as chosen by lbm_init) for later steps, e.g. a
+ * result of lbm_autotune saved from an earlier run. LBM_EINVAL if out of range. */
+int lbm_set_tiling(lbm_handle* h, int variant);
+
 /* ---- one step without device allocation (this entry point has no counterpart in the paper)
  *
  * Some callers cannot call cudaMalloc: a host loop that must not stall other streams on

@@ -123,7 +123,8 @@ struct lbm_handle {
   double* parts[2] = {nullptr, nullptr};
   int pcur = 0;          // parts[pcur] holds the partials of f[cur]
   int npart = 0;         // partials in parts[pcur]
-  int P = 0;             // partial slots per buffer (= step grid)
+  int P = 0;             // CTAs of the current step launch (= partials it writes)
+  int Pcap = 0;          // partial slots per buffer (largest grid over the tile variants)
   int* status = nullptr;
   double* red = nullptr; // small device outputs
   double* rho_now = nullptr;
@@ -145,27 +146,42 @@ struct Layout {
   size_t f0, f1, parts0, parts1, status, red, rho_now, rho_prev, ux, uy, rowmean, total;
 };
 
-int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err) {
-  const int s = p.precision == LBM_FP32 ? 4 : 8;
-  const int H = 16 / s;
-  const int bw_max = p.precision == LBM_FP32 ? 1024 : 512;
+int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int variant = 0) {
+  const int H = p.precision == LBM_FP32 ? 4 : 2;
+  int bw_max = 0;
+  if (!lbm::step_variant_info(p.precision, variant, &bw_max, &t->threads, &t->smem_bytes)) {
+    set_err(err, "unknown tile variant %d", variant);
+    return LBM_EINVAL;
+  }
+  t->variant = variant;
   t->nx = p.nx;
   t->ny = p.ny;
   t->band_w = std::min(p.nx, bw_max);
   t->nbands = (p.nx + t->band_w - 1) / t->band_w;
-  t->threads = std::min(512, std::max(32, (t->band_w + 31) / 32 * 32));
-  t->smem_bytes = int(lbm::step_smem_bytes(p.precision, t->band_w, t->threads));
   if (t->band_w % H) {
     set_err(err, "internal: band width %d not a multiple of %d", t->band_w, H);
     return LBM_EINVAL;
   }
-  int per_sm = lbm::step_max_ctas_per_sm(p.precision, lbm::MODE_STEP, t->threads, t->smem_bytes);
+  int per_sm = lbm::step_max_ctas_per_sm(p.precision, variant, t->threads, t->smem_bytes);
   if (per_sm < 1) per_sm = 1;
+  // one wave: every CTA resident at once, so neighbouring strips stream their shared
+  // halo rows at the same time
   const long target = long(nsm) * per_sm;
-  long nstrips = std::max(1L, std::min<long>(p.ny, (target + t->nbands - 1) / t->nbands));
+  long nstrips = std::max(1L, std::min<long>(p.ny, target / t->nbands));
   t->strip_h = int((p.ny + nstrips - 1) / nstrips);
   t->nstrips = (p.ny + t->strip_h - 1) / t->strip_h;
   return LBM_OK;
+}
+
+// Partial slots a handle needs: the largest grid over the tile variants.
+int max_partials(const lbm_params& p, int nsm, char* err) {
+  int P = 0;
+  for (int v = 0; v < lbm::step_num_variants(p.precision); ++v) {
+    lbm::StepTiling t;
+    if (plan_tiling(p, nsm, &t, err, v)) return -1;
+    P = std::max(P, t.nbands * t.nstrips);
+  }
+  return P;
 }
 
 Layout layout_for(const lbm_params& p, int P) {
@@ -321,7 +337,9 @@ int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes) {
   }
   lbm::StepTiling t;
   if ((rc = plan_tiling(*p, nsm, &t, g_err))) return rc;
-  *bytes = layout_for(*p, t.nbands * t.nstrips).total;
+  const int cap = max_partials(*p, nsm, g_err);
+  if (cap < 0) return LBM_EINVAL;
+  *bytes = layout_for(*p, cap).total;
   return LBM_OK;
 }
 
@@ -351,7 +369,9 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
   if (e != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return fail(LBM_ECUDA); }
   if ((rc = plan_tiling(*p, h->nsm, &h->tiling, h->err))) return fail(rc);
   h->P = h->tiling.nbands * h->tiling.nstrips;
-  const Layout L = layout_for(*p, h->P);
+  h->Pcap = max_partials(*p, h->nsm, h->err);
+  if (h->Pcap < 0) return fail(LBM_EINVAL);
+  const Layout L = layout_for(*p, h->Pcap);
   if (p->workspace) {
     if (p->workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(p->workspace) & 255)) {
       set_err(h->err, "workspace needs %zu bytes at 256-byte alignment (got %llu)", L.total,
@@ -602,6 +622,68 @@ int lbm_coexistence(double a, double b, double R, double T, double* rho_v, doubl
   if (rho_v) *rho_v = rv;
   if (rho_l) *rho_l = rl;
   if (p_sat) *p_sat = ps;
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_handle* h, int steps, int* variant, double* ms) {
+  if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
+  if (steps < 1) { set_err(h->err, "steps must be >= 1"); return LBM_EINVAL; }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LBM_CUDA(h, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(h, ce, "cudaEventCreate"); }
+  int best = -1, rc = LBM_OK;
+  float best_ms = 0.f;
+  lbm::StepTiling best_t{};
+  // every candidate reads the current state and writes the other buffer; the state and
+  // its partial sums are left as they were
+  lbm::StepIO io{};
+  io.fin = h->f[h->cur];
+  io.fout = h->f[1 - h->cur];
+  io.part_in = h->parts[h->pcur];
+  io.npart_in = h->npart;
+  io.part_out = h->parts[1 - h->pcur];
+  io.status = h->status;
+  for (int v = 0; v < lbm::step_num_variants(h->p.precision) && rc == LBM_OK; ++v) {
+    lbm::StepTiling t;
+    if (plan_tiling(h->p, h->nsm, &t, h->err, v)) continue;
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = lbm::launch_step(h->p.precision, lbm::MODE_STEP, t, h->phys, io, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = lbm::launch_step(h->p.precision, lbm::MODE_STEP, t, h->phys, io, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t_ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, e0, e1);
+    if (e != cudaSuccess) { rc = cuda_fail(h, e, "autotune"); break; }
+    if (best < 0 || t_ms < best_ms) { best = v; best_ms = t_ms; best_t = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best < 0) { set_err(h->err, "no tile variant fits this lattice"); return LBM_EINVAL; }
+  h->tiling = best_t;
+  h->P = best_t.nbands * best_t.nstrips;
+  if (variant) *variant = best;
+  if (ms) *ms = double(best_ms) / steps;
+  return LBM_OK;
+}
+
+int lbm_tile_variants(int precision) {
+  if (precision != LBM_FP32 && precision != LBM_FP64) {
+    set_err(g_err, "precision must be LBM_FP32 or LBM_FP64");
+    return LBM_EINVAL;
+  }
+  return lbm::step_num_variants(precision);
+}
+
+int lbm_set_tiling(lbm_handle* h, int variant) {
+  if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
+  lbm::StepTiling t;
+  int rc = plan_tiling(h->p, h->nsm, &t, h->err, variant);
+  if (rc) return rc;
+  h->tiling = t;
+  h->P = t.nbands * t.nstrips;
   return LBM_OK;
 }
 

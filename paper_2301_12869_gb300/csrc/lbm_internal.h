@@ -31,6 +31,7 @@ struct StepTiling {
   int nx, ny;
   int band_w, nbands, strip_h, nstrips;
   int threads, smem_bytes;
+  int variant;  // index into the kernel's tile variants (0 = default)
 };
 
 enum StepMode : int { MODE_STEP = 0, MODE_MOMENTS = 1 };
@@ -49,8 +50,10 @@ struct StepIO {
 
 // ---- launch wrappers (lbm_kernels.cu). All are asynchronous on `stream`.
 int stages();  // pipeline depth of the fused kernel
-size_t step_smem_bytes(int precision, int band_w, int threads);
-int step_max_ctas_per_sm(int precision, int mode, int threads, int smem_bytes);
+int step_num_variants(int precision);
+// widest x band one CTA covers, threads per CTA, dynamic shared bytes of a tile variant
+bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem);
+int step_max_ctas_per_sm(int precision, int variant, int threads, int smem_bytes);
 cudaError_t step_prepare(int precision);  // sets the dynamic shared memory limit
 cudaError_t launch_step(int precision, int mode, const StepTiling& t, const StepPhys& ph,
                         const StepIO& io, cudaStream_t stream);
@@ -76,7 +79,7 @@ cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, dou
 // ---- host helpers of lbm_api.cu shared with other entry points (same behaviour as lbm_init's)
 int validate_params(const lbm_params* p, char* err);  // err: 512 bytes
 StepPhys phys_from_params(const lbm_params& p, double rho_ref);
-int plan_step_tiling(const lbm_params& p, int nsm, StepTiling* t, char* err);
+int plan_step_tiling(const lbm_params& p, int nsm, StepTiling* t, char* err);  // default variant
 void set_last_error(const char* msg);  // text returned by lbm_last_error(NULL)
 
 }  // namespace lbm

@@ -32,12 +32,12 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 namespace lbm {
 namespace {
 
 constexpr int kStages = 4;           // pipeline depth (rows of source planes in shared memory)
-constexpr int kMaxThreads = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // bound of an mbarrier wait (about 2 s)
 
 // ---- D2Q9 velocity set, Eq. VelocitySet: c_0 = (0,0); c_1..4 = (1,0),(0,1),(-1,0),(0,-1);
@@ -162,35 +162,48 @@ __device__ __forceinline__ double warp_sum_partials(const double* part, int n) {
 }
 
 // ---- per-node physics
+// Division and square root: IEEE in FP64 (the FP64 path is checked to 1e-14); in FP32
+// the fast intrinsics __fdividef (<= 2 ulp) and rsqrtf (<= 2 ulp) add at most a few
+// ulp, far inside the FP32 path's 1e-6 bound against the FP64 oracle.
+template <typename T>
+__device__ __forceinline__ T fast_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ __forceinline__ T nonneg_sqrt(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float nonneg_sqrt<float>(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 // Eq. EOS (Carnahan-Starling) and Eq. InteractionPotential with c = 1, c_s^2 = 1/3.
 template <typename T>
 __device__ __forceinline__ T psi_of(T rho, const PhysT<T>& k, int& flag) {
   const T eta = k.b4 * rho;
   const T om = T(1) - eta;
   const T num = T(1) + eta * (T(1) + eta * (T(1) - eta));
-  const T p = rho * k.RT * num / (om * om * om) - k.a * rho * rho;
+  const T p = fast_div(rho * k.RT * num, om * om * om) - k.a * rho * rho;
   T rad = k.twoOverG * (p - rho * T(1.0 / 3.0));
   if (!(rad >= T(0))) {  // psi undefined (or NaN): non-physical state
     flag |= STATUS_NONPHYS;
     rad = T(0);
   }
-  return sqrt(rad);
+  return nonneg_sqrt(rad);
 }
 
 // Pull streaming (Eq. LBE) from a stage: slot i holds the source row of plane i at
 // x offset -c_ix, or, where the link crosses a wall, plane opp(i) of the node's own
 // row and column (halfway bounce-back: no x offset).
-template <typename T>
-__device__ __forceinline__ void pull(const T* st, int SW, int loc, bool lo_wall, bool hi_wall, T (&g)[9]) {
-  g[0] = st[0 * SW + loc];
-  g[1] = st[1 * SW + loc - 1];
-  g[2] = st[2 * SW + loc];
-  g[3] = st[3 * SW + loc + 1];
-  g[4] = st[4 * SW + loc];
-  g[5] = st[5 * SW + loc - (lo_wall ? 0 : 1)];
-  g[6] = st[6 * SW + loc + (lo_wall ? 0 : 1)];
-  g[7] = st[7 * SW + loc + (hi_wall ? 0 : 1)];
-  g[8] = st[8 * SW + loc - (hi_wall ? 0 : 1)];
+template <typename T, int SW>
+__device__ __forceinline__ void pull(const T* st, int loc, bool lo_wall, bool hi_wall, T (&g)[9]) {
+  const T* p = st + loc;
+  g[0] = p[0 * SW];
+  g[1] = p[1 * SW - 1];
+  g[2] = p[2 * SW];
+  g[3] = p[3 * SW + 1];
+  g[4] = p[4 * SW];
+  g[5] = lo_wall ? p[5 * SW] : p[5 * SW - 1];
+  g[6] = lo_wall ? p[6 * SW] : p[6 * SW + 1];
+  g[7] = hi_wall ? p[7 * SW] : p[7 * SW + 1];
+  g[8] = hi_wall ? p[8 * SW] : p[8 * SW - 1];
 }
 
 template <typename T>
@@ -201,7 +214,7 @@ __device__ __forceinline__ T sum9(const T (&g)[9]) {
 // One node: forces, velocity and the MRT collision with Li's forcing in moment
 // space, on deviations g. (Sx, Sy) = sum_i w(|c_i|^2) psi(x + c_i) c_i (zero on wall
 // rows), so F_int = -G psi S and |F_int|^2 / psi^2 = G^2 |S|^2.
-template <typename T>
+template <typename T, bool UNIT>
 __device__ __forceinline__ void collide_node(const T (&g)[9], T psi_c, T Sx, T Sy, T dmean, const PhysT<T>& k,
                                              T (&o)[9], T& rho_o, T& ux_o, T& uy_o, int& flag) {
   // moments of g with the rows of Eq. MatrixMRT
@@ -220,7 +233,7 @@ __device__ __forceinline__ void collide_node(const T (&g)[9], T psi_c, T Sx, T S
   const T Fy = -k.G * psi_c * Sy + base * k.gy;
   if (!(rho > T(0))) flag |= STATUS_NONPHYS;
   // Eq. Momentum: rho u = sum_i f_i c_i + F/2
-  const T inv_rho = T(1) / rho;
+  const T inv_rho = fast_div(T(1), rho);
   const T ux = (jx + T(0.5) * Fx) * inv_rho;
   const T uy = (jy + T(0.5) * Fy) * inv_rho;
   rho_o = rho;
@@ -248,14 +261,27 @@ __device__ __forceinline__ void collide_node(const T (&g)[9], T psi_c, T Sx, T S
   const T St_pxx = T(2) * (ux * Fx - uy * Fy);
   const T St_pxy = ux * Fy + uy * Fx;
   // m* = m - Lambda (m - m_eq) + (I - Lambda/2) S~   (Eqs. LBE, OperatorMRT, LiFS)
-  const T e_s = m_e - k.s_e * (m_e - meq_e) + k.h_e * St_e;
-  const T eps_s = m_eps - k.s_vs * (m_eps - meq_eps) + k.h_vs * St_eps;
-  const T jx_s = jx - k.s_j * (jx - rux) + k.h_j * Fx;
-  const T qx_s = m_qx - k.s_q * (m_qx + rux) - k.h_q * Fx;
-  const T jy_s = jy - k.s_j * (jy - ruy) + k.h_j * Fy;
-  const T qy_s = m_qy - k.s_q * (m_qy + ruy) - k.h_q * Fy;
-  const T pxx_s = m_pxx - k.s_nu * (m_pxx - meq_pxx) + k.h_nu * St_pxx;
-  const T pxy_s = m_pxy - k.s_nu * (m_pxy - meq_pxy) + k.h_nu * St_pxy;
+  T e_s, eps_s, jx_s, qx_s, jy_s, qy_s, pxx_s, pxy_s;
+  if constexpr (UNIT) {
+    // every tau = 1 (Lambda = I): m* = m_eq + S~/2, the same operator without m - m_eq
+    e_s = meq_e + T(0.5) * St_e;
+    eps_s = meq_eps + T(0.5) * St_eps;
+    jx_s = rux + T(0.5) * Fx;
+    qx_s = -rux - T(0.5) * Fx;
+    jy_s = ruy + T(0.5) * Fy;
+    qy_s = -ruy - T(0.5) * Fy;
+    pxx_s = meq_pxx + T(0.5) * St_pxx;
+    pxy_s = meq_pxy + T(0.5) * St_pxy;
+  } else {
+    e_s = m_e - k.s_e * (m_e - meq_e) + k.h_e * St_e;
+    eps_s = m_eps - k.s_vs * (m_eps - meq_eps) + k.h_vs * St_eps;
+    jx_s = jx - k.s_j * (jx - rux) + k.h_j * Fx;
+    qx_s = m_qx - k.s_q * (m_qx + rux) - k.h_q * Fx;
+    jy_s = jy - k.s_j * (jy - ruy) + k.h_j * Fy;
+    qy_s = m_qy - k.s_q * (m_qy + ruy) - k.h_q * Fy;
+    pxx_s = m_pxx - k.s_nu * (m_pxx - meq_pxx) + k.h_nu * St_pxx;
+    pxy_s = m_pxy - k.s_nu * (m_pxy - meq_pxy) + k.h_nu * St_pxy;
+  }
   // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
   // (the rows of M are orthogonal)
   const T r9 = dr * T(1.0 / 9.0);
@@ -281,34 +307,39 @@ __device__ __forceinline__ void collide_node(const T (&g)[9], T psi_c, T Sx, T S
 template <typename T>
 __host__ __device__ constexpr int halo_of() { return int(16 / sizeof(T)); }
 
-template <typename T>
-__host__ __device__ size_t step_smem(int band_w) {
-  const size_t SW = size_t(band_w) + 2 * halo_of<T>();
-  size_t off = (size_t(kStages) * 9 * SW + 4 * (size_t(band_w) + 2)) * sizeof(T);
-  off = (off + 15) & ~size_t(15);
+template <typename T, int BW>
+__host__ __device__ constexpr size_t step_smem() {
+  constexpr int SW = BW + 2 * halo_of<T>();
+  constexpr size_t off = ((size_t(kStages) * 9 * SW + 4 * (size_t(BW) + 2)) * sizeof(T) + 15) & ~size_t(15);
   return off + kStages * sizeof(uint64_t) + 33 * sizeof(double);
 }
 
 // ---- the fused step (MODE_STEP) / moments export (MODE_MOMENTS)
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling tl, const PhysT<T> k, const StepIO io) {
+//
+// CTA b: x band (b % nbands) of width tl.band_w (<= BW), strip (b / nbands) of
+// tl.strip_h rows. Even strips walk their rows upward, odd strips downward, so two
+// neighbouring strips reach their common halo rows at the same time (L2 reuse).
+// Template parameters: real type, mode, all-unit relaxation, band width BW (nodes along
+// x per CTA), nodes per thread NPT (threads = BW / NPT), CTAs per SM the launch bounds
+// aim for.
+template <typename T, int MODE, bool UNIT, int BW, int NPT, int MINB>
+__global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling tl, const PhysT<T> k, const StepIO io) {
+  constexpr int NT = BW / NPT;
   constexpr int H = halo_of<T>();
+  constexpr int SW = BW + 2 * H;  // stage row: H halo, band, H halo
+  constexpr int RW = BW + 2;      // psi ring row: one halo node each side
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int BW = tl.band_w;
-  const int SW = BW + 2 * H;
-  const int RW = BW + 2;
   T* stage = reinterpret_cast<T*>(smem_raw);
   T* ring = stage + size_t(kStages) * 9 * SW;
-  size_t off = (size_t(kStages) * 9 * SW + 4 * size_t(RW)) * sizeof(T);
-  off = (off + 15) & ~size_t(15);
+  constexpr size_t off = ((size_t(kStages) * 9 * SW + 4 * size_t(RW)) * sizeof(T) + 15) & ~size_t(15);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + off);
   double* red = reinterpret_cast<double*>(smem_raw + off + kStages * sizeof(uint64_t));
 
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int nx = tl.nx, ny = tl.ny;
   const int band = blockIdx.x % tl.nbands, strip = blockIdx.x / tl.nbands;
-  const int xa = band * BW, xb = min(xa + BW, nx), w = xb - xa;
+  const int xa = band * tl.band_w, xb = min(xa + tl.band_w, nx), w = xb - xa;
   const int ya = strip * tl.strip_h, yb = min(ya + tl.strip_h, ny);
 
   // <rho> - rho_ref of Eq. Gravity_2: the previous step's partials, finished in a fixed order
@@ -328,11 +359,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
 
   const int r_lo = max(ya - 1, 0), r_hi = min(yb, ny - 1);
   const int nrows = r_hi - r_lo + 1;
+  const bool up = (strip & 1) == 0;
+  auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
   const T* fin = static_cast<const T*>(io.fin);
   T* fout = static_cast<T*>(io.fout);
+
+  // contiguous pieces of the periodic span [xa - H, xb + H): (global x, stage x, count)
+  // piece 0 starts at the left halo; interior bands need only it
+  int npc, g0, s0, n0, g1 = 0, s1 = 0, n1 = 0, g2 = 0, s2 = 0, n2 = 0;
+  if (xa >= H) {
+    g0 = xa - H; s0 = 0; n0 = w + H; npc = 1;
+  } else {
+    g0 = nx - H; s0 = 0; n0 = H;
+    g1 = xa;     s1 = H; n1 = w; npc = 2;
+  }
+  if (xb + H <= nx) {
+    if (npc == 1) n0 += H; else n1 += H;
+  } else if (npc == 1) {
+    g1 = 0; s1 = H + w; n1 = H; npc = 2;
+  } else {
+    g2 = 0; s2 = H + w; n2 = H; npc = 3;
+  }
   const uint32_t row_bytes = uint32_t(9 * (w + 2 * H) * sizeof(T));
-  const int xl = (xa >= H) ? xa - H : nx - H;   // left halo source (periodic)
-  const int xr = (xb + H <= nx) ? xb : 0;       // right halo source (periodic)
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
@@ -340,42 +388,49 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
   }
   __syncthreads();
 
-  // producer: row kk of the walk into stage kk % kStages
+  // producer (all lanes of warp 0): walk row kk into stage kk % kStages, one copy per lane
   auto issue = [&](int kk) {
-    const int r = r_lo + kk, s = kk % kStages;
-    mbar_expect_tx(&full[s], row_bytes);
-#pragma unroll 1
-    for (int i = 0; i < 9; ++i) {
-      int plane = i, row = r - cy_of(i);
+    const int q = row_of(kk), s = kk % kStages;
+    if (lane == 0) mbar_expect_tx(&full[s], row_bytes);
+    __syncwarp();
+    for (int c = lane; c < 9 * npc; c += 32) {
+      const int i = c / npc, pc = c - i * npc;
+      int plane = i, row = q - cy_of(i);
       if (row < 0 || row >= ny) {
         plane = opp_of(i);
-        row = r;
+        row = q;
       }
-      const T* src = fin + (size_t(plane) * ny + row) * size_t(nx);
-      T* dst = stage + (size_t(s) * 9 + i) * SW;
-      bulk_g2s(dst, src + xl, H * sizeof(T), &full[s]);
-      bulk_g2s(dst + H, src + xa, uint32_t(w * sizeof(T)), &full[s]);
-      bulk_g2s(dst + H + w, src + xr, H * sizeof(T), &full[s]);
+      const int gx = pc == 0 ? g0 : (pc == 1 ? g1 : g2);
+      const int sx = pc == 0 ? s0 : (pc == 1 ? s1 : s2);
+      const int cnt = pc == 0 ? n0 : (pc == 1 ? n1 : n2);
+      const T* src = fin + (size_t(plane) * ny + row) * size_t(nx) + gx;
+      T* dst = stage + (size_t(s) * 9 + i) * SW + sx;
+      bulk_g2s(dst, src, uint32_t(cnt * sizeof(T)), &full[s]);
     }
   };
-  int issued = 0;
-  if (tid == 0) {
+  int issued = 0;  // meaningful in warp 0
+  if (warp == 0) {
     for (; issued < min(kStages, nrows); ++issued) issue(issued);
   }
 
   int flag = 0;
   Acc<T> acc;
 
-  auto collide_row = [&](int y, int s) {
+  auto collide_row = [&](int y, int s, auto full_band) {
+    constexpr bool FULL = decltype(full_band)::value;  // w == BW: no per-node bounds checks
     const T* st = stage + size_t(s) * 9 * SW;
     const bool lo_wall = (y == 0), hi_wall = (y == ny - 1);
     const bool interior = !lo_wall && !hi_wall;
     const T* pc = ring + (y & 3) * RW;
     const T* pn = ring + ((y + 1) & 3) * RW;
     const T* ps = ring + ((y - 1) & 3) * RW;
-    for (int j = 1 + tid; j <= w; j += nthr) {
+    T* dst_row = fout + size_t(y) * nx + xa;
+#pragma unroll
+    for (int n = 0; n < NPT; ++n) {
+      const int j = 1 + tid + n * NT;  // node x = xa + j - 1
+      if (!FULL && j > w) continue;
       T g[9];
-      pull(st, SW, j - 1 + H, lo_wall, hi_wall, g);
+      pull<T, SW>(st, j - 1 + H, lo_wall, hi_wall, g);
       T Sx = T(0), Sy = T(0);
       if (interior) {  // Eq. ShanChenForce stencil: w(1) = 1/3, w(2) = 1/12
         const T E = pc[j + 1], Wt = pc[j - 1], N = pn[j], S = ps[j];
@@ -384,16 +439,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
         Sy = T(1.0 / 3.0) * (N - S) + T(1.0 / 12.0) * ((NE + NW) - (SE + SWt));
       }
       T o[9], rho, ux, uy;
-      collide_node<T>(g, pc[j], Sx, Sy, dmean, k, o, rho, ux, uy, flag);
-      const size_t x = size_t(xa + j - 1);
+      collide_node<T, UNIT>(g, pc[j], Sx, Sy, dmean, k, o, rho, ux, uy, flag);
       if (MODE == MODE_STEP) {
         const size_t plane = size_t(ny) * nx;
-        T* dst = fout + size_t(y) * nx + x;
+        T* dst = dst_row + (j - 1);
 #pragma unroll
         for (int i = 0; i < 9; ++i) dst[i * plane] = o[i];
         acc.add(sum9(o));
       } else {
-        const size_t idx = size_t(y) * nx + x;
+        const size_t idx = size_t(y) * nx + xa + (j - 1);
         if (io.rho_out) io.rho_out[idx] = double(rho);
         if (io.ux_out) io.ux_out[idx] = double(ux);
         if (io.uy_out) io.uy_out[idx] = double(uy);
@@ -404,15 +458,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
   bool failed = false;
   int kk = 0;
   for (; kk < nrows; ++kk) {
-    const int r = r_lo + kk, s = kk % kStages;
+    const int q = row_of(kk), s = kk % kStages;
     const bool ok = mbar_wait_bounded(&full[s], uint32_t((kk / kStages) & 1));
     if (ok) {
+      // rho and psi of pulled row q for the band and one halo node on each side
       const T* st = stage + size_t(s) * 9 * SW;
-      const bool lo_wall = (r == 0), hi_wall = (r == ny - 1);
-      T* pr = ring + (r & 3) * RW;
-      for (int j = tid; j < w + 2; j += nthr) {  // x = xa - 1 + j
+      const bool lo_wall = (q == 0), hi_wall = (q == ny - 1);
+      T* pr = ring + (q & 3) * RW;
+      auto psi_row = [&](auto full_band) {
+        constexpr bool FULL = decltype(full_band)::value;
+#pragma unroll
+        for (int n = 0; n < NPT; ++n) {
+          const int j = 1 + tid + n * NT;  // x = xa - 1 + j
+          if (FULL || j <= w) {
+            T g[9];
+            pull<T, SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+            pr[j] = psi_of<T>(k.rho_ref + sum9(g), k, flag);
+          }
+        }
+      };
+      if (w == BW)
+        psi_row(std::true_type{});
+      else
+        psi_row(std::false_type{});
+      if (warp == (NT / 32) - 1 && lane < 2) {  // the two halo nodes x = xa - 1 and x = xb
+        const int j = lane ? w + 1 : 0;
         T g[9];
-        pull(st, SW, j - 1 + H, lo_wall, hi_wall, g);
+        pull<T, SW>(st, j - 1 + H, lo_wall, hi_wall, g);
         pr[j] = psi_of<T>(k.rho_ref + sum9(g), k, flag);
       }
     }
@@ -420,8 +492,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
       failed = true;
       break;
     }
-    if (tid == 0 && kk >= 2 && issued < nrows) issue(issued++);
-    if (kk >= 1 && r - 1 >= ya) collide_row(r - 1, (kk - 1) % kStages);
+    // stage of walk row kk - 2 is free: every thread finished colliding it before the barrier
+    if (warp == 0 && kk >= 2 && issued < nrows) issue(issued++);
+    if (kk >= 1) {
+      const int y = row_of(kk - 1);
+      if (y >= ya && y < yb) {
+        if (w == BW)
+          collide_row(y, (kk - 1) % kStages, std::true_type{});
+        else
+          collide_row(y, (kk - 1) % kStages, std::false_type{});
+      }
+    }
   }
   if (failed) {
     if (tid == 0) {
@@ -432,7 +513,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
     }
     return;
   }
-  if (r_hi == yb - 1) collide_row(yb - 1, (nrows - 1) % kStages);  // top wall row (yb == ny)
+  {  // last walk row: own only at a wall (no halo row beyond it), psi neighbours not needed
+    const int y = row_of(nrows - 1);
+    if (y >= ya && y < yb) collide_row(y, (nrows - 1) % kStages, std::false_type{});
+  }
 
   if (__syncthreads_or(flag) && tid == 0) atomicOr(io.status, STATUS_NONPHYS);
   if (MODE == MODE_STEP) {
@@ -440,8 +524,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) step_kernel(const StepTiling t
     if (lane == 0) red[warp] = v;
     __syncthreads();
     if (warp == 0) {
-      const int nw = (nthr + 31) >> 5;
-      const double t = warp_sum(lane < nw ? red[lane] : 0.0);
+      const double t = warp_sum(lane < NT / 32 ? red[lane] : 0.0);
       if (lane == 0) io.part_out[blockIdx.x] = t;
     }
   }
@@ -566,13 +649,60 @@ __global__ void profile_scan_kernel(const double* prof, int ny, double level, do
   out[2] = mn;
 }
 
-template <typename T>
-cudaError_t prepare_t() {
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<T, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(step_kernel<T, MODE_MOMENTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+// ---- tile variants of the fused kernel: (real, band width, nodes per thread, CTAs/SM).
+// Variant 0 of each precision is the default; lbm_autotune times the others.
+using StepFnF = void (*)(StepTiling, PhysT<float>, StepIO);
+using StepFnD = void (*)(StepTiling, PhysT<double>, StepIO);
+
+struct VariantF {
+  int bw, npt;
+  StepFnF step, step_unit, moments;
+  size_t smem;
+};
+struct VariantD {
+  int bw, npt;
+  StepFnD step, step_unit, moments;
+  size_t smem;
+};
+
+template <int BW, int NPT, int MINB>
+constexpr VariantF make_f() {
+  return VariantF{BW, NPT, step_kernel<float, MODE_STEP, false, BW, NPT, MINB>,
+                  step_kernel<float, MODE_STEP, true, BW, NPT, MINB>,
+                  step_kernel<float, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<float, BW>()};
+}
+template <int BW, int NPT, int MINB>
+constexpr VariantD make_d() {
+  return VariantD{BW, NPT, step_kernel<double, MODE_STEP, false, BW, NPT, MINB>,
+                  step_kernel<double, MODE_STEP, true, BW, NPT, MINB>,
+                  step_kernel<double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
+}
+
+const VariantF kVariantsF[] = {
+    make_f<256, 2, 5>(),  // 4 warps, 42 KB shared
+    make_f<128, 1, 6>(),  // 4 warps, 22 KB shared
+    make_f<256, 1, 3>(),  // 8 warps, 42 KB shared
+    make_f<512, 4, 2>(),  // 4 warps, 83 KB shared
+    make_f<128, 2, 8>(),  // 2 warps, 22 KB shared
+};
+const VariantD kVariantsD[] = {
+    make_d<128, 1, 4>(),
+    make_d<64, 1, 8>(),
+};
+constexpr int kNumF = sizeof(kVariantsF) / sizeof(kVariantsF[0]);
+constexpr int kNumD = sizeof(kVariantsD) / sizeof(kVariantsD[0]);
+
+template <class V>
+cudaError_t prepare_variant(const V& v) {
+  for (auto fn : {(const void*)v.step, (const void*)v.step_unit, (const void*)v.moments}) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(v.smem));
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool unit_relaxation(const StepPhys& p) {
+  return p.s_e == 1.0 && p.s_vs == 1.0 && p.s_j == 1.0 && p.s_q == 1.0 && p.s_nu == 1.0;
 }
 
 int grid_for(size_t n, int block) {
@@ -587,38 +717,57 @@ int grid_for(size_t n, int block) {
 // ---------------------------------------------------------------- launch wrappers
 int stages() { return kStages; }
 
-size_t step_smem_bytes(int precision, int band_w, int /*threads*/) {
-  return precision == 1 ? step_smem<float>(band_w) : step_smem<double>(band_w);
+int step_num_variants(int precision) { return precision == 1 ? kNumF : kNumD; }
+
+bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem) {
+  if (variant < 0 || variant >= step_num_variants(precision)) return false;
+  int bw, npt;
+  size_t sm;
+  if (precision == 1) {
+    bw = kVariantsF[variant].bw; npt = kVariantsF[variant].npt; sm = kVariantsF[variant].smem;
+  } else {
+    bw = kVariantsD[variant].bw; npt = kVariantsD[variant].npt; sm = kVariantsD[variant].smem;
+  }
+  *band_w = bw;
+  *threads = bw / npt;
+  *smem = int(sm);
+  return true;
 }
 
-int step_max_ctas_per_sm(int precision, int mode, int threads, int smem_bytes) {
+int step_max_ctas_per_sm(int precision, int variant, int threads, int smem_bytes) {
+  const void* fn = precision == 1 ? (const void*)kVariantsF[variant].step : (const void*)kVariantsD[variant].step;
   int n = 0;
-  const void* fn = nullptr;
-  if (precision == 1)
-    fn = mode == MODE_STEP ? (const void*)step_kernel<float, MODE_STEP> : (const void*)step_kernel<float, MODE_MOMENTS>;
-  else
-    fn = mode == MODE_STEP ? (const void*)step_kernel<double, MODE_STEP> : (const void*)step_kernel<double, MODE_MOMENTS>;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem_bytes) != cudaSuccess) return 0;
   return n;
 }
 
-cudaError_t step_prepare(int precision) { return precision == 1 ? prepare_t<float>() : prepare_t<double>(); }
+cudaError_t step_prepare(int precision) {
+  if (precision == 1) {
+    for (const auto& v : kVariantsF) {
+      cudaError_t e = prepare_variant(v);
+      if (e != cudaSuccess) return e;
+    }
+  } else {
+    for (const auto& v : kVariantsD) {
+      cudaError_t e = prepare_variant(v);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_step(int precision, int mode, const StepTiling& t, const StepPhys& ph, const StepIO& io,
                         cudaStream_t stream) {
   const dim3 grid(t.nbands * t.nstrips), block(t.threads);
+  const bool unit = unit_relaxation(ph);
   if (precision == 1) {
-    const PhysT<float> k = to_phys<float>(ph);
-    if (mode == MODE_STEP)
-      step_kernel<float, MODE_STEP><<<grid, block, t.smem_bytes, stream>>>(t, k, io);
-    else
-      step_kernel<float, MODE_MOMENTS><<<grid, block, t.smem_bytes, stream>>>(t, k, io);
+    const VariantF& v = kVariantsF[t.variant];
+    const StepFnF fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
+    fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<float>(ph), io);
   } else {
-    const PhysT<double> k = to_phys<double>(ph);
-    if (mode == MODE_STEP)
-      step_kernel<double, MODE_STEP><<<grid, block, t.smem_bytes, stream>>>(t, k, io);
-    else
-      step_kernel<double, MODE_MOMENTS><<<grid, block, t.smem_bytes, stream>>>(t, k, io);
+    const VariantD& v = kVariantsD[t.variant];
+    const StepFnD fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
+    fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<double>(ph), io);
   }
   return cudaGetLastError();
 }

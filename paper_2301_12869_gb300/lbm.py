@@ -38,6 +38,7 @@ EXPORTS = (
     "lbm_params_default", "lbm_workspace_bytes", "lbm_init", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
     "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
+    "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling",
 )
 
 
@@ -90,6 +91,9 @@ def load(path: str = LIB_PATH):
         "lbm_coexistence": (i32, [d, d, d, d, P(d), P(d), P(d)]),
         "lbm_launch_info": (i32, [vp, P(i32), P(i32), P(i32), P(i32), P(i32), P(i32)]),
         "lbm_step_noalloc": (i32, [P(lbm_params), vp, vp, vp]),
+        "lbm_autotune": (i32, [vp, i32, P(i32), P(d)]),
+        "lbm_tile_variants": (i32, [i32]),
+        "lbm_set_tiling": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +214,25 @@ def lbm_launch_info(h):
     _check(load().lbm_launch_info(h, *[ctypes.byref(v) for v in vals]), h)
     keys = ("grid", "block", "smem_bytes", "band_width", "strip_rows", "stages")
     return {k: v.value for k, v in zip(keys, vals)}
+
+
+def lbm_autotune(h, steps=20):
+    """Times the fused kernel's tile variants on this lattice and keeps the fastest;
+    returns (variant, ms per step)."""
+    v, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load().lbm_autotune(h, int(steps), ctypes.byref(v), ctypes.byref(ms)), h)
+    return v.value, ms.value
+
+
+def lbm_tile_variants(precision):
+    n = load().lbm_tile_variants(int(precision))
+    if n < 0:
+        _check(n)
+    return n
+
+
+def lbm_set_tiling(h, variant):
+    _check(load().lbm_set_tiling(h, int(variant)), h)
 
 
 def lbm_step_noalloc(p, f_in, f_out, stream=None):

@@ -346,3 +346,41 @@ def test_full_size_large_domain_sampled(precision, tol):
         assert lbm.lbm_status(h) == lbm.LBM_OK
     finally:
         lbm.lbm_destroy(h)
+
+
+# ---------------------------------------------------------------- tile variants and autotune
+@pytest.mark.parametrize("precision, nx, ny, tol", [("fp32", 1028, 150, 2e-6), ("fp64", 1040, 150, 1e-14)])
+def test_every_tile_variant_matches_oracle(precision, nx, ny, tol):
+    """Each tile variant of the fused kernel (band width x threads) on a lattice with a
+    ragged last band, general MRT relaxation and then all-unit relaxation."""
+    for extra in (MRT, {}):
+        p = params(nx, ny, 0.8, precision, form=2, g=(1e-5, -1e-4), **extra)
+        op = oracle_params(p)
+        rho0 = column(p, 0.8, noise=1e-3)
+        f0 = None
+        for v in range(lbm.lbm_tile_variants(p.precision)):
+            h = lbm.lbm_init(p, rho0)
+            try:
+                lbm.lbm_set_tiling(h, v)
+                if f0 is None:
+                    f0 = state(h, p)
+                    want = olbm.run(f0, op, 2)
+                lbm.lbm_step(h, 2)
+                assert np.max(np.abs(state(h, p) - want)) <= tol, (v, extra)
+            finally:
+                lbm.lbm_destroy(h)
+
+
+def test_autotune_keeps_state_and_picks_a_variant():
+    p = params(1024, 256, 0.8, "fp32", form=2, g=(0.0, -1e-4))
+    h = lbm.lbm_init(p, column(p, 0.8, noise=1e-3))
+    try:
+        lbm.lbm_step(h, 3)
+        before = state(h, p)
+        v, ms = lbm.lbm_autotune(h, 5)
+        assert 0 <= v < lbm.lbm_tile_variants(p.precision) and ms > 0
+        np.testing.assert_array_equal(state(h, p), before)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_tiling(h, 99)
+    finally:
+        lbm.lbm_destroy(h)
