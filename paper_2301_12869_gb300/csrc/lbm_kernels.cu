@@ -606,6 +606,236 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   }
 }
 
+// ---- the fused step without CTA barriers in the row loop (FP32 node pairs)
+//
+// NWC consumer warps each own 64 nodes of the band (32 lanes x one pair) and walk the
+// strip's rows on their own: psi of the three rows around the collided row stays in
+// registers, x-neighbours come from the adjacent lanes by shuffles, and only the lanes at
+// a warp's edges evaluate one extra psi value from the stage (which holds the whole band
+// plus halos). One producer warp refills a stage once every consumer warp has arrived on
+// that stage's `empty` mbarrier. Template: mode, all-unit relaxation, consumer warps,
+// stages, CTAs per SM the launch bounds aim for.
+template <int NWC, int S>
+__host__ __device__ constexpr size_t ws_smem() {
+  constexpr int SW = 64 * NWC + 8;
+  constexpr size_t off = (size_t(S) * 9 * SW * sizeof(float) + 15) & ~size_t(15);
+  return off + 2 * S * sizeof(uint64_t) + (NWC + 2) * sizeof(double);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct PsiRow {  // psi at the left neighbour, the lane's own pair, the right neighbour
+  float l;
+  f2 c;
+  float r;
+};
+
+template <int MODE, bool UNIT, int NWC, int S, int MINB>
+__global__ void __launch_bounds__((NWC + 1) * 32, MINB)
+    step_kernel_ws(const StepTiling tl, const PhysT<f2> k, const StepIO io) {
+  using T = float;
+  using V = f2;
+  constexpr int BW = 64 * NWC;
+  constexpr int H = 4;
+  constexpr int SW = BW + 2 * H;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* stage = reinterpret_cast<float*>(smem_raw);
+  constexpr size_t off = (size_t(S) * 9 * SW * sizeof(float) + 15) & ~size_t(15);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + off);
+  uint64_t* empty = full + S;
+  double* red = reinterpret_cast<double*>(empty + S);
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int nx = tl.nx, ny = tl.ny;
+  const int band = blockIdx.x % tl.nbands, strip = blockIdx.x / tl.nbands;
+  const int xa = band * tl.band_w, xb = min(xa + tl.band_w, nx), w = xb - xa;
+  const int ya = strip * tl.strip_h, yb = min(ya + tl.strip_h, ny);
+
+  V dmean = cst<V>(0.0);
+  if (k.form == 2) {
+    if (warp == 0) {
+      const double s = warp_sum_partials(io.part_in, io.npart_in);
+      if (lane == 0) red[NWC + 1] = s;
+    }
+    __syncthreads();
+    dmean = cst<V>(red[NWC + 1] / (double(nx) * double(ny)));
+  }
+  if (ya >= yb || w <= 0) {
+    if (MODE == MODE_STEP && tid == 0) io.part_out[blockIdx.x] = 0.0;
+    return;
+  }
+
+  const int r_lo = max(ya - 1, 0), r_hi = min(yb, ny - 1);
+  const int nrows = r_hi - r_lo + 1;
+  const bool up = (strip & 1) == 0;
+  auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
+  const T* fin = static_cast<const T*>(io.fin);
+  T* fout = static_cast<T*>(io.fout);
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NWC);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  int flag = 0;
+  if (warp == NWC) {
+    // ---------------- producer warp
+    int npc, g0, s0, n0, g1 = 0, s1 = 0, n1 = 0, g2 = 0, s2 = 0, n2 = 0;
+    if (xa >= H) {
+      g0 = xa - H; s0 = 0; n0 = w + H; npc = 1;
+    } else {
+      g0 = nx - H; s0 = 0; n0 = H;
+      g1 = xa;     s1 = H; n1 = w; npc = 2;
+    }
+    if (xb + H <= nx) {
+      if (npc == 1) n0 += H; else n1 += H;
+    } else if (npc == 1) {
+      g1 = 0; s1 = H + w; n1 = H; npc = 2;
+    } else {
+      g2 = 0; s2 = H + w; n2 = H; npc = 3;
+    }
+    const uint32_t row_bytes = uint32_t(9 * (w + 2 * H) * sizeof(T));
+    int kk = 0;
+    for (; kk < nrows; ++kk) {
+      const int s = kk % S;
+      // the stage's previous row (kk - S) must be released by every consumer warp
+      if (kk >= S && !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], uint32_t(((kk / S) - 1) & 1)))) {
+        flag |= STATUS_TIMEOUT;
+        break;
+      }
+      const int q = row_of(kk);
+      if (lane == 0) mbar_expect_tx(&full[s], row_bytes);
+      __syncwarp();
+      for (int c = lane; c < 9 * npc; c += 32) {
+        const int i = c / npc, pc = c - i * npc;
+        int plane = i, row = q - cy_of(i);
+        if (row < 0 || row >= ny) {
+          plane = opp_of(i);
+          row = q;
+        }
+        const int gx = pc == 0 ? g0 : (pc == 1 ? g1 : g2);
+        const int sx = pc == 0 ? s0 : (pc == 1 ? s1 : s2);
+        const int cnt = pc == 0 ? n0 : (pc == 1 ? n1 : n2);
+        const T* src = fin + (size_t(plane) * ny + row) * size_t(nx) + gx;
+        T* dst = stage + (size_t(s) * 9 + i) * SW + sx;
+        bulk_g2s(dst, src, uint32_t(cnt * sizeof(T)), &full[s]);
+      }
+    }
+    if (flag && lane == 0) {
+      // let the copies in flight land before the CTA's shared memory is released
+      for (int q = max(0, kk - S); q < kk; ++q)
+        (void)mbar_wait_bounded(&full[q % S], uint32_t((q / S) & 1), kWaitCycles / 8);
+    }
+  } else {
+    // ---------------- consumer warp: nodes j, j+1 of the band (x = xa + j - 1)
+    const int j = 1 + 64 * warp + 2 * lane;
+    const bool active = j <= w;  // w is a multiple of 4, so j + 1 <= w too
+    const bool need_l = active && lane == 0;
+    const bool need_r = active && (lane == 31 || j + 2 > w);
+    Acc<V> acc;
+    PsiRow pm{0.f, cst<V>(0.0), 0.f}, p0 = pm, pp = pm;  // rows kk-2, kk-1, kk of the walk
+    const V c13 = cst<V>(1.0 / 3.0), c112 = cst<V>(1.0 / 12.0);
+
+    auto scalar_psi = [&](const T* st, int jh, bool lo_wall, bool hi_wall) {
+      T g[9];
+      pull<SW>(st, jh - 1 + H, lo_wall, hi_wall, g);
+      const T rh = sum9(g);
+      return lo(psi_of<V>(k.rho_ref + make_f2(rh, rh), k, flag));
+    };
+    auto collide = [&](int y, int s, const PsiRow& ps, const PsiRow& pc, const PsiRow& pn) {
+      const T* st = stage + size_t(s) * 9 * SW;
+      const bool lo_wall = (y == 0), hi_wall = (y == ny - 1);
+      V g[9];
+      pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+      V Sx = cst<V>(0.0), Sy = cst<V>(0.0);
+      if (!lo_wall && !hi_wall) {  // Eq. ShanChenForce stencil: w(1) = 1/3, w(2) = 1/12
+        // per row: west (psi(j-1), psi(j)), east (psi(j+1), psi(j+2)), centre (psi(j), psi(j+1))
+        const V Wc = make_f2(pc.l, lo(pc.c)), Ec = make_f2(hi(pc.c), pc.r);
+        const V Wn = make_f2(pn.l, lo(pn.c)), En = make_f2(hi(pn.c), pn.r);
+        const V Ws = make_f2(ps.l, lo(ps.c)), Es = make_f2(hi(ps.c), ps.r);
+        Sx = fmadd(c13, Ec - Wc, c112 * ((En - Wn) + (Es - Ws)));
+        Sy = fmadd(c13, pn.c - ps.c, c112 * ((En + Wn) - (Es + Ws)));
+      }
+      V o[9], rho, ux, uy;
+      collide_node<V, UNIT>(g, pc.c, Sx, Sy, dmean, k, o, rho, ux, uy, flag);
+      const size_t node = size_t(y) * nx + xa + (j - 1);
+      if (MODE == MODE_STEP) {
+        const size_t plane = size_t(ny) * nx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) *reinterpret_cast<V*>(fout + node + i * plane) = o[i];
+        acc.add(sum9(o));
+      } else {
+        if (io.rho_out) { io.rho_out[node] = lo(rho); io.rho_out[node + 1] = hi(rho); }
+        if (io.ux_out) { io.ux_out[node] = lo(ux); io.ux_out[node + 1] = hi(ux); }
+        if (io.uy_out) { io.uy_out[node] = lo(uy); io.uy_out[node + 1] = hi(uy); }
+      }
+    };
+
+    bool failed = false;
+    for (int kk = 0; kk < nrows; ++kk) {
+      const int q = row_of(kk), s = kk % S;
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], uint32_t((kk / S) & 1)))) {
+        flag |= STATUS_TIMEOUT;
+        failed = true;
+        break;
+      }
+      const T* st = stage + size_t(s) * 9 * SW;
+      const bool lo_wall = (q == 0), hi_wall = (q == ny - 1);
+      PsiRow nw;
+      nw.c = cst<V>(0.0);
+      if (active) {
+        V g[9];
+        pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+        nw.c = psi_of<V>(k.rho_ref + sum9(g), k, flag);
+      }
+      nw.l = __shfl_up_sync(0xffffffffu, hi(nw.c), 1);
+      nw.r = __shfl_down_sync(0xffffffffu, lo(nw.c), 1);
+      if (need_l || need_r) {  // warp-edge lanes: a neighbour another warp (or the halo) owns
+        const float v = scalar_psi(st, need_l ? j - 1 : j + 2, lo_wall, hi_wall);
+        if (need_l) nw.l = v; else nw.r = v;
+        if (need_l && need_r) nw.r = scalar_psi(st, j + 2, lo_wall, hi_wall);
+      }
+      pm = p0;
+      p0 = pp;
+      pp = nw;
+      if (kk >= 1) {
+        const int y = row_of(kk - 1);
+        if (active && y >= ya && y < yb) {
+          // walk rows kk-2 / kk are south / north of y when walking up, and the reverse down
+          if (up)
+            collide(y, (kk - 1) % S, pm, p0, pp);
+          else
+            collide(y, (kk - 1) % S, pp, p0, pm);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[(kk - 1) % S]);  // this warp is done with row kk-1
+      }
+    }
+    if (!failed) {  // last walk row: own only at a wall, where the stencil is not needed
+      const int y = row_of(nrows - 1);
+      if (active && y >= ya && y < yb) collide(y, (nrows - 1) % S, pp, pp, pp);
+    }
+    if (MODE == MODE_STEP) {
+      const double v = warp_sum(acc.value());
+      if (lane == 0) red[warp] = v;
+    }
+  }
+
+  if (__syncthreads_or(flag & STATUS_NONPHYS) && tid == 0) atomicOr(io.status, STATUS_NONPHYS);
+  if (__syncthreads_or(flag & STATUS_TIMEOUT) && tid == 0) atomicOr(io.status, STATUS_TIMEOUT);
+  if (MODE == MODE_STEP && warp == 0) {
+    const double t = warp_sum(lane < NWC ? red[lane] : 0.0);
+    if (lane == 0) io.part_out[blockIdx.x] = t;
+  }
+}
+
 // ---- initial state g_i = f_i^eq(rho0, 0) - w_i rho_ref = w_i (rho0 - rho_ref)
 template <typename T>
 __global__ void init_kernel(const double* __restrict__ rho0, T* __restrict__ f, int nx, int ny, double rho_ref) {
@@ -732,21 +962,21 @@ using StepFnP = void (*)(StepTiling, PhysT<f2>, StepIO);
 using StepFnD = void (*)(StepTiling, PhysT<double>, StepIO);
 
 struct VariantF {  // FP32 storage; `paired` variants evaluate two nodes per value
-  int bw, npt;
+  int bw, threads;
   bool paired;
   StepFnF step, step_unit, moments;      // scalar variants
   StepFnP pstep, pstep_unit, pmoments;   // paired variants
   size_t smem;
 };
 struct VariantD {
-  int bw, npt;
+  int bw, threads;
   StepFnD step, step_unit, moments;
   size_t smem;
 };
 
 template <int BW, int NPT, int MINB>
 constexpr VariantF make_f() {
-  return VariantF{BW, NPT, false,
+  return VariantF{BW, BW / NPT, false,
                   step_kernel<float, float, MODE_STEP, false, BW, NPT, MINB>,
                   step_kernel<float, float, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<float, float, MODE_MOMENTS, false, BW, NPT, MINB>,
@@ -754,24 +984,33 @@ constexpr VariantF make_f() {
 }
 template <int BW, int NPT, int MINB>
 constexpr VariantF make_p() {
-  return VariantF{BW, NPT, true, nullptr, nullptr, nullptr,
+  return VariantF{BW, BW / NPT, true, nullptr, nullptr, nullptr,
                   step_kernel<float, f2, MODE_STEP, false, BW, NPT, MINB>,
                   step_kernel<float, f2, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<float, f2, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<float, BW>()};
 }
 template <int BW, int NPT, int MINB>
 constexpr VariantD make_d() {
-  return VariantD{BW, NPT, step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB>,
+  return VariantD{BW, BW / NPT, step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB>,
                   step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
 }
 
+template <int NWC, int S, int MINB>
+constexpr VariantF make_ws() {
+  return VariantF{64 * NWC, (NWC + 1) * 32, true, nullptr, nullptr, nullptr,
+                  step_kernel_ws<MODE_STEP, false, NWC, S, MINB>, step_kernel_ws<MODE_STEP, true, NWC, S, MINB>,
+                  step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB>, ws_smem<NWC, S>()};
+}
+
 const VariantF kVariantsF[] = {
-    make_p<256, 2, 5>(),  // pairs, 4 warps, 42 KB shared
-    make_f<256, 2, 5>(),  // scalar, 4 warps, 42 KB shared
-    make_p<512, 4, 2>(),  // pairs x2, 4 warps, 83 KB shared
-    make_p<128, 2, 8>(),  // pairs, 2 warps, 22 KB shared
-    make_p<512, 2, 2>(),  // pairs, 8 warps, 83 KB shared
+    make_ws<8, 4, 2>(),      // barrier-free: 8 consumer warps + producer, 4 stages, 75 KB
+    make_ws<4, 4, 4>(),      // barrier-free: 4 consumer warps + producer, 4 stages, 38 KB
+    make_p<256, 2, 5>(),     // pairs, 4 warps, 42 KB shared, one CTA barrier per row
+    make_f<256, 2, 5>(),     // scalar, 4 warps, 42 KB shared, one CTA barrier per row
+    make_p<512, 4, 2>(),     // two pairs per thread, 4 warps, 83 KB shared
+    make_ws<4, 6, 3>(),      // barrier-free, 6 stages, 57 KB
+    make_ws<2, 6, 6>(),      // barrier-free, 2 consumer warps, 29 KB
 };
 const VariantD kVariantsD[] = {
     make_d<128, 1, 4>(),
@@ -820,16 +1059,11 @@ int step_num_variants(int precision) { return precision == 1 ? kNumF : kNumD; }
 
 bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem) {
   if (variant < 0 || variant >= step_num_variants(precision)) return false;
-  int bw, npt;
-  size_t sm;
   if (precision == 1) {
-    bw = kVariantsF[variant].bw; npt = kVariantsF[variant].npt; sm = kVariantsF[variant].smem;
+    *band_w = kVariantsF[variant].bw; *threads = kVariantsF[variant].threads; *smem = int(kVariantsF[variant].smem);
   } else {
-    bw = kVariantsD[variant].bw; npt = kVariantsD[variant].npt; sm = kVariantsD[variant].smem;
+    *band_w = kVariantsD[variant].bw; *threads = kVariantsD[variant].threads; *smem = int(kVariantsD[variant].smem);
   }
-  *band_w = bw;
-  *threads = bw / npt;
-  *smem = int(sm);
   return true;
 }
 
