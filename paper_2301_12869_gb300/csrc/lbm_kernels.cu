@@ -847,21 +847,23 @@ __global__ void init_kernel(const double* __restrict__ rho0, T* __restrict__ f, 
   }
 }
 
-// ---- FP64 partial sums of sum_i g_i: block b covers nodes [b*chunk, (b+1)*chunk)
+// ---- FP64 partial sums of sum_i g_i: block b covers nodes [b*chunk, (b+1)*chunk).
+// FP32 storage: node sums in FP32, accumulated per thread with the two-sum pair (the
+// FP64 pipe of GB300 is slow); FP64 storage: plain FP64 sums.
 template <typename T>
 __global__ void partials_kernel(const T* __restrict__ f, int nx, int ny, double* __restrict__ part) {
   __shared__ double red[32];
   const size_t n = size_t(nx) * ny;
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t q0 = blockIdx.x * chunk, q1 = min(n, q0 + chunk);
-  double s = 0.0;
+  Acc<T> acc;
   for (size_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-    double node = 0.0;
+    T g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) node += double(f[i * n + q]);
-    s += node;
+    for (int i = 0; i < 9; ++i) g[i] = f[i * n + q];
+    acc.add(sum9(g));
   }
-  s = warp_sum(s);
+  const double s = warp_sum(acc.value());
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x < 32) {
