@@ -160,6 +160,60 @@ int lbm_tile_variants(int precision);
  * result of lbm_autotune saved from an earlier run. LBM_EINVAL if out of range. */
 int lbm_set_tiling(lbm_handle* h, int variant);
 
+/* ---- batched independent columns: the 1-D liquid-column problem of Sec. IV for many
+ * parameter sets at once, in one persistent launch
+ *
+ * A batch holds ncols independent lattices nx x ny_c (periodic x, walls at both ends) that
+ * share nx, the precision, the EOS constants a, b, R, G, sigma and the relaxation times of
+ * `p`, and differ in height, temperature, gravity and gravity form. */
+typedef struct lbm_column {
+  int32_t ny;            /* rows */
+  int32_t gravity_form;  /* LBM_GRAVITY_RHO_G or LBM_GRAVITY_RHO_MINUS_MEAN_G */
+  double T;              /* temperature */
+  double gx, gy;         /* gravity */
+} lbm_column;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->ny, p->T, p->gx,
+ * p->gy, p->gravity_form and p->workspace are ignored; p->rho_ref NaN means: each column's
+ * mean rho0 in FP32, 0 in FP64). cols: ncols descriptors (host). rho0: the columns' initial
+ * densities concatenated, column c holding nx * ny_c doubles [y][x], in host or device
+ * memory per rho0_where; the state is the rest equilibrium f_i^eq(rho0, 0). Each column
+ * needs 2 nx ny_c sizeof(real) <= 200 KiB. stream: a cudaStream_t or NULL (the batch then
+ * uses a private non-blocking stream). The library allocates the device memory.
+ * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const double* rho0, int rho0_where,
+                   void* stream, lbm_batch** out);
+
+/* Advance every column until its residual max_x |rho_t(x) - rho_(t-1)(x)|, evaluated every
+ * check_every (>= 2) steps, is <= tol, or until it has taken max_steps more steps. One
+ * persistent launch over all columns (each CTA takes the tallest remaining column), issued
+ * as a CUDA graph captured at the first run. Synchronises; seconds (may be NULL) receives
+ * the device time of the launch. Per-column non-physical states are reported by
+ * lbm_batch_results. */
+int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, double* seconds);
+
+/* Per column (host arrays of ncols, any may be NULL): total steps taken, last residual
+ * (+inf before the first check), status (LBM_OK or LBM_ENONPHYS). Returns LBM_ENONPHYS if
+ * any column is non-physical. Synchronises. */
+int lbm_batch_results(const lbm_batch* b, int64_t* steps, double* residual, int* status);
+
+/* rho and u of every column as the next step evaluates them, concatenated like rho0, in
+ * host or device memory per `where` (any pointer may be NULL). Synchronises. */
+int lbm_batch_moments(lbm_batch* b, double* rho, double* ux, double* uy, int where);
+
+/* Absolute populations of every column, concatenated [col][i][y][x] (9 nx ny_c doubles per
+ * column), host or device. Synchronises. */
+int lbm_batch_get_state(lbm_batch* b, double* f, int where);
+
+/* A new batch with src's columns and current state in another precision (e.g. an FP32 run
+ * continued in FP64 below the FP32 rounding floor); step counts carry over. */
+int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out);
+
+/* Release a batch. NULL is accepted. */
+int lbm_batch_destroy(lbm_batch* b);
+
 /* ---- one step without device allocation (this entry point has no counterpart in the paper)
  *
  * Some callers cannot call cudaMalloc: a host loop that must not stall other streams on

@@ -1,0 +1,661 @@
+// Batched independent columns: one persistent launch advances thousands of small
+// nx x ny_c lattices (each with its own height, temperature, gravity and gravity form)
+// to a residual target. Method per column: the same step as lbm_kernels.cu (arXiv
+// 2301.12869, Sec. III), evaluated by lbm_physics.cuh.
+//
+// Design: a CTA takes one column at a time by atomic work stealing (tallest first) and
+// iterates it to convergence. The column's two population buffers stay in global memory
+// - with a few hundred columns in flight the working set is L2-resident on GB300 - while
+// psi, the residual snapshot and the partial sums live in shared memory. A step is two
+// phases over all nodes of the column with one CTA barrier after each: (A) pull, rho and
+// psi; (B) pull, Shan-Chen stencil, collision, store, and a CTA-wide FP64 reduction of
+// the stored mass that gives the next step's <rho> (Eq. Gravity_2). Every `check_every`
+// steps the residual max |rho_t - rho_(t-1)| decides whether the column has converged.
+// The launch (counter reset + kernel) is captured once per batch into a CUDA graph; the
+// run parameters live in device memory so the graph is reused by every run.
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_physics.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct BatchCol {
+  int ny, form;
+  long long node_off;  // nodes of the columns before this one
+  double RT, gx, gy, rho_ref;
+};
+
+struct RunParams {
+  double tol;
+  long long max_steps;
+  int check_every;
+};
+
+struct BatchArgs {
+  const BatchCol* cols;
+  const int* order;  // processing order (tallest first)
+  int ncols, nx;
+  void* fA;  // state of every column (concatenated [col][9][ny][nx]); always holds the state between runs
+  void* fB;  // second buffer of the same layout
+  double a, b, G, sig_e, sig_vs, s_e, s_vs, s_j, s_q, s_nu;
+  const RunParams* run;
+  int* counter;
+  long long* steps;
+  double* resid;
+  int* status;
+  double* rho_out;  // MODE_MOMENTS outputs, concatenated like rho0
+  double* ux_out;
+  double* uy_out;
+};
+
+template <typename T>
+__device__ lbm::PhysT<T> column_phys(const BatchArgs& a, const BatchCol& c) {
+  lbm::PhysT<T> k;
+  k.rho_ref = T(c.rho_ref);
+  k.RT = T(c.RT);
+  k.a = T(a.a);
+  k.b4 = T(a.b / 4.0);
+  k.twoOverG = T(2.0 / a.G);
+  k.negG = T(-a.G);
+  k.G2 = T(a.G * a.G);
+  k.s_e = T(a.s_e); k.s_vs = T(a.s_vs); k.s_j = T(a.s_j); k.s_q = T(a.s_q); k.s_nu = T(a.s_nu);
+  k.h_e = T(1.0 - 0.5 * a.s_e); k.h_vs = T(1.0 - 0.5 * a.s_vs); k.h_j = T(1.0 - 0.5 * a.s_j);
+  k.h_q = T(1.0 - 0.5 * a.s_q); k.h_nu = T(1.0 - 0.5 * a.s_nu);
+  k.sig_e = T(a.sig_e);
+  k.nsig_vs = T(-a.sig_vs);
+  k.gx = T(c.gx);
+  k.gy = T(c.gy);
+  k.form = c.form;
+  return k;
+}
+
+// pull streaming (Eq. LBE) of node (x, y) of a column: f_i(x, y) = f*_i(x - c_ix, y - c_iy),
+// x periodic; at the walls the opposite population of the same node (halfway bounce-back)
+template <typename T>
+__device__ __forceinline__ void pull_col(const T* f, int nx, int ny, int N, int x, int y, T (&g)[9]) {
+  const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+  const int node = y * nx + x;
+  const bool lo = (y == 0), hi = (y == ny - 1);
+  g[0] = f[0 * N + node];
+  g[1] = f[1 * N + y * nx + xl];
+  g[3] = f[3 * N + y * nx + xr];
+  g[2] = lo ? f[4 * N + node] : f[2 * N + (y - 1) * nx + x];
+  g[5] = lo ? f[7 * N + node] : f[5 * N + (y - 1) * nx + xl];
+  g[6] = lo ? f[8 * N + node] : f[6 * N + (y - 1) * nx + xr];
+  g[4] = hi ? f[2 * N + node] : f[4 * N + (y + 1) * nx + x];
+  g[7] = hi ? f[5 * N + node] : f[7 * N + (y + 1) * nx + xr];
+  g[8] = hi ? f[6 * N + node] : f[8 * N + (y + 1) * nx + xl];
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+
+template <typename T, int MODE, bool UNIT>
+__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ double red[2][kWarps];  // mass partials of the state each iteration reads
+  __shared__ double rmax[kWarps];
+  __shared__ int s_col;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const RunParams run = *a.run;
+  const int K = run.check_every;
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_col = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int ci = s_col;
+    if (ci >= a.ncols) break;
+    const int c = a.order[ci];
+    const BatchCol col = a.cols[c];
+    const int nx = a.nx, ny = col.ny, N = nx * ny;
+    T* psi_s = reinterpret_cast<T*>(sm_raw);
+    T* rho_prev = psi_s + N;
+    const lbm::PhysT<T> k = column_phys<T>(a, col);
+    T* cur = static_cast<T*>(a.fA) + 9 * col.node_off;
+    T* nxt = static_cast<T*>(a.fB) + 9 * col.node_off;
+
+    {  // mass of the stored state, for <rho> of the first step
+      lbm::Acc<T> acc;
+      for (int n = tid; n < N; n += kThreads) {
+        T g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = cur[i * N + n];
+        acc.add9(g);
+      }
+      const double v = lbm::warp_sum(acc.value());
+      if (lane == 0) red[0][warp] = v;
+    }
+    __syncthreads();
+
+    int flag = 0;
+    double res = MODE == lbm::MODE_STEP ? a.resid[c] : 0.0;
+    long long it = 0;
+    const long long iters = MODE == lbm::MODE_STEP ? run.max_steps : 1;
+    for (; it < iters; ++it) {
+      const int p = int(it & 1);
+      double msum = 0.0;
+      for (int w2 = 0; w2 < kWarps; ++w2) msum += red[p][w2];  // same order in every thread
+      const T dmean = T(msum / double(N));
+      const bool save = MODE == lbm::MODE_STEP && K >= 2 && ((it + 2) % K == 0);
+      const bool chk = MODE == lbm::MODE_STEP && K >= 2 && ((it + 1) % K == 0);
+      // (A) rho and psi of every node (Eqs. Density, EOS, InteractionPotential)
+      for (int n = tid; n < N; n += kThreads) {
+        const int x = n % nx, y = n / nx;
+        T g[9];
+        pull_col(cur, nx, ny, N, x, y, g);
+        const T rho = k.rho_ref + lbm::sum9(g);
+        psi_s[n] = lbm::psi_of<T>(rho, k, flag);
+        if (save) rho_prev[n] = rho;
+      }
+      __syncthreads();
+      // (B) forces, velocity, collision, store (Eqs. ShanChenForce, Gravity_1/2, Momentum,
+      // OperatorMRT, LiFS)
+      lbm::Acc<T> acc;
+      double rm = 0.0;
+      for (int n = tid; n < N; n += kThreads) {
+        const int x = n % nx, y = n / nx;
+        const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+        T g[9];
+        pull_col(cur, nx, ny, N, x, y, g);
+        T Sx = T(0), Sy = T(0);
+        if (y > 0 && y < ny - 1) {  // stencil w(1) = 1/3, w(2) = 1/12; zero on the wall rows
+          const T* pc = psi_s + y * nx;
+          const T* pn = pc + nx;
+          const T* ps = pc - nx;
+          const T E = pc[xr], Wt = pc[xl], Nn = pn[x], Ss = ps[x];
+          const T NE = pn[xr], NW = pn[xl], SE = ps[xr], SWt = ps[xl];
+          Sx = lbm::fmadd(T(1.0 / 3.0), E - Wt, T(1.0 / 12.0) * ((NE - NW) + (SE - SWt)));
+          Sy = lbm::fmadd(T(1.0 / 3.0), Nn - Ss, T(1.0 / 12.0) * ((NE + NW) - (SE + SWt)));
+        }
+        T o[9], rho, ux, uy;
+        lbm::collide_node<T, UNIT>(g, psi_s[n], Sx, Sy, dmean, k, o, rho, ux, uy, flag);
+        if (MODE == lbm::MODE_STEP) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) nxt[i * N + n] = o[i];
+          acc.add9(o);
+          if (chk) rm = fmax(rm, fabs(double(rho) - double(rho_prev[n])));
+        } else {
+          const long long idx = col.node_off + n;
+          if (a.rho_out) a.rho_out[idx] = double(rho);
+          if (a.ux_out) a.ux_out[idx] = double(ux);
+          if (a.uy_out) a.uy_out[idx] = double(uy);
+        }
+      }
+      if (MODE != lbm::MODE_STEP) break;
+      const double v = lbm::warp_sum(acc.value());
+      const double m = warp_max(rm);
+      if (lane == 0) {
+        red[p ^ 1][warp] = v;
+        rmax[warp] = m;
+      }
+      __syncthreads();
+      T* t = cur;
+      cur = nxt;
+      nxt = t;
+      if (chk) {
+        double r = 0.0;
+        for (int w2 = 0; w2 < kWarps; ++w2) r = fmax(r, rmax[w2]);
+        res = r;
+        if (!(r > run.tol)) {  // converged (uniform decision)
+          ++it;
+          break;
+        }
+      }
+    }
+    if (MODE == lbm::MODE_STEP) {
+      T* A = static_cast<T*>(a.fA) + 9 * col.node_off;
+      if (cur != A)  // the state ends in the second buffer: copy it back
+        for (int e = tid; e < 9 * N; e += kThreads) A[e] = cur[e];
+    }
+    const int any = __syncthreads_or(flag);
+    if (tid == 0 && MODE == lbm::MODE_STEP) {
+      a.steps[c] += it;
+      a.resid[c] = res;
+      if (any) a.status[c] |= lbm::STATUS_NONPHYS;
+    }
+  }
+}
+
+// g_i = w_i (rho0 - rho_ref) for every column
+template <typename T>
+__global__ void batch_init_kernel(const BatchCol* cols, int ncols, int nx, const double* rho0, T* f) {
+  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const BatchCol col = cols[c];
+    const int N = nx * col.ny;
+    T* fc = f + 9 * col.node_off;
+    const double* r = rho0 + col.node_off;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const double d = r[n] - col.rho_ref;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fc[i * N + n] = T(lbm::w_of(i) * d);
+    }
+  }
+}
+
+// absolute populations of every column (to_double) or back (from_double)
+template <typename T>
+__global__ void batch_state_kernel(const BatchCol* cols, int ncols, int nx, T* f, double* out, bool to_double) {
+  for (int c = blockIdx.x; c < ncols; c += gridDim.x) {
+    const BatchCol col = cols[c];
+    const int N = nx * col.ny;
+    T* fc = f + 9 * col.node_off;
+    double* oc = out + 9 * col.node_off;
+    for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+      const double w = lbm::w_of(e / N) * col.rho_ref;
+      if (to_double)
+        oc[e] = double(fc[e]) + w;
+      else
+        fc[e] = T(oc[e] - w);
+    }
+  }
+}
+
+thread_local char g_berr[512] = "";
+
+int bfail(int code, const char* msg) {
+  snprintf(g_berr, sizeof(g_berr), "%s", msg);
+  lbm::set_last_error(g_berr);
+  return code;
+}
+
+}  // namespace
+
+struct lbm_batch {
+  lbm_params p{};
+  int ncols = 0, nx = 0, max_ny = 0;
+  long long total_nodes = 0;
+  size_t s = 4;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<BatchCol> cols;
+  BatchCol* cols_d = nullptr;
+  int* order_d = nullptr;
+  void* fA = nullptr;
+  void* fB = nullptr;
+  int* counter = nullptr;
+  RunParams* run_d = nullptr;
+  long long* steps_d = nullptr;
+  double* resid_d = nullptr;
+  int* status_d = nullptr;
+  int grid = 0;
+  size_t smem = 0;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+template <typename T, int MODE, bool UNIT>
+void* batch_fn() {
+  return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT>);
+}
+
+void* pick_kernel(int precision, int mode, bool unit) {
+  if (precision == LBM_FP32) {
+    if (mode == lbm::MODE_MOMENTS) return batch_fn<float, lbm::MODE_MOMENTS, false>();
+    return unit ? batch_fn<float, lbm::MODE_STEP, true>() : batch_fn<float, lbm::MODE_STEP, false>();
+  }
+  if (mode == lbm::MODE_MOMENTS) return batch_fn<double, lbm::MODE_MOMENTS, false>();
+  return unit ? batch_fn<double, lbm::MODE_STEP, true>() : batch_fn<double, lbm::MODE_STEP, false>();
+}
+
+BatchArgs make_args(const lbm_batch* b) {
+  BatchArgs a{};
+  a.cols = b->cols_d;
+  a.order = b->order_d;
+  a.ncols = b->ncols;
+  a.nx = b->nx;
+  a.fA = b->fA;
+  a.fB = b->fB;
+  a.a = b->p.a;
+  a.b = b->p.b;
+  a.G = b->p.G;
+  a.sig_e = b->p.sigma / (b->p.tau_e - 0.5);
+  a.sig_vs = b->p.sigma / (b->p.tau_varsigma - 0.5);
+  a.s_e = 1.0 / b->p.tau_e;
+  a.s_vs = 1.0 / b->p.tau_varsigma;
+  a.s_j = 1.0 / b->p.tau_j;
+  a.s_q = 1.0 / b->p.tau_q;
+  a.s_nu = 1.0 / b->p.tau_nu;
+  a.run = b->run_d;
+  a.counter = b->counter;
+  a.steps = b->steps_d;
+  a.resid = b->resid_d;
+  a.status = b->status_d;
+  return a;
+}
+
+bool unit_tau(const lbm_params& p) {
+  return p.tau_e == 1.0 && p.tau_varsigma == 1.0 && p.tau_j == 1.0 && p.tau_q == 1.0 && p.tau_nu == 1.0;
+}
+
+cudaError_t launch(const lbm_batch* b, int mode, BatchArgs args) {
+  void* fn = pick_kernel(b->p.precision, mode, unit_tau(b->p));
+  void* kargs[] = {&args};
+  return cudaLaunchKernel(fn, dim3(b->grid), dim3(kThreads), kargs, b->smem, b->stream);
+}
+
+void free_batch(lbm_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* ptr : {(void*)b->cols_d, (void*)b->order_d, b->fA, b->fB, (void*)b->counter, (void*)b->run_d,
+                    (void*)b->steps_d, (void*)b->resid_d, (void*)b->status_d})
+    if (ptr) cudaFree(ptr);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const double* rho0, int rho0_where,
+                   void* stream, lbm_batch** out) {
+  if (!p || !cols || !rho0 || !out || ncols <= 0) return bfail(LBM_EINVAL, "p, cols, rho0, out must be set and ncols > 0");
+  *out = nullptr;
+  // validate the shared parameters with a representative column
+  lbm_params q = *p;
+  q.ny = cols[0].ny;
+  q.T = cols[0].T;
+  q.gravity_form = cols[0].gravity_form;
+  char err[512];
+  int rc = lbm::validate_params(&q, err);
+  if (rc) return bfail(rc, err);
+  if (p->nx > 64) return bfail(LBM_EINVAL, "batched columns are at most 64 nodes wide");
+  if (rho0_where != LBM_HOST && rho0_where != LBM_DEVICE) return bfail(LBM_EINVAL, "rho0_where must be LBM_HOST or LBM_DEVICE");
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return bfail(LBM_ENOMEM, "out of host memory");
+  b->p = *p;
+  b->ncols = ncols;
+  b->nx = p->nx;
+  b->s = p->precision == LBM_FP32 ? 4 : 8;
+  auto fail = [&](int code, const char* msg) {
+    free_batch(b);
+    return bfail(code, msg);
+  };
+  long long off = 0;
+  b->cols.resize(ncols);
+  for (int c = 0; c < ncols; ++c) {
+    const lbm_column& in = cols[c];
+    q.ny = in.ny;
+    q.T = in.T;
+    q.gx = in.gx;
+    q.gy = in.gy;
+    q.gravity_form = in.gravity_form;
+    if ((rc = lbm::validate_params(&q, err))) return fail(rc, err);
+    if (2.0 * p->nx * in.ny * (p->precision == LBM_FP32 ? 4 : 8) > 200.0 * 1024)
+      return fail(LBM_EINVAL, "column too large for the batch kernel's shared memory (2 nx ny sizeof(real) <= 200 KiB)");
+    BatchCol& bc = b->cols[c];
+    bc.ny = in.ny;
+    bc.form = in.gravity_form;
+    bc.node_off = off;
+    bc.RT = p->R * in.T;
+    bc.gx = in.gx;
+    bc.gy = in.gy;
+    bc.rho_ref = 0.0;
+    off += (long long)p->nx * in.ny;
+    b->max_ny = std::max(b->max_ny, in.ny);
+  }
+  b->total_nodes = off;
+  // deviation reference per column: the mean of its rho0 in FP32, 0 in FP64 (or p->rho_ref)
+  std::vector<double> rho_h;
+  const double* rho_src = rho0;
+  if (rho0_where == LBM_DEVICE && p->precision == LBM_FP32 && std::isnan(p->rho_ref)) {
+    rho_h.resize(size_t(off));
+    if (cudaMemcpy(rho_h.data(), rho0, size_t(off) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(LBM_ECUDA, "copy of rho0");
+    rho_src = rho_h.data();
+  }
+  for (int c = 0; c < ncols; ++c) {
+    BatchCol& bc = b->cols[c];
+    if (!std::isnan(p->rho_ref)) {
+      bc.rho_ref = p->rho_ref;
+    } else if (p->precision == LBM_FP32) {
+      const long long n = (long long)p->nx * bc.ny;
+      double s = 0.0;
+      for (long long i = 0; i < n; ++i) s += rho_src[bc.node_off + i];
+      bc.rho_ref = s / double(n);
+    }
+  }
+  if (stream) {
+    b->stream = static_cast<cudaStream_t>(stream);
+  } else {  // graph capture needs a stream other than the legacy default one
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(LBM_ECUDA, "stream");
+    b->own_stream = true;
+  }
+  const size_t state = size_t(off) * 9 * b->s;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  alloc((void**)&b->cols_d, sizeof(BatchCol) * ncols);
+  alloc((void**)&b->order_d, sizeof(int) * ncols);
+  alloc(&b->fA, state);
+  alloc(&b->fB, state);
+  alloc((void**)&b->counter, sizeof(int));
+  alloc((void**)&b->run_d, sizeof(RunParams));
+  alloc((void**)&b->steps_d, sizeof(long long) * ncols);
+  alloc((void**)&b->resid_d, sizeof(double) * ncols);
+  alloc((void**)&b->status_d, sizeof(int) * ncols);
+  if (e != cudaSuccess) return fail(LBM_ENOMEM, "device allocation for the batch failed");
+  // tallest columns first (longest work first balances the work-stealing queue)
+  std::vector<int> order(ncols);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cols[x].ny > cols[y].ny; });
+  std::vector<double> inf(ncols, INFINITY);
+  e = cudaMemcpyAsync(b->cols_d, b->cols.data(), sizeof(BatchCol) * ncols, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->order_d, order.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->steps_d, 0, sizeof(long long) * ncols, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->resid_d, inf.data(), sizeof(double) * ncols, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->status_d, 0, sizeof(int) * ncols, b->stream);
+  // rho0 on the device: a host rho0 is staged through the second buffer (8 bytes per node
+  // fit in its 9 * sizeof(real) bytes per node)
+  double* rho_d = const_cast<double*>(rho0);
+  if (e == cudaSuccess && rho0_where == LBM_HOST) {
+    e = cudaMemcpyAsync(b->fB, rho0, size_t(off) * 8, cudaMemcpyHostToDevice, b->stream);
+    rho_d = static_cast<double*>(b->fB);
+  }
+  if (e == cudaSuccess && rho_d) {
+    if (p->precision == LBM_FP32)
+      batch_init_kernel<float><<<std::min(ncols, 4096), 256, 0, b->stream>>>(b->cols_d, ncols, b->nx, rho_d, (float*)b->fA);
+    else
+      batch_init_kernel<double><<<std::min(ncols, 4096), 256, 0, b->stream>>>(b->cols_d, ncols, b->nx, rho_d, (double*)b->fA);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
+  // persistent grid: resident CTAs on every SM, capped so that the columns in flight keep
+  // their two buffers in L2 (about 96 MB)
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  b->smem = size_t(2) * size_t(b->nx) * size_t(b->max_ny) * b->s;
+  for (int mode : {lbm::MODE_STEP, lbm::MODE_MOMENTS})
+    for (bool u : {false, true}) {
+      e = cudaFuncSetAttribute(pick_kernel(p->precision, mode, u), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(b->smem));
+      if (e != cudaSuccess) return fail(LBM_ECUDA, "batch kernel shared memory limit");
+    }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(p->precision, lbm::MODE_STEP, unit_tau(*p)),
+                                                kThreads, b->smem);
+  const double avg_bytes = 2.0 * 9.0 * double(b->s) * double(off) / double(ncols);
+  const int l2_cap = std::max(nsm, int(96.0e6 / avg_bytes));
+  b->grid = std::max(1, std::min({nsm * std::max(per_sm, 1), l2_cap, ncols}));
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, double* seconds) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  if (max_steps < 0 || check_every < 2 || !(tol >= 0)) return bfail(LBM_EINVAL, "need max_steps >= 0, check_every >= 2, tol >= 0");
+  RunParams rp{tol, (long long)max_steps, check_every};
+  cudaError_t e = cudaMemcpyAsync(b->run_d, &rp, sizeof(rp), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && !b->graph) {  // capture [counter reset -> persistent kernel] once
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream);
+      cudaError_t e2 = launch(b, lbm::MODE_STEP, make_args(b));
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess && seconds) {
+    e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+  if (e == cudaSuccess && seconds) e = cudaEventRecord(t1, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess && seconds) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, t0, t1);
+    *seconds = ms * 1e-3;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_results(const lbm_batch* b, int64_t* steps, double* residual, int* status) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  cudaError_t e = cudaSuccess;
+  if (steps) e = cudaMemcpyAsync(steps, b->steps_d, sizeof(long long) * b->ncols, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess && residual)
+    e = cudaMemcpyAsync(residual, b->resid_d, sizeof(double) * b->ncols, cudaMemcpyDeviceToHost, b->stream);
+  std::vector<int> st(b->ncols);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(st.data(), b->status_d, sizeof(int) * b->ncols, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  bool bad = false;
+  for (int c = 0; c < b->ncols; ++c) {
+    const int code = (st[c] & lbm::STATUS_NONPHYS) ? LBM_ENONPHYS : LBM_OK;
+    bad |= code != LBM_OK;
+    if (status) status[c] = code;
+  }
+  return bad ? bfail(LBM_ENONPHYS, "at least one column became non-physical") : LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch* b, double* rho, double* ux, double* uy, int where) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  if (where != LBM_HOST && where != LBM_DEVICE) return bfail(LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
+  const size_t bytes = size_t(b->total_nodes) * 8;
+  double* d[3] = {rho, ux, uy};
+  double* tmp[3] = {nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  if (where == LBM_HOST)  // staged through freshly allocated device buffers
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      if (d[i]) e = cudaMalloc(&tmp[i], bytes);
+  BatchArgs a = make_args(b);
+  a.rho_out = where == LBM_HOST ? tmp[0] : rho;
+  a.ux_out = where == LBM_HOST ? tmp[1] : ux;
+  a.uy_out = where == LBM_HOST ? tmp[2] : uy;
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->counter, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = launch(b, lbm::MODE_MOMENTS, a);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    if (where == LBM_HOST && d[i]) e = cudaMemcpyAsync(d[i], tmp[i], bytes, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (double* t : tmp)
+    if (t) cudaFree(t);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_get_state(lbm_batch* b, double* f, int where) {
+  if (!b || !f || (where != LBM_HOST && where != LBM_DEVICE)) return bfail(LBM_EINVAL, "bad batch, f or where");
+  const size_t bytes = size_t(b->total_nodes) * 9 * 8;
+  double* dst = f;
+  cudaError_t e = cudaSuccess;
+  if (where == LBM_HOST) e = cudaMalloc(&dst, bytes);
+  const int g = std::min(b->ncols, 4096);
+  if (e == cudaSuccess) {
+    if (b->p.precision == LBM_FP32)
+      batch_state_kernel<float><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (float*)b->fA, dst, true);
+    else
+      batch_state_kernel<double><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (double*)b->fA, dst, true);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && where == LBM_HOST) e = cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (where == LBM_HOST && dst) cudaFree(dst);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out) {
+  if (!src || !out || (precision != LBM_FP32 && precision != LBM_FP64)) return bfail(LBM_EINVAL, "bad arguments");
+  *out = nullptr;
+  // the new batch starts from src's state: absolute populations through a device buffer
+  const size_t n9 = size_t(src->total_nodes) * 9;
+  double* abs_d = nullptr;
+  if (cudaMalloc(&abs_d, n9 * 8) != cudaSuccess) return bfail(LBM_ENOMEM, "conversion buffer");
+  lbm_batch* s = const_cast<lbm_batch*>(src);
+  int rc = lbm_batch_get_state(s, abs_d, LBM_DEVICE);
+  std::vector<lbm_column> cols(src->ncols);
+  for (int c = 0; c < src->ncols; ++c) {
+    cols[c].ny = src->cols[c].ny;
+    cols[c].gravity_form = src->cols[c].form;
+    cols[c].T = src->cols[c].RT / src->p.R;
+    cols[c].gx = src->cols[c].gx;
+    cols[c].gy = src->cols[c].gy;
+  }
+  // rho0 placeholder: the column means (only the deviation reference uses it)
+  std::vector<double> rho0(size_t(src->total_nodes));
+  for (int c = 0; c < src->ncols; ++c)
+    std::fill(rho0.begin() + src->cols[c].node_off, rho0.begin() + src->cols[c].node_off + src->nx * src->cols[c].ny,
+              src->cols[c].rho_ref);
+  lbm_params p = src->p;
+  p.precision = precision;
+  if (rc == LBM_OK) rc = lbm_batch_init(&p, cols.data(), src->ncols, rho0.data(), LBM_HOST, src->own_stream ? nullptr : src->stream, out);
+  if (rc == LBM_OK) {
+    lbm_batch* b = *out;
+    for (int c = 0; c < b->ncols; ++c) b->cols[c].rho_ref = precision == LBM_FP64 && std::isnan(src->p.rho_ref) ? 0.0 : src->cols[c].rho_ref;
+    cudaError_t e = cudaMemcpyAsync(b->cols_d, b->cols.data(), sizeof(BatchCol) * b->ncols, cudaMemcpyHostToDevice, b->stream);
+    const int g = std::min(b->ncols, 4096);
+    if (e == cudaSuccess) {
+      if (precision == LBM_FP32)
+        batch_state_kernel<float><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (float*)b->fA, abs_d, false);
+      else
+        batch_state_kernel<double><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (double*)b->fA, abs_d, false);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->steps_d, src->steps_d, sizeof(long long) * b->ncols, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+      lbm_batch_destroy(b);
+      *out = nullptr;
+      rc = bfail(LBM_ECUDA, cudaGetErrorString(e));
+    }
+  }
+  cudaFree(abs_d);
+  return rc;
+}
+
+int lbm_batch_destroy(lbm_batch* b) {
+  if (b && b->stream) cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -39,6 +39,8 @@ EXPORTS = (
     "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
     "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling",
+    "lbm_batch_init", "lbm_batch_run", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
+    "lbm_batch_convert", "lbm_batch_destroy",
 )
 
 
@@ -53,6 +55,11 @@ class lbm_params(ctypes.Structure):
         ("gravity_form", ctypes.c_int32), ("reserved0", ctypes.c_int32),
         ("rho_ref", ctypes.c_double), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
     ]
+
+
+class lbm_column(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int32), ("gravity_form", ctypes.c_int32), ("T", ctypes.c_double),
+                ("gx", ctypes.c_double), ("gy", ctypes.c_double)]
 
 
 class LbmError(RuntimeError):
@@ -94,6 +101,13 @@ def load(path: str = LIB_PATH):
         "lbm_autotune": (i32, [vp, i32, P(i32), P(d)]),
         "lbm_tile_variants": (i32, [i32]),
         "lbm_set_tiling": (i32, [vp, i32]),
+        "lbm_batch_init": (i32, [P(lbm_params), P(lbm_column), i32, vp, i32, vp, P(vp)]),
+        "lbm_batch_run": (i32, [vp, d, i64, i32, P(d)]),
+        "lbm_batch_results": (i32, [vp, vp, vp, vp]),
+        "lbm_batch_moments": (i32, [vp, vp, vp, vp, i32]),
+        "lbm_batch_get_state": (i32, [vp, vp, i32]),
+        "lbm_batch_convert": (i32, [vp, i32, P(vp)]),
+        "lbm_batch_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +253,59 @@ def lbm_step_noalloc(p, f_in, f_out, stream=None):
     """One step f_out = step(f_in) on caller-owned device arrays of deviations
     f_i - w_i rho_ref (real type of p.precision), with no device allocation."""
     _check(load().lbm_step_noalloc(ctypes.byref(p), _ptr(f_in)[0], _ptr(f_out)[0], stream))
+
+
+def lbm_batch_init(p, columns, rho0, stream=None):
+    """columns: sequence of dicts with ny, gravity_form (or form), T, gx, gy."""
+    arr = (lbm_column * len(columns))()
+    for c, col in zip(arr, columns):
+        c.ny = int(col["ny"])
+        c.gravity_form = int(col.get("gravity_form", col.get("form", 1)))
+        c.T = float(col["T"])
+        c.gx = float(col.get("gx", 0.0))
+        c.gy = float(col.get("gy", 0.0))
+    addr, where = _ptr(rho0)
+    b = ctypes.c_void_p()
+    _check(load().lbm_batch_init(ctypes.byref(p), arr, len(columns), addr, where, stream, ctypes.byref(b)))
+    return b
+
+
+def lbm_batch_run(b, tol, max_steps, check_every=100):
+    """Runs every column to its residual target or max_steps; returns the device seconds."""
+    sec = ctypes.c_double()
+    _check(load().lbm_batch_run(b, float(tol), int(max_steps), int(check_every), ctypes.byref(sec)))
+    return sec.value
+
+
+def lbm_batch_results(b, ncols, check=True):
+    steps = np.zeros(ncols, dtype=np.int64)
+    res = np.zeros(ncols)
+    status = np.zeros(ncols, dtype=np.int32)
+    rc = load().lbm_batch_results(b, steps.ctypes.data, res.ctypes.data, status.ctypes.data)
+    if check and rc != LBM_ENONPHYS:
+        _check(rc)
+    return steps, res, status
+
+
+def lbm_batch_moments(b, rho=None, ux=None, uy=None):
+    wheres = {w for _, w in map(_ptr, (rho, ux, uy)) if w is not None}
+    where = wheres.pop() if wheres else LBM_HOST
+    _check(load().lbm_batch_moments(b, _ptr(rho)[0], _ptr(ux)[0], _ptr(uy)[0], where))
+
+
+def lbm_batch_get_state(b, f):
+    addr, where = _ptr(f)
+    _check(load().lbm_batch_get_state(b, addr, where))
+
+
+def lbm_batch_convert(b, precision):
+    out = ctypes.c_void_p()
+    _check(load().lbm_batch_convert(b, int(precision), ctypes.byref(out)))
+    return out
+
+
+def lbm_batch_destroy(b):
+    _check(load().lbm_batch_destroy(b))
 
 
 # ---------------------------------------------------------------- convenience

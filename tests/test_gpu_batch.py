@@ -1,0 +1,176 @@
+"""GPU tests of the batched-column runner (lbm_batch_*) against the FP64 oracle.
+
+Each column of a batch is an independent nx x ny_c lattice with its own height,
+temperature, gravity and gravity form; every column is checked against the
+oracle run on that column alone. Tolerances as in test_gpu_parity.py: FP64
+1e-14 per step for a few steps, FP32 1e-6 sqrt(n) + 1e-6.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import eos
+from oracle import lbm as olbm
+from paper_2301_12869_gb300 import _build, inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+A, B, R = 0.25, 4.0, 1.0
+RHO_C, T_C, P_C = eos.critical_point(A, B, R)
+NX = 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(lbm.LIB_PATH):
+        _build.build()
+    lbm.load()
+
+
+def make_columns(n, seed, heights=(8, 16, 24, 32, 48, 64)):
+    rng = np.random.default_rng(seed)
+    cols, rhos = [], []
+    for c in range(n):
+        ny = int(heights[c % len(heights)])
+        Tr = float(rng.uniform(0.72, 0.92))
+        gy = -float(10 ** rng.uniform(-6, -4))
+        form = 1 + (c % 2)
+        frac = float(rng.uniform(0.3, 0.7))
+        rv, rl, _ = eos.maxwell(Tr * T_C, A, B, R)
+        rho0 = inputs.column_rho0(NX, ny, rl, rv, max(1, int(round(frac * ny))), width=3.0)
+        cols.append(dict(ny=ny, T=Tr * T_C, gx=0.0, gy=gy, form=form))
+        rhos.append(rho0)
+    return cols, rhos
+
+
+def batch_params(precision, **kw):
+    kw.setdefault("a", A)
+    return lbm.make_params(NX, 8, 0.8 * T_C, precision, **kw)
+
+
+def oracle_column(col, p):
+    return olbm.Params(nx=NX, ny=col["ny"], a=A, b=B, R=R, T=col["T"], G=p.G, sigma=p.sigma, tau_rho=p.tau_rho,
+                       tau_e=p.tau_e, tau_varsigma=p.tau_varsigma, tau_j=p.tau_j, tau_q=p.tau_q, tau_nu=p.tau_nu,
+                       g=(col["gx"], col["gy"]), form=col["form"])
+
+
+def split_state(f_all, cols):
+    out, off = [], 0
+    for col in cols:
+        n = 9 * NX * col["ny"]
+        out.append(f_all[off:off + n].reshape(9, col["ny"], NX))
+        off += n
+    return out
+
+
+@pytest.mark.parametrize("precision, steps, tol, taus", [
+    ("fp64", 7, 1e-14, {}),
+    ("fp64", 7, 1e-14, dict(tau_e=0.8, tau_varsigma=1.1, tau_q=1.2, tau_nu=0.7)),
+    ("fp32", 50, 1e-6 * math.sqrt(50) + 1e-6, {}),
+])
+def test_every_column_matches_oracle(precision, steps, tol, taus):
+    cols, rhos = make_columns(24, seed=3)
+    p = batch_params(precision, **taus)
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        total = sum(9 * NX * c["ny"] for c in cols)
+        f0 = np.empty(total)
+        lbm.lbm_batch_get_state(b, f0)
+        lbm.lbm_batch_run(b, 0.0, steps, check_every=1000)
+        f1 = np.empty(total)
+        lbm.lbm_batch_get_state(b, f1)
+        st, res, status = lbm.lbm_batch_results(b, len(cols))
+        assert np.all(st == steps) and np.all(status == 0)
+        for col, g0, g1 in zip(cols, split_state(f0, cols), split_state(f1, cols)):
+            want = olbm.run(g0, oracle_column(col, p), steps)
+            assert np.max(np.abs(g1 - want)) <= tol, col
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_batch_column_equals_single_lattice_handle():
+    """The batch runner and lbm_step give the same state for the same column (FP64)."""
+    cols, rhos = make_columns(3, seed=9, heights=(40,))
+    p = batch_params("fp64")
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_run(b, 0.0, 300, check_every=1000)
+        f = np.empty(sum(9 * NX * c["ny"] for c in cols))
+        lbm.lbm_batch_get_state(b, f)
+        for col, rho0, g in zip(cols, rhos, split_state(f, cols)):
+            q = lbm.make_params(NX, col["ny"], col["T"], "fp64", a=A, form=col["form"], g=(col["gx"], col["gy"]))
+            h = lbm.lbm_init(q, rho0)
+            lbm.lbm_step(h, 300)
+            fh = np.empty((9, col["ny"], NX))
+            lbm.lbm_get_state(h, fh)
+            lbm.lbm_destroy(h)
+            assert np.max(np.abs(fh - g)) <= 1e-13
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_residual_target_and_precision_continuation():
+    """FP32 to its rounding floor, then FP64 to 1e-10: every column reaches the target,
+    and the final profiles agree with an FP64-only run to the FP32 path's accuracy."""
+    cols, rhos = make_columns(8, seed=5, heights=(16, 24))
+    rho_all = np.concatenate([r.ravel() for r in rhos])
+    b32 = lbm.lbm_batch_init(batch_params("fp32"), cols, rho_all)
+    b64 = lbm.lbm_batch_init(batch_params("fp64"), cols, rho_all)
+    try:
+        lbm.lbm_batch_run(b32, 1e-6, 200000, check_every=100)
+        st32, res32, _ = lbm.lbm_batch_results(b32, len(cols))
+        assert np.all(res32 <= 1e-6)
+        b = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
+        try:
+            lbm.lbm_batch_run(b, 1e-10, 400000, check_every=100)
+            st, res, status = lbm.lbm_batch_results(b, len(cols))
+            assert np.all(res <= 1e-10) and np.all(status == 0)
+            assert np.all(st >= st32)
+            lbm.lbm_batch_run(b64, 1e-10, 400000, check_every=100)
+            _, res64, _ = lbm.lbm_batch_results(b64, len(cols))
+            assert np.all(res64 <= 1e-10)
+            n = rho_all.size
+            r1, r2 = np.empty(n), np.empty(n)
+            lbm.lbm_batch_moments(b, rho=r1)
+            lbm.lbm_batch_moments(b64, rho=r2)
+            # both are steady states of the same columns: equal to the FP32 mass error
+            assert np.max(np.abs(r1 - r2)) <= 1e-5
+        finally:
+            lbm.lbm_batch_destroy(b)
+    finally:
+        lbm.lbm_batch_destroy(b32)
+        lbm.lbm_batch_destroy(b64)
+
+
+def test_batch_moments_match_oracle():
+    cols, rhos = make_columns(6, seed=11)
+    p = batch_params("fp64")
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_run(b, 0.0, 20, check_every=1000)
+        total = sum(NX * c["ny"] for c in cols)
+        f = np.empty(9 * total)
+        lbm.lbm_batch_get_state(b, f)
+        rho, ux, uy = np.empty(total), np.empty(total), np.empty(total)
+        lbm.lbm_batch_moments(b, rho, ux, uy)
+        off = 0
+        for col, g in zip(cols, split_state(f, cols)):
+            n = NX * col["ny"]
+            mac = olbm.macroscopic(g, oracle_column(col, p))
+            np.testing.assert_allclose(rho[off:off + n].reshape(col["ny"], NX), mac.rho, rtol=0, atol=1e-14)
+            np.testing.assert_allclose(uy[off:off + n].reshape(col["ny"], NX), mac.u[1], rtol=0, atol=1e-13)
+            off += n
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_batch_rejects_oversized_columns():
+    p = batch_params("fp64")
+    with pytest.raises(lbm.LbmError, match="shared memory"):
+        lbm.lbm_batch_init(p, [dict(ny=4000, T=0.8 * T_C, form=1)], np.full(4 * 4000, 0.1))
