@@ -249,6 +249,63 @@ def run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot):
     }
 
 
+# ---------------------------------------------------------------- batched columns
+def run_columns(args):
+    """Time to steady state of independent liquid columns (the batched workload): seeded
+    4 x H columns from the batched-column generator (T/T_c ~ U[0.70, 0.95], |g| log-uniform
+    in [1e-6, 1e-4], either gravity form, liquid fraction ~ U[0.3, 0.7]) restricted to the
+    heights in --column-heights, each run to max |rho_t - rho_(t-1)| <= 1e-10 (checked every
+    100 steps): plain FP64 against FP32 down to 1e-7 followed by FP64 from that state."""
+    import numpy as np
+
+    from paper_2301_12869_gb300 import inputs, lbm
+
+    heights = tuple(int(h) for h in args.column_heights.split(","))
+    gen = [c for c in inputs.batched_columns(4 * args.columns, seed=SEED) if c["ny"] in heights][: args.columns]
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    cols, rhos = [], []
+    for c in gen:
+        T = c["Tr"] * Tc
+        rv, rl, _ = lbm.lbm_coexistence(A, B, R, T)
+        rhos.append(inputs.column_rho0(4, c["ny"], rl, rv, max(1, int(round(c["liquid_fraction"] * c["ny"])))))
+        cols.append(dict(ny=c["ny"], T=T, gy=c["gy"], form=c["form"]))
+    rho = np.concatenate([r.ravel() for r in rhos])
+    nodes = rho.size
+    cap = args.column_max_steps
+    out = {}
+    p64 = lbm.make_params(4, 8, 0.8 * Tc, "fp64", a=A, b=B, R=R)
+    b64 = lbm.lbm_batch_init(p64, cols, rho)
+    t64 = lbm.lbm_batch_run(b64, 1e-10, cap, 100)
+    st64, res64, s64 = lbm.lbm_batch_results(b64, len(cols), check=False)
+    lbm.lbm_batch_destroy(b64)
+    p32 = lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R)
+    b32 = lbm.lbm_batch_init(p32, cols, rho)
+    t32 = lbm.lbm_batch_run(b32, 1e-7, cap, 100)
+    st32, _, _ = lbm.lbm_batch_results(b32, len(cols), check=False)
+    bc = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
+    lbm.lbm_batch_destroy(b32)
+    tpol = lbm.lbm_batch_run(bc, 1e-10, cap, 100)
+    stc, resc, sc = lbm.lbm_batch_results(bc, len(cols), check=False)
+    lbm.lbm_batch_destroy(bc)
+    ok64 = (res64 <= 1e-10) & (s64 == 0)
+    okc = (resc <= 1e-10) & (sc == 0)
+    both = ok64 & okc
+    out = {
+        "metric": "time to steady state (residual 1e-10), batched columns", "unit": "s",
+        "value": t32 + tpol, "higher_is_better": False, "impl": "gb300", "n_gpus": 1,
+        "config": {"workload": f"{len(cols)} seeded 4xH liquid columns, H in {heights}", "nodes": nodes,
+                   "max_steps": cap, "check_every": 100},
+        "fp64_plain": {"seconds": t64, "converged": int(ok64.sum()), "nonphysical": int((s64 != 0).sum()),
+                       "node_steps_per_s": float(np.sum(st64 * [4 * c["ny"] for c in cols]) / t64)},
+        "fp32_then_fp64": {"seconds": t32 + tpol, "fp32_seconds": t32, "fp64_seconds": tpol,
+                           "converged": int(okc.sum()), "nonphysical": int((sc != 0).sum())},
+        "speedup_vs_fp64": t64 / (t32 + tpol),
+        "steps_ratio_converged": float(np.sum(stc[both]) / max(1, np.sum(st64[both]))),
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- main
 def run_reference(args, world, rank):
     if rank != 0:
@@ -279,6 +336,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
+    ap.add_argument("--workload", choices=["domain", "columns"], default="domain",
+                    help="domain: the 1024 x 4096 single-domain throughput line (default); "
+                         "columns: time to steady state of batched columns")
+    ap.add_argument("--columns", type=int, default=1024)
+    ap.add_argument("--column-heights", default="64,128")
+    ap.add_argument("--column-max-steps", type=int, default=200000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -286,6 +349,8 @@ def main(argv=None):
 
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload == "columns":
+        return run_columns(args) if rank == 0 else 0
 
     import numpy as np
     import torch

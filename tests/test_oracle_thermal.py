@@ -1,0 +1,77 @@
+"""Pins of the energy-equation oracle (oracle/thermal.py): exactness of the stencils on
+polynomials, the steady linear conduction profile of Eq. Temp_Profile, the discrete decay
+rate of a diffusing Fourier mode through Heun's RK2, and the C-S (dp/dT)_rho."""
+import numpy as np
+import pytest
+
+from oracle import eos, lbm, thermal
+
+A, B, R = 0.25, 4.0, 1.0
+RHO_C, T_C, P_C = eos.critical_point(A, B, R)
+
+
+def params(nx, ny):
+    return lbm.Params(nx=nx, ny=ny, a=A, b=B, R=R, T=0.8 * T_C)
+
+
+def test_dp_dT_matches_finite_difference_of_eos():
+    p = params(1, 1)
+    rho = np.linspace(0.01, 0.4, 40)
+    h = 1e-7 * T_C
+    fd = (eos.p_eos(rho, p.T + h, A, B, R) - eos.p_eos(rho, p.T - h, A, B, R)) / (2 * h)
+    np.testing.assert_allclose(thermal.dp_dT(rho, p), fd, rtol=1e-7)
+
+
+def test_linear_conduction_profile_is_steady():
+    """With u = 0 and T linear between T_bot and T_top at the wall positions, every term
+    of Eq. Energy_Equation vanishes (Eq. Temp_Profile)."""
+    ny, nx = 30, 6
+    th = thermal.Thermal(T_bot=0.95 * T_C, T_top=0.80 * T_C)
+    T = thermal.linear_profile(ny, nx, th.T_bot, th.T_top)
+    rho = np.full((ny, nx), 0.2)
+    z = np.zeros_like(rho)
+    r = thermal.rate(T, rho, z, z, params(nx, ny), th)
+    assert np.max(np.abs(r)) < 1e-18
+    np.testing.assert_array_equal(thermal.energy_step(T, rho, z, z, params(nx, ny), th), T)
+
+
+def test_stencils_exact_on_linear_and_quadratic_fields():
+    ny, nx = 12, 10
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    phi = 0.3 + 0.02 * Y
+    pad = thermal.with_ghosts(phi, lambda r: 2 * (0.3 - 0.01) - r, lambda r: 2 * (0.3 + 0.02 * (ny - 0.5)) - r)
+    gx, gy = thermal.gradient(pad)
+    np.testing.assert_allclose(gy, 0.02, rtol=1e-13)
+    np.testing.assert_allclose(gx, 0.0, atol=1e-16)
+    # quadratic in y on interior rows: the lattice Laplacian of q y^2 is 2 q
+    q = 1e-3
+    phi = q * Y**2
+    pad = thermal.with_ghosts(phi, lambda r: r * 0 + q, lambda r: r * 0 + q * ny**2)
+    lap = thermal.laplacian(pad)
+    np.testing.assert_allclose(lap[1:-1], 2 * q, rtol=1e-12)
+    # divergence of u = (alpha x, beta y) away from the periodic seam and the walls
+    ux = 1e-3 * X
+    uy = 2e-3 * Y
+    uxp = thermal.with_ghosts(ux, lambda r: r, lambda r: r)
+    uyp = thermal.with_ghosts(uy, lambda r: r - 2e-3, lambda r: r + 2e-3)
+    div = thermal.divergence(uxp, uyp)
+    np.testing.assert_allclose(div[1:-1, 1:-1], 3e-3, rtol=1e-12)
+
+
+def test_diffusing_mode_decays_at_the_discrete_rate():
+    """u = 0, uniform rho: a mode cos(k x) decays each Heun step by 1 + z + z^2/2 with
+    z = D lambda(k), D = kappa/(rho c_v), lambda(k) = (2/cs^2) sum_i w_i (cos(k c_ix) - 1).
+    Checked on the middle row of 9, out of reach of the wall ghosts for both stages."""
+    nx, ny = 32, 9
+    T0, amp, rho0 = 0.8 * T_C, 1e-3 * T_C, 0.1
+    th = thermal.Thermal(c_v=5.0, kappa=0.02, T_bot=T0, T_top=T0)
+    k = 2 * np.pi * 3 / nx
+    mode = np.cos(k * np.arange(nx, dtype=float))
+    T = T0 + amp * mode[None, :] * np.ones((ny, 1))
+    rho = np.full_like(T, rho0)
+    z = np.zeros_like(T)
+    lam = 2 / lbm.CS2 * sum(lbm.W[i] * (np.cos(k * lbm.C[i, 0]) - 1) for i in range(9))
+    zz = th.kappa / (rho0 * th.c_v) * lam
+    Tn = thermal.energy_step(T, rho, z, z, params(nx, ny), th)
+    sel = np.abs(mode) > 0.5
+    np.testing.assert_allclose((Tn[4, sel] - T0) / (amp * mode[sel]), 1 + zz + zz**2 / 2, rtol=1e-10)
