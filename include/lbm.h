@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 /* ---- status codes */
 enum {
@@ -74,18 +74,26 @@ typedef struct lbm_params {
   double tau_rho, tau_e, tau_varsigma, tau_j, tau_q, tau_nu; /* Eq. RelaxationMatrix */
   double gx, gy;          /* gravitational acceleration vector */
   int32_t gravity_form;   /* LBM_GRAVITY_RHO_G or LBM_GRAVITY_RHO_MINUS_MEAN_G */
-  int32_t reserved0;
+  int32_t thermal;        /* 0: isothermal, T uniform. 1: thermal variant (Sec. III): a
+                             temperature field T(x) enters Eq. EOS at every node and is
+                             advanced after each LBM step by Eq. Energy_Equation */
   double rho_ref;         /* populations are stored as f_i - w_i rho_ref; NaN = choose
                              (mean of rho0 for FP32, 0 for FP64) */
   void* workspace;        /* optional caller-owned DEVICE buffer of lbm_workspace_bytes();
                              borrowed, must outlive the handle; NULL = library allocates */
   uint64_t workspace_bytes;
+  /* thermal variant only (thermal = 1); Eq. Energy_Equation with constant kappa */
+  double c_v;             /* specific heat at constant volume (> 0) */
+  double kappa;           /* thermal conductivity (>= 0) */
+  double T_bot, T_top;    /* wall temperatures below row 0 and above row ny-1 (> 0), imposed
+                             half a link beyond the rows like the bounce-back walls */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;
 
 /* Paper defaults: a = 0.5, b = 4, R = 1 (Sec. IV), G = -1, sigma = 1.385, all tau = 1
- * (Sec. IV), gravity off, form 1, FP64, rho_ref = NaN, no workspace. nx, ny, T unset (0). */
+ * (Sec. IV), gravity off, form 1, FP64, rho_ref = NaN, no workspace, isothermal, with
+ * c_v = 5 and kappa = 0.02 (Sec. IV) ready for thermal = 1. nx, ny, T, T_bot, T_top unset (0). */
 void lbm_params_default(lbm_params* p);
 
 /* Device bytes a handle needs for p (populations A/B, reduction partials, moments scratch). */
@@ -101,7 +109,12 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
 /* Advance nsteps >= 0 time steps (asynchronous on the handle's stream). Each step is
  * one launch of the fused kernel: stream, rho, psi, <rho>, F_int, F_g, u, MRT + Li
  * forcing, store. Device-side faults (non-physical state, timeouts) are recorded in a
- * sticky status returned by the next synchronising call. */
+ * sticky status returned by the next synchronising call.
+ * Thermal variant: psi uses R T(x) of the current temperature field; then a moments
+ * launch gives rho and u of the new populations (as the next step evaluates them) and two
+ * launches advance T by Heun's second-order Runge-Kutta (dt = 1) on Eq. Energy_Equation,
+ * with isotropic D2Q9-weighted central differences and the wall temperatures T_bot, T_top
+ * (ghost rows T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of the current state, as the next step evaluates them: the stored
@@ -120,9 +133,18 @@ int lbm_reduce(lbm_handle* h, int kind, double* out);
 int lbm_get_state(lbm_handle* h, double* f, int where, int64_t* steps_done);
 int lbm_set_state(lbm_handle* h, const double* f, int where, int64_t steps_done);
 
-/* Change T, G, sigma, tau_*, gx, gy, gravity_form between steps (the paper's
- * equilibrate-then-change protocol). nx, ny, precision, rho_ref, a, b, R must match. */
+/* Change T, G, sigma, tau_*, gx, gy, gravity_form (and c_v, kappa, T_bot, T_top of the
+ * thermal variant) between steps (the paper's equilibrate-then-change protocol).
+ * nx, ny, precision, rho_ref, a, b, R and thermal must match. */
 int lbm_set_params(lbm_handle* h, const lbm_params* p);
+
+/* Thermal variant: the temperature field, nx*ny doubles [y][x] in host or device memory
+ * per `where` (stored in the handle's precision). lbm_init sets the steady conduction
+ * profile T(y) = T_bot + (T_top - T_bot)(y + 1/2)/ny (Eq. Temp_Profile with constant kappa).
+ * The caller keeps T > 0. LBM_EINVAL on an isothermal handle. get synchronises when
+ * where == LBM_HOST; set synchronises always. */
+int lbm_set_temperature(lbm_handle* h, const double* T, int where);
+int lbm_get_temperature(lbm_handle* h, double* T, int where);
 
 /* Synchronise and return the sticky device status (LBM_OK, LBM_ENONPHYS, LBM_ETIMEOUT). */
 int lbm_status(lbm_handle* h);
@@ -175,8 +197,8 @@ typedef struct lbm_column {
 
 typedef struct lbm_batch lbm_batch;
 
-/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->ny, p->T, p->gx,
- * p->gy, p->gravity_form and p->workspace are ignored; p->rho_ref NaN means: each column's
+/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->thermal must be 0;
+ * p->ny, p->T, p->gx, p->gy, p->gravity_form and p->workspace are ignored; p->rho_ref NaN means: each column's
  * mean rho0 in FP32, 0 in FP64). cols: ncols descriptors (host). rho0: the columns' initial
  * densities concatenated, column c holding nx * ny_c doubles [y][x], in host or device
  * memory per rho0_where; the state is the rest equilibrium f_i^eq(rho0, 0). Each column
@@ -225,7 +247,7 @@ int lbm_batch_destroy(lbm_batch* b);
  * f_in, f_out: distinct DEVICE arrays of 9*nx*ny reals (float for LBM_FP32, double for
  *   LBM_FP64), layout [i][y][x] in the order of Eq. VelocitySet, holding the deviations
  *   f_i - w_i rho_ref with rho_ref = p->rho_ref (NaN means 0). Caller-owned; read / written.
- * p: as for lbm_init; p->workspace is ignored. stream: a cudaStream_t (NULL = default).
+ * p: as for lbm_init, isothermal (thermal = 0); p->workspace is ignored. stream: a cudaStream_t (NULL = default).
  * Scratch: the FP64 partial mass sums that give <rho> (Eq. Gravity_2) and a status word
  *   live in a file-scope __device__ array of 65 792 bytes inside liblbm, held by every
  *   device that loads the library until the process exits. Its 4096 partial slots bound

@@ -132,6 +132,9 @@ struct lbm_handle {
   double* ux = nullptr;
   double* uy = nullptr;
   double* rowmean = nullptr;
+  void* Tf = nullptr;    // thermal variant: temperature field real[ny][nx]
+  void* Tstar = nullptr; // Heun predictor and first stage rate (scratch)
+  void* Tk1 = nullptr;
   bool have_prev = false;
   int64_t steps = 0;
   lbm::StepTiling tiling{};
@@ -143,7 +146,7 @@ struct lbm_handle {
 namespace {
 
 struct Layout {
-  size_t f0, f1, parts0, parts1, status, red, rho_now, rho_prev, ux, uy, rowmean, total;
+  size_t f0, f1, parts0, parts1, status, red, rho_now, rho_prev, ux, uy, rowmean, Tf, Tstar, Tk1, total;
 };
 
 int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int variant = 0) {
@@ -201,6 +204,10 @@ Layout layout_for(const lbm_params& p, int P) {
   L.ux = take(N * 8);
   L.uy = take(N * 8);
   L.rowmean = take(size_t(p.ny) * 8);
+  const size_t nT = p.thermal ? N * s : 0;
+  L.Tf = take(nT);
+  L.Tstar = take(nT);
+  L.Tk1 = take(nT);
   L.total = o;
   return L;
 }
@@ -227,6 +234,12 @@ int validate(const lbm_params* p, char* err) {
   if (p->gravity_form != LBM_GRAVITY_RHO_G && p->gravity_form != LBM_GRAVITY_RHO_MINUS_MEAN_G) {
     set_err(err, "gravity_form must be LBM_GRAVITY_RHO_G or LBM_GRAVITY_RHO_MINUS_MEAN_G"); return LBM_EINVAL;
   }
+  if (p->thermal != 0 && p->thermal != 1) { set_err(err, "thermal must be 0 or 1"); return LBM_EINVAL; }
+  if (p->thermal && !(p->c_v > 0 && p->kappa >= 0 && p->T_bot > 0 && p->T_top > 0 && std::isfinite(p->c_v) &&
+                      std::isfinite(p->kappa) && std::isfinite(p->T_bot) && std::isfinite(p->T_top))) {
+    set_err(err, "thermal variant needs c_v > 0, kappa >= 0, T_bot > 0, T_top > 0");
+    return LBM_EINVAL;
+  }
   return LBM_OK;
 }
 
@@ -234,6 +247,7 @@ lbm::StepPhys phys_of(const lbm_params& p, double rho_ref) {
   lbm::StepPhys k{};
   k.rho_ref = rho_ref;
   k.RT = p.R * p.T;
+  k.R = p.R;
   k.a = p.a;
   k.b = p.b;
   k.G = p.G;
@@ -287,6 +301,7 @@ int refresh_partials(lbm_handle* h) {
 
 int run_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
   lbm::StepIO io{};
+  io.Tfield = h->Tf;
   io.fin = h->f[h->cur];
   io.part_in = h->parts[h->pcur];
   io.npart_in = h->npart;
@@ -324,6 +339,8 @@ void lbm_params_default(lbm_params* p) {
   p->tau_rho = p->tau_e = p->tau_varsigma = p->tau_j = p->tau_q = p->tau_nu = 1.0;
   p->gravity_form = LBM_GRAVITY_RHO_G;
   p->rho_ref = NAN;
+  p->c_v = 5.0;
+  p->kappa = 0.02;
 }
 
 int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes) {
@@ -397,6 +414,11 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
   h->ux = reinterpret_cast<double*>(base + L.ux);
   h->uy = reinterpret_cast<double*>(base + L.uy);
   h->rowmean = reinterpret_cast<double*>(base + L.rowmean);
+  if (p->thermal) {
+    h->Tf = base + L.Tf;
+    h->Tstar = base + L.Tstar;
+    h->Tk1 = base + L.Tk1;
+  }
 
   // initial density on the device (staged through the rho_now scratch when on the host)
   const double* rho_dev = rho0;
@@ -428,6 +450,8 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
 
   e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = lbm::launch_init(p->precision, rho_dev, h->f[0], p->nx, p->ny, rho_ref, h->stream);
+  if (e == cudaSuccess && p->thermal)
+    e = lbm::launch_linear_T(p->precision, p->nx, p->ny, p->T_bot, p->T_top, h->Tf, h->stream);
   if (e != cudaSuccess) { cuda_fail(h, e, "init kernel"); return fail(LBM_ECUDA); }
   h->cur = 0;
   h->pcur = 0;
@@ -443,17 +467,26 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (nsteps < 0) { set_err(h->err, "nsteps must be >= 0"); return LBM_EINVAL; }
   lbm::StepIO io{};
   io.status = h->status;
+  io.Tfield = h->Tf;
+  const lbm_params& p = h->p;
   for (int64_t t = 0; t < nsteps; ++t) {
     io.fin = h->f[h->cur];
     io.fout = h->f[1 - h->cur];
     io.part_in = h->parts[h->pcur];
     io.npart_in = h->npart;
     io.part_out = h->parts[1 - h->pcur];
-    LBM_CUDA(h, lbm::launch_step(h->p.precision, lbm::MODE_STEP, h->tiling, h->phys, io, h->stream));
+    LBM_CUDA(h, lbm::launch_step(p.precision, lbm::MODE_STEP, h->tiling, h->phys, io, h->stream));
     h->cur = 1 - h->cur;
     h->pcur = 1 - h->pcur;
     h->npart = h->P;
     ++h->steps;
+    if (p.thermal) {
+      // rho, u of the new populations with the force of T^n, then T^n -> T^(n+1)
+      int rc = run_moments(h, h->rho_now, h->ux, h->uy);
+      if (rc) return rc;
+      LBM_CUDA(h, lbm::launch_energy_step(p.precision, p.nx, p.ny, p.R, p.b, p.c_v, p.kappa, p.T_bot, p.T_top,
+                                          h->rho_now, h->ux, h->uy, h->Tf, h->Tstar, h->Tk1, h->stream));
+    }
   }
   return LBM_OK;
 }
@@ -568,13 +601,38 @@ int lbm_set_state(lbm_handle* h, const double* f, int where, int64_t steps_done)
   return LBM_OK;
 }
 
+int lbm_set_temperature(lbm_handle* h, const double* T, int where) {
+  if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
+  if (!h->Tf) { set_err(h->err, "the handle is isothermal (thermal = 0)"); return LBM_EINVAL; }
+  if (!T || (where != LBM_HOST && where != LBM_DEVICE)) { set_err(h->err, "bad T or where"); return LBM_EINVAL; }
+  const double* src = T;
+  if (where == LBM_HOST) {  // staged through ux
+    LBM_CUDA(h, cudaMemcpyAsync(h->ux, T, h->N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    src = h->ux;
+  }
+  LBM_CUDA(h, lbm::launch_plane_from_double(h->p.precision, src, h->Tf, h->N, 0.0, h->stream));
+  LBM_CUDA(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_get_temperature(lbm_handle* h, double* T, int where) {
+  if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
+  if (!h->Tf) { set_err(h->err, "the handle is isothermal (thermal = 0)"); return LBM_EINVAL; }
+  if (!T || (where != LBM_HOST && where != LBM_DEVICE)) { set_err(h->err, "bad T or where"); return LBM_EINVAL; }
+  double* dst = where == LBM_DEVICE ? T : h->ux;  // host path stages through ux
+  LBM_CUDA(h, lbm::launch_plane_to_double(h->p.precision, h->Tf, dst, h->N, 0.0, h->stream));
+  if (where == LBM_DEVICE) return LBM_OK;
+  LBM_CUDA(h, cudaMemcpyAsync(T, h->ux, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return device_status(h);
+}
+
 int lbm_set_params(lbm_handle* h, const lbm_params* p) {
   if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
   int rc = validate(p, h->err);
   if (rc) return rc;
   if (p->nx != h->p.nx || p->ny != h->p.ny || p->precision != h->p.precision || p->a != h->p.a || p->b != h->p.b ||
-      p->R != h->p.R) {
-    set_err(h->err, "nx, ny, precision, a, b and R cannot change on a live handle");
+      p->R != h->p.R || p->thermal != h->p.thermal) {
+    set_err(h->err, "nx, ny, precision, a, b, R and thermal cannot change on a live handle");
     return LBM_EINVAL;
   }
   const double rho_ref = h->p.rho_ref;
@@ -644,6 +702,7 @@ int lbm_autotune(lbm_handle* h, int steps, int* variant, double* ms) {
   io.npart_in = h->npart;
   io.part_out = h->parts[1 - h->pcur];
   io.status = h->status;
+  io.Tfield = h->Tf;
   for (int v = 0; v < lbm::step_num_variants(h->p.precision) && rc == LBM_OK; ++v) {
     lbm::StepTiling t;
     if (plan_tiling(h->p, h->nsm, &t, h->err, v)) continue;

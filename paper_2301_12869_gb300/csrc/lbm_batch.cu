@@ -66,6 +66,7 @@ __device__ lbm::PhysT<T> column_phys(const BatchArgs& a, const BatchCol& c) {
   lbm::PhysT<T> k;
   k.rho_ref = T(c.rho_ref);
   k.RT = T(c.RT);
+  k.R = T(0.0);  // unused: batched columns are isothermal
   k.a = T(a.a);
   k.b4 = T(a.b / 4.0);
   k.twoOverG = T(2.0 / a.G);
@@ -377,6 +378,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   char err[512];
   int rc = lbm::validate_params(&q, err);
   if (rc) return bfail(rc, err);
+  if (p->thermal) return bfail(LBM_EINVAL, "batched columns are isothermal (thermal must be 0)");
   if (p->nx > 64) return bfail(LBM_EINVAL, "batched columns are at most 64 nodes wide");
   if (rho0_where != LBM_HOST && rho0_where != LBM_DEVICE) return bfail(LBM_EINVAL, "rho0_where must be LBM_HOST or LBM_DEVICE");
   lbm_batch* b = new (std::nothrow) lbm_batch();

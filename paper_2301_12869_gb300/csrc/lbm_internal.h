@@ -17,7 +17,7 @@ enum : int { STATUS_NONPHYS = 1, STATUS_TIMEOUT = 2 };
 // Physical constants of one step, FP64 masters (converted to the kernel's real type).
 struct StepPhys {
   double rho_ref;          // populations are stored as g_i = f_i - w_i rho_ref
-  double RT, a, b;         // Eq. EOS: R T, a, b
+  double RT, R, a, b;      // Eq. EOS: R T, R, a, b
   double G;                // Eqs. ShanChenForce / InteractionPotential
   double s_e, s_vs, s_j, s_q, s_nu;   // diagonal of Lambda (Eq. RelaxationMatrix): 1/tau
   double sig_e, sig_vs;    // sigma/(tau_e - 1/2), sigma/(tau_varsigma - 1/2) of Eq. LiFS
@@ -46,6 +46,7 @@ struct StepIO {
   double* rho_out;         // MODE_MOMENTS outputs, [y][x] doubles (may be NULL)
   double* ux_out;
   double* uy_out;
+  const void* Tfield;      // thermal variant: real[ny][nx] temperature (NULL: uniform T)
 };
 
 // ---- launch wrappers (lbm_kernels.cu). All are asynchronous on `stream`.
@@ -75,6 +76,15 @@ cudaError_t launch_max_speed(const double* ux, const double* uy, size_t n, doubl
 cudaError_t launch_row_means(const double* rho, int nx, int ny, double* rowmean, cudaStream_t stream);
 // out[0] = first crossing height of rowmean through level (NaN if none); out[1] = max; out[2] = min
 cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, double* out, cudaStream_t stream);
+
+// ---- thermal variant (lbm_thermal.cu): Eq. Energy_Equation on a real[ny][nx] field
+// One Heun step (two launches): k1 = L(Tcur), Tstar = Tcur + k1, Tcur += (k1 + L(Tstar))/2,
+// with rho, ux, uy ([y][x] doubles) held fixed. Tstar and k1 are scratch fields.
+cudaError_t launch_energy_step(int precision, int nx, int ny, double R, double b, double c_v, double kappa,
+                               double T_bot, double T_top, const double* rho, const double* ux, const double* uy,
+                               void* Tcur, void* Tstar, void* k1, cudaStream_t stream);
+// Tf = T_bot + (T_top - T_bot)(y + 1/2)/ny
+cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, void* Tf, cudaStream_t stream);
 
 // ---- host helpers of lbm_api.cu shared with other entry points (same behaviour as lbm_init's)
 int validate_params(const lbm_params* p, char* err);  // err: 512 bytes

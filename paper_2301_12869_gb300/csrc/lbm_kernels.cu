@@ -134,6 +134,12 @@ __device__ __forceinline__ void pull(const float* st, int loc, bool lo_wall, boo
   g[8] = hi_wall ? aligned(8 * SW) : pair(8 * SW - 1);
 }
 
+// value(s) of a field at p: one node, or an aligned pair of nodes
+__device__ __forceinline__ float load_value(const float* p, float) { return *p; }
+__device__ __forceinline__ double load_value(const double* p, double) { return *p; }
+__device__ __forceinline__ f2 load_value(const float* p, f2) { return *reinterpret_cast<const f2*>(p); }
+__device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
 // ---- the fused step (MODE_STEP) / moments export (MODE_MOMENTS)
 //
 // Template parameters: storage type T, value type V (T, or f2 for pairs of FP32 nodes),
@@ -187,6 +193,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
   const T* fin = static_cast<const T*>(io.fin);
   T* fout = static_cast<T*>(io.fout);
+  const T* Tf = static_cast<const T*>(io.Tfield);  // thermal variant: local temperature
 
   // contiguous pieces of the periodic span [xa - H, xb + H): (global x, stage x, count)
   // piece 0 starts at the left halo; interior bands need only it
@@ -319,7 +326,8 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
           if (FULL || j <= w) {
             V g[9];
             pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
-            const V psi = psi_of<V>(k.rho_ref + sum9(g), k, flag);
+            const V RT = Tf ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
+            const V psi = psi_of<V>(k.rho_ref + sum9(g), RT, k, flag);
             if constexpr (VW == 1) {
               pr[j] = psi;
             } else {
@@ -338,9 +346,16 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
         T g[9];
         pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
         const T rho_h = sum9(g);
-        V rho_v;
-        if constexpr (VW == 1) rho_v = rho_h; else rho_v = make_f2(rho_h, rho_h);
-        const V psi = psi_of<V>(k.rho_ref + rho_v, k, flag);
+        const T Th = Tf ? Tf[size_t(q) * nx + wrap_x(xa + j - 1, nx)] : T(0);
+        V rho_v, T_v;
+        if constexpr (VW == 1) {
+          rho_v = rho_h;
+          T_v = Th;
+        } else {
+          rho_v = make_f2(rho_h, rho_h);
+          T_v = make_f2(Th, Th);
+        }
+        const V psi = psi_of<V>(k.rho_ref + rho_v, Tf ? k.R * T_v : k.RT, k, flag);
         if constexpr (VW == 1) pr[j] = psi; else pr[j] = lo(psi);
       }
     }
@@ -454,6 +469,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
   auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
   const T* fin = static_cast<const T*>(io.fin);
   T* fout = static_cast<T*>(io.fout);
+  const T* Tf = static_cast<const T*>(io.Tfield);  // thermal variant: local temperature
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -523,11 +539,13 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     PsiRow pm{0.f, cst<V>(0.0), 0.f}, p0 = pm, pp = pm;  // rows kk-2, kk-1, kk of the walk
     const V c13 = cst<V>(1.0 / 3.0), c112 = cst<V>(1.0 / 12.0);
 
-    auto scalar_psi = [&](const T* st, int jh, bool lo_wall, bool hi_wall) {
+    auto scalar_psi = [&](const T* st, int q, int jh, bool lo_wall, bool hi_wall) {
       T g[9];
       pull<SW>(st, jh - 1 + H, lo_wall, hi_wall, g);
       const T rh = sum9(g);
-      return lo(psi_of<V>(k.rho_ref + make_f2(rh, rh), k, flag));
+      const T Th = Tf ? Tf[size_t(q) * nx + wrap_x(xa + jh - 1, nx)] : T(0);
+      const V RT = Tf ? k.R * make_f2(Th, Th) : k.RT;
+      return lo(psi_of<V>(k.rho_ref + make_f2(rh, rh), RT, k, flag));
     };
     // g: the pulled populations of row y, kept in registers since its psi pass
     auto collide = [&](int y, const V (&g)[9], const PsiRow& ps, const PsiRow& pc, const PsiRow& pn) {
@@ -575,14 +593,19 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       if (active) pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
       float el = 0.f, er = 0.f;  // psi of the warp-edge neighbours (another warp's or the halo)
       if (need_l || need_r) {
-        const float v = scalar_psi(st, need_l ? j - 1 : j + 2, lo_wall, hi_wall);
+        const float v = scalar_psi(st, q, need_l ? j - 1 : j + 2, lo_wall, hi_wall);
         if (need_l) el = v; else er = v;
-        if (need_l && need_r) er = scalar_psi(st, j + 2, lo_wall, hi_wall);
+        if (need_l && need_r) er = scalar_psi(st, q, j + 2, lo_wall, hi_wall);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);  // this warp has read everything it needs of row kk
       PsiRow nw;
-      nw.c = active ? psi_of<V>(k.rho_ref + sum9(g), k, flag) : cst<V>(0.0);
+      if (active) {
+        const V RT = Tf ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
+        nw.c = psi_of<V>(k.rho_ref + sum9(g), RT, k, flag);
+      } else {
+        nw.c = cst<V>(0.0);
+      }
       nw.l = __shfl_up_sync(0xffffffffu, hi(nw.c), 1);
       nw.r = __shfl_down_sync(0xffffffffu, lo(nw.c), 1);
       if (need_l) nw.l = el;

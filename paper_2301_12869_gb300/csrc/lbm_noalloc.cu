@@ -46,6 +46,7 @@ extern "C" int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_o
   char err[512];
   int rc = lbm::validate_params(p, err);
   if (rc) return fail(rc, err);
+  if (p->thermal) return fail(LBM_EINVAL, "lbm_step_noalloc is isothermal (thermal must be 0)");
   if (!f_in || !f_out || f_in == f_out) return fail(LBM_EINVAL, "f_in and f_out must be distinct device arrays");
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

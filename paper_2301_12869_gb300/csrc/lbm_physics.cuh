@@ -31,7 +31,7 @@ __host__ __device__ constexpr double w_of(int i) { return i == 0 ? 4.0 / 9.0 : (
 // Physical constants of a step in the value type V (a pair holds the same constant twice).
 template <typename V>
 struct PhysT {
-  V rho_ref, RT, a, b4, twoOverG, negG, G2;
+  V rho_ref, RT, R, a, b4, twoOverG, negG, G2;
   V s_e, s_vs, s_j, s_q, s_nu;      // Lambda entries (general relaxation only)
   V h_e, h_vs, h_j, h_q, h_nu;      // 1 - s/2 (diagonal of I - Lambda/2)
   V sig_e, nsig_vs;                 // sigma/(tau_e - 1/2), -sigma/(tau_varsigma - 1/2)
@@ -59,6 +59,7 @@ PhysT<V> to_phys(const StepPhys& p) {
   PhysT<V> k;
   k.rho_ref = c(p.rho_ref);
   k.RT = c(p.RT);
+  k.R = c(p.R);
   k.a = c(p.a);
   k.b4 = c(p.b / 4.0);
   k.twoOverG = c(2.0 / p.G);
@@ -129,16 +130,21 @@ __device__ __forceinline__ double warp_sum_partials(const double* part, int n) {
 
 // Eq. EOS (Carnahan-Starling) and Eq. InteractionPotential with c = 1, c_s^2 = 1/3.
 template <typename V>
-__device__ __forceinline__ V psi_of(V rho, const PhysT<V>& k, int& flag) {
+__device__ __forceinline__ V psi_of(V rho, V RT, const PhysT<V>& k, int& flag) {
   const V one = cst<V>(1.0);
   const V eta = k.b4 * rho;
   const V om = one - eta;
   const V num = fmadd(eta, fmadd(eta, om, one), one);  // 1 + eta + eta^2 - eta^3
-  const V p = fast_div(rho * k.RT * num, om * om * om) - k.a * rho * rho;
+  const V p = fast_div(rho * RT * num, om * om * om) - k.a * rho * rho;
   bool bad = false;
   const V psi = sqrt_checked(k.twoOverG * fmadd(rho, cst<V>(-1.0 / 3.0), p), bad);
   if (bad) flag |= STATUS_NONPHYS;  // 2 (p_EOS - rho/3)/G < 0 or NaN: psi undefined
   return psi;
+}
+// isothermal: R T of the parameters
+template <typename V>
+__device__ __forceinline__ V psi_of(V rho, const PhysT<V>& k, int& flag) {
+  return psi_of(rho, k.RT, k, flag);
 }
 
 template <typename V>

@@ -38,7 +38,7 @@ EXPORTS = (
     "lbm_params_default", "lbm_workspace_bytes", "lbm_init", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
     "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
-    "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling",
+    "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
     "lbm_batch_init", "lbm_batch_run", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
     "lbm_batch_convert", "lbm_batch_destroy",
 )
@@ -52,8 +52,9 @@ class lbm_params(ctypes.Structure):
         ("tau_rho", ctypes.c_double), ("tau_e", ctypes.c_double), ("tau_varsigma", ctypes.c_double),
         ("tau_j", ctypes.c_double), ("tau_q", ctypes.c_double), ("tau_nu", ctypes.c_double),
         ("gx", ctypes.c_double), ("gy", ctypes.c_double),
-        ("gravity_form", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("gravity_form", ctypes.c_int32), ("thermal", ctypes.c_int32),
         ("rho_ref", ctypes.c_double), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
+        ("c_v", ctypes.c_double), ("kappa", ctypes.c_double), ("T_bot", ctypes.c_double), ("T_top", ctypes.c_double),
     ]
 
 
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
         "lbm_autotune": (i32, [vp, i32, P(i32), P(d)]),
         "lbm_tile_variants": (i32, [i32]),
         "lbm_set_tiling": (i32, [vp, i32]),
+        "lbm_set_temperature": (i32, [vp, vp, i32]),
+        "lbm_get_temperature": (i32, [vp, vp, i32]),
         "lbm_batch_init": (i32, [P(lbm_params), P(lbm_column), i32, vp, i32, vp, P(vp)]),
         "lbm_batch_run": (i32, [vp, d, i64, i32, P(d)]),
         "lbm_batch_results": (i32, [vp, vp, vp, vp]),
@@ -192,6 +195,16 @@ def lbm_get_state(h, f):
 def lbm_set_state(h, f, steps_done=0):
     addr, where = _ptr(f)
     _check(load().lbm_set_state(h, addr, where, int(steps_done)), h)
+
+
+def lbm_set_temperature(h, T):
+    addr, where = _ptr(T)
+    _check(load().lbm_set_temperature(h, addr, where), h)
+
+
+def lbm_get_temperature(h, T):
+    addr, where = _ptr(T)
+    _check(load().lbm_get_temperature(h, addr, where), h)
 
 
 def lbm_set_params(h, p):
@@ -363,6 +376,12 @@ class Lattice:
 
     def set_state(self, f, steps_done=0):
         lbm_set_state(self.h, np.ascontiguousarray(f, dtype=np.float64), steps_done)
+
+    def temperature(self):
+        t = self._torch
+        T = t.empty((self.ny, self.nx), dtype=t.float64, device=self._ws.device)
+        lbm_get_temperature(self.h, T)
+        return T
 
     def status(self):
         return lbm_status(self.h)

@@ -42,6 +42,8 @@ def test_params_struct_layout_matches(lib):
     assert (p.a, p.b, p.R, p.sigma, p.G) == (0.5, 4.0, 1.0, 1.385, -1.0)
     assert all(getattr(p, t) == 1.0 for t in ("tau_rho", "tau_e", "tau_varsigma", "tau_j", "tau_q", "tau_nu"))
     assert math.isnan(p.rho_ref)
+    # isothermal by default; c_v = 5 and kappa = 0.02 of Sec. IV for the thermal variant
+    assert p.thermal == 0 and (p.c_v, p.kappa) == (5.0, 0.02)
 
 
 @pytest.mark.parametrize(
@@ -54,6 +56,10 @@ def test_params_struct_layout_matches(lib):
         (dict(gravity_form=3), "gravity_form"),
         (dict(size=8), "params.size"),
         (dict(T=-1.0), "T > 0"),
+        (dict(thermal=2), "thermal must be 0 or 1"),
+        (dict(thermal=1), "T_bot > 0"),  # wall temperatures unset
+        (dict(thermal=1, T_bot=0.02, T_top=0.02, c_v=0.0), "c_v > 0"),
+        (dict(thermal=1, T_bot=0.02, T_top=0.02, kappa=-1.0), "kappa >= 0"),
     ],
 )
 def test_init_rejects_bad_parameters(lib, change, fragment):
