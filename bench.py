@@ -306,6 +306,143 @@ def run_columns(args):
     return 0
 
 
+# ---------------------------------------------------------------- thermal variant
+TH_NX, TH_NY, TH_LIQUID = 512, 2048, 1024
+TH_TBOT, TH_TTOP, TH_GY = 0.95, 0.80, -5e-5
+# per node and step, as launched: fused step 72 B populations + 4 B T; moments pass 36 B
+# populations + 4 B T read, 24 B rho/u written; Heun kernel 4 B T + 24 B rho/u read, 4 B T
+# written (FP32 storage, FP64 rho and u; FP64 storage doubles the population and T terms)
+TH_BYTES_PER_NODE = {"fp32": 76 + 64 + 32, "fp64": 152 + 104 + 40}
+# The heated column goes non-physical: its 1024 vapour rows weigh more than the vapour's
+# saturation pressure can carry at g_y = -5e-5 (scale height of the vapour ~100 rows), so
+# the vapour falls freely and the top empties (max |u| = |g| t) within ~5000 steps. Timed
+# runs restore the post-warm-up populations and temperature every TH_WINDOW steps.
+TH_WINDOW = 1000
+
+
+def thermal_setup(precision, lbm, inputs):
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    T_mid = TH_TBOT + (TH_TTOP - TH_TBOT) * TH_LIQUID / TH_NY  # conduction profile at the interface
+    rv, rl, _ = lbm.lbm_coexistence(A, B, R, T_mid * Tc)
+    rho0 = inputs.column_rho0(TH_NX, TH_NY, rl, rv, TH_LIQUID, noise_amp=NOISE, seed=SEED)
+    p = lbm.make_params(TH_NX, TH_NY, T_mid * Tc, precision, a=A, b=B, R=R, form=1, g=(0.0, TH_GY), thermal=1,
+                        T_bot=TH_TBOT * Tc, T_top=TH_TTOP * Tc)
+    return p, rho0, Tc
+
+
+_LEVELS = {}
+
+
+def coexistence_midpoint(lbm, T, Tc):
+    """(rho_l + rho_v)/2 of the Maxwell rule at T, interpolated from 400 temperatures."""
+    import numpy as np
+
+    if "T" not in _LEVELS:
+        grid = np.linspace(0.70, 0.999, 400) * Tc
+        _LEVELS["T"] = grid
+        _LEVELS["mid"] = np.array([0.5 * sum(lbm.lbm_coexistence(A, B, R, t)[:2]) for t in grid])
+    return np.interp(T, _LEVELS["T"], _LEVELS["mid"])
+
+
+def crossing_heights(lbm, h, Tc):
+    """Heights (from the bottom wall, linear interpolation of the x-averaged profiles) where
+    rho crosses the level halfway between the coexistence densities at the row's mean T:
+    the first is the top of the liquid at the bottom wall (the nucleation height once a
+    vapour layer forms there)."""
+    import numpy as np
+
+    rho = np.empty((TH_NY, TH_NX))
+    T = np.empty((TH_NY, TH_NX))
+    lbm.lbm_moments(h, rho)
+    lbm.lbm_get_temperature(h, T)
+    rbar, Tbar = rho.mean(axis=1), T.mean(axis=1)
+    d = rbar - coexistence_midpoint(lbm, Tbar, Tc)
+    out = []
+    for y in range(TH_NY - 1):
+        if (d[y] > 0) != (d[y + 1] > 0):
+            out.append(y + d[y] / (d[y] - d[y + 1]))
+    return out
+
+
+def run_thermal(args, torch, lbm, inputs):
+    """Throughput of the thermal step (fused LBM step with T(x) in psi, moments pass, two
+    Heun stages of the energy equation) on the 512 x 2048 heated-from-below column; with
+    --thermal-track, config 4 in full (FP32 and FP64, --thermal-steps steps) with the
+    liquid/vapour crossing heights every --thermal-every steps."""
+    import numpy as np
+
+    p, rho0, Tc = thermal_setup(args.precision, lbm, inputs)
+    nodes = TH_NX * TH_NY
+    lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
+    lat.step(args.warmup)
+    snap_f = torch.empty((9, TH_NY, TH_NX), dtype=torch.float64, device="cuda")
+    snap_T = torch.empty((TH_NY, TH_NX), dtype=torch.float64, device="cuda")
+    lbm.lbm_get_state(lat.h, snap_f)
+    lbm.lbm_get_temperature(lat.h, snap_T)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    restores = 0
+    with ClockSampler(0) as clocks:
+        start.record(stream)
+        done = 0
+        while done < args.steps:
+            n = min(TH_WINDOW, args.steps - done)
+            lat.step(n)
+            done += n
+            if done < args.steps:
+                lbm.lbm_set_state(lat.h, snap_f)
+                lbm.lbm_set_temperature(lat.h, snap_T)
+                restores += 1
+        end.record(stream)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    status = lat.status()
+    lat.close()
+    del lat
+    peaks, peak_kind = measured_peaks()
+    step_s = ms / 1e3 / args.steps
+    bytes_step = TH_BYTES_PER_NODE[args.precision] * nodes
+    line = {
+        "metric": "MLUPS (thermal step)", "value": nodes * args.steps / (ms / 1e3) / 1e6, "unit": "MLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic", "impl": "gb300",
+        "config": {"workload": f"thermal liquid column {TH_NX}x{TH_NY}, heated from below", "T_bot_over_Tc": TH_TBOT,
+                   "T_top_over_Tc": TH_TTOP, "gravity": "rho g", "g_y": TH_GY, "liquid_rows": TH_LIQUID,
+                   "c_v": p.c_v, "kappa": p.kappa, "noise": NOISE, "seed": SEED,
+                   "l2": "state 151 MB (FP32) > 129 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": bytes_step / step_s / 1e9 / peaks["hbm_gbs"], "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "whole thermal step (fused step, moments, Heun: 3 launches)",
+                     "bytes_per_node": TH_BYTES_PER_NODE[args.precision]},
+        "gpu_launches": 3 * args.steps + restores * (9 + 1 + 1), "restores": restores,
+        "physical_window": f"populations and T restored from the post-warm-up snapshot every {TH_WINDOW} steps",
+        "clocks": clocks.summary(), "status": status,
+    }
+    if args.thermal_track:
+        track = {}
+        for prec in ("fp32", "fp64"):
+            q, rho0, Tc = thermal_setup(prec, lbm, inputs)
+            h = lbm.lbm_init(q, rho0)
+            rows, t0 = [], time.perf_counter()
+            done = 0
+            while done < args.thermal_steps:
+                n = min(args.thermal_every, args.thermal_steps - done)
+                lbm.lbm_step(h, n)
+                done += n
+                st = lbm.lbm_status(h)
+                rows.append({"step": done, "status": st, "max_u": lbm.lbm_reduce(h, lbm.LBM_REDUCE_MAX_U, check=False)[0][0],
+                             "crossings": [round(c, 3) for c in crossing_heights(lbm, h, Tc)] if st == 0 else None})
+                if st != 0:
+                    break
+            track[prec] = {"seconds": time.perf_counter() - t0, "samples": rows}
+            lbm.lbm_destroy(h)
+        line["track"] = track
+    print(json.dumps(line), flush=True)
+    return 0 if status == 0 else 2
+
+
 # ---------------------------------------------------------------- main
 def run_reference(args, world, rank):
     if rank != 0:
@@ -336,9 +473,13 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
-    ap.add_argument("--workload", choices=["domain", "columns"], default="domain",
+    ap.add_argument("--workload", choices=["domain", "columns", "thermal"], default="domain",
                     help="domain: the 1024 x 4096 single-domain throughput line (default); "
-                         "columns: time to steady state of batched columns")
+                         "columns: time to steady state of batched columns; "
+                         "thermal: the 512 x 2048 thermal column")
+    ap.add_argument("--thermal-track", action="store_true")
+    ap.add_argument("--thermal-steps", type=int, default=8000)
+    ap.add_argument("--thermal-every", type=int, default=500)
     ap.add_argument("--columns", type=int, default=1024)
     ap.add_argument("--column-heights", default="64,128")
     ap.add_argument("--column-max-steps", type=int, default=200000)
@@ -361,6 +502,8 @@ def main(argv=None):
         print(json.dumps({"error": "no CUDA device"}))
         return 1
     torch.cuda.set_device(local)
+    if args.workload == "thermal":
+        return run_thermal(args, torch, lbm, inputs) if rank == 0 else 0
     if world > 1:
         import torch.distributed as dist
 

@@ -172,14 +172,16 @@ int lbm_launch_info(const lbm_handle* h, int* grid, int* block, int* smem_bytes,
  * CTA) for `steps` launches on this lattice - every candidate reads the current state and
  * writes the spare buffer, so the state is unchanged - and keeps the fastest for later
  * lbm_step / lbm_moments calls. variant, ms (mean time per step of the winner): may be NULL.
- * Synchronises the handle's stream. */
+ * A thermal handle considers only the variants that carry thermal kernels (variant 0 of
+ * each precision). Synchronises the handle's stream. */
 int lbm_autotune(lbm_handle* h, int steps, int* variant, double* ms);
 
 /* Number of tile variants of the fused kernel for a precision (LBM_EINVAL otherwise). */
 int lbm_tile_variants(int precision);
 
 /* Use tile variant `variant` (0 = default, as chosen by lbm_init) for later steps, e.g. a
- * result of lbm_autotune saved from an earlier run. LBM_EINVAL if out of range. */
+ * result of lbm_autotune saved from an earlier run. LBM_EINVAL if out of range, or if the
+ * handle is thermal and the variant has no thermal kernels (only variant 0 has). */
 int lbm_set_tiling(lbm_handle* h, int variant);
 
 /* ---- batched independent columns: the 1-D liquid-column problem of Sec. IV for many

@@ -133,8 +133,7 @@ struct lbm_handle {
   double* uy = nullptr;
   double* rowmean = nullptr;
   void* Tf = nullptr;    // thermal variant: temperature field real[ny][nx]
-  void* Tstar = nullptr; // Heun predictor and first stage rate (scratch)
-  void* Tk1 = nullptr;
+  void* Tnext = nullptr; // the field after the next energy step (swapped with Tf)
   bool have_prev = false;
   int64_t steps = 0;
   lbm::StepTiling tiling{};
@@ -146,7 +145,7 @@ struct lbm_handle {
 namespace {
 
 struct Layout {
-  size_t f0, f1, parts0, parts1, status, red, rho_now, rho_prev, ux, uy, rowmean, Tf, Tstar, Tk1, total;
+  size_t f0, f1, parts0, parts1, status, red, rho_now, rho_prev, ux, uy, rowmean, Tf, Tnext, total;
 };
 
 int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int variant = 0) {
@@ -154,6 +153,10 @@ int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int
   int bw_max = 0;
   if (!lbm::step_variant_info(p.precision, variant, &bw_max, &t->threads, &t->smem_bytes)) {
     set_err(err, "unknown tile variant %d", variant);
+    return LBM_EINVAL;
+  }
+  if (p.thermal && !lbm::step_variant_thermal(p.precision, variant)) {
+    set_err(err, "tile variant %d has no thermal kernels", variant);
     return LBM_EINVAL;
   }
   t->variant = variant;
@@ -181,6 +184,7 @@ int max_partials(const lbm_params& p, int nsm, char* err) {
   int P = 0;
   for (int v = 0; v < lbm::step_num_variants(p.precision); ++v) {
     lbm::StepTiling t;
+    if (p.thermal && !lbm::step_variant_thermal(p.precision, v)) continue;
     if (plan_tiling(p, nsm, &t, err, v)) return -1;
     P = std::max(P, t.nbands * t.nstrips);
   }
@@ -206,8 +210,7 @@ Layout layout_for(const lbm_params& p, int P) {
   L.rowmean = take(size_t(p.ny) * 8);
   const size_t nT = p.thermal ? N * s : 0;
   L.Tf = take(nT);
-  L.Tstar = take(nT);
-  L.Tk1 = take(nT);
+  L.Tnext = take(nT);
   L.total = o;
   return L;
 }
@@ -352,6 +355,13 @@ int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes) {
     set_err(g_err, "no CUDA device");
     return LBM_ECUDA;
   }
+  // the grid plan depends on the occupancy the kernels reach with their shared-memory
+  // limit set, as in lbm_init
+  const cudaError_t e = lbm::step_prepare(p->precision);
+  if (e != cudaSuccess) {
+    set_err(g_err, "kernel attributes: %s", cudaGetErrorString(e));
+    return LBM_ECUDA;
+  }
   lbm::StepTiling t;
   if ((rc = plan_tiling(*p, nsm, &t, g_err))) return rc;
   const int cap = max_partials(*p, nsm, g_err);
@@ -416,8 +426,7 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
   h->rowmean = reinterpret_cast<double*>(base + L.rowmean);
   if (p->thermal) {
     h->Tf = base + L.Tf;
-    h->Tstar = base + L.Tstar;
-    h->Tk1 = base + L.Tk1;
+    h->Tnext = base + L.Tnext;
   }
 
   // initial density on the device (staged through the rho_now scratch when on the host)
@@ -467,9 +476,9 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (nsteps < 0) { set_err(h->err, "nsteps must be >= 0"); return LBM_EINVAL; }
   lbm::StepIO io{};
   io.status = h->status;
-  io.Tfield = h->Tf;
   const lbm_params& p = h->p;
   for (int64_t t = 0; t < nsteps; ++t) {
+    io.Tfield = h->Tf;
     io.fin = h->f[h->cur];
     io.fout = h->f[1 - h->cur];
     io.part_in = h->parts[h->pcur];
@@ -485,7 +494,8 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
       int rc = run_moments(h, h->rho_now, h->ux, h->uy);
       if (rc) return rc;
       LBM_CUDA(h, lbm::launch_energy_step(p.precision, p.nx, p.ny, p.R, p.b, p.c_v, p.kappa, p.T_bot, p.T_top,
-                                          h->rho_now, h->ux, h->uy, h->Tf, h->Tstar, h->Tk1, h->stream));
+                                          h->rho_now, h->ux, h->uy, h->Tf, h->Tnext, h->stream));
+      std::swap(h->Tf, h->Tnext);
     }
   }
   return LBM_OK;

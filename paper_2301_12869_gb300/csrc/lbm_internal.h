@@ -52,6 +52,7 @@ struct StepIO {
 // ---- launch wrappers (lbm_kernels.cu). All are asynchronous on `stream`.
 int stages();  // pipeline depth of the fused kernel
 int step_num_variants(int precision);
+bool step_variant_thermal(int precision, int variant);  // has thermal kernels (io.Tfield set)
 // widest x band one CTA covers, threads per CTA, dynamic shared bytes of a tile variant
 bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem);
 int step_max_ctas_per_sm(int precision, int variant, int threads, int smem_bytes);
@@ -78,11 +79,11 @@ cudaError_t launch_row_means(const double* rho, int nx, int ny, double* rowmean,
 cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, double* out, cudaStream_t stream);
 
 // ---- thermal variant (lbm_thermal.cu): Eq. Energy_Equation on a real[ny][nx] field
-// One Heun step (two launches): k1 = L(Tcur), Tstar = Tcur + k1, Tcur += (k1 + L(Tstar))/2,
-// with rho, ux, uy ([y][x] doubles) held fixed. Tstar and k1 are scratch fields.
+// One Heun step in one launch: Tout = Tin + (k1 + k2)/2 with k1 = L(Tin), k2 = L(Tin + k1),
+// rho, ux, uy ([y][x] doubles) held fixed. Tin and Tout are distinct real[ny][nx] fields.
 cudaError_t launch_energy_step(int precision, int nx, int ny, double R, double b, double c_v, double kappa,
                                double T_bot, double T_top, const double* rho, const double* ux, const double* uy,
-                               void* Tcur, void* Tstar, void* k1, cudaStream_t stream);
+                               const void* Tin, void* Tout, cudaStream_t stream);
 // Tf = T_bot + (T_top - T_bot)(y + 1/2)/ny
 cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, void* Tf, cudaStream_t stream);
 

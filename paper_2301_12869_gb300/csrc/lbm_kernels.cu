@@ -145,11 +145,11 @@ __device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (
 // Template parameters: storage type T, value type V (T, or f2 for pairs of FP32 nodes),
 // mode, all-unit relaxation, band width BW (nodes along x per CTA), nodes per thread NPT
 // (threads = BW / NPT; a thread owns NPT / width(V) values), CTAs per SM the launch
-// bounds aim for.
+// bounds aim for; TH: thermal variant, psi uses R T(x) of the field io.Tfield (else R T).
 // CTA b: x band (b % nbands) of width tl.band_w (<= BW), strip (b / nbands) of
 // tl.strip_h rows. Even strips walk their rows upward, odd strips downward, so two
 // neighbouring strips reach their common halo rows at the same time (L2 reuse).
-template <typename T, typename V, int MODE, bool UNIT, int BW, int NPT, int MINB>
+template <typename T, typename V, int MODE, bool UNIT, int BW, int NPT, int MINB, bool TH = false>
 __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling tl, const PhysT<V> k, const StepIO io) {
   constexpr int NT = BW / NPT;
   constexpr int VW = VecTraits<V>::width;  // nodes per value
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
   const T* fin = static_cast<const T*>(io.fin);
   T* fout = static_cast<T*>(io.fout);
-  const T* Tf = static_cast<const T*>(io.Tfield);  // thermal variant: local temperature
+  const T* Tf = TH ? static_cast<const T*>(io.Tfield) : nullptr;  // thermal variant: local temperature
 
   // contiguous pieces of the periodic span [xa - H, xb + H): (global x, stage x, count)
   // piece 0 starts at the left halo; interior bands need only it
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
           if (FULL || j <= w) {
             V g[9];
             pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
-            const V RT = Tf ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
+            const V RT = TH ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
             const V psi = psi_of<V>(k.rho_ref + sum9(g), RT, k, flag);
             if constexpr (VW == 1) {
               pr[j] = psi;
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
         T g[9];
         pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
         const T rho_h = sum9(g);
-        const T Th = Tf ? Tf[size_t(q) * nx + wrap_x(xa + j - 1, nx)] : T(0);
+        const T Th = TH ? Tf[size_t(q) * nx + wrap_x(xa + j - 1, nx)] : T(0);
         V rho_v, T_v;
         if constexpr (VW == 1) {
           rho_v = rho_h;
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
           rho_v = make_f2(rho_h, rho_h);
           T_v = make_f2(Th, Th);
         }
-        const V psi = psi_of<V>(k.rho_ref + rho_v, Tf ? k.R * T_v : k.RT, k, flag);
+        const V psi = psi_of<V>(k.rho_ref + rho_v, TH ? k.R * T_v : k.RT, k, flag);
         if constexpr (VW == 1) pr[j] = psi; else pr[j] = lo(psi);
       }
     }
@@ -427,7 +427,7 @@ struct PsiRow {  // psi at the left neighbour, the lane's own pair, the right ne
   float r;
 };
 
-template <int MODE, bool UNIT, int NWC, int S, int MINB>
+template <int MODE, bool UNIT, int NWC, int S, int MINB, bool TH = false>
 __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     step_kernel_ws(const StepTiling tl, const PhysT<f2> k, const StepIO io) {
   using T = float;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
   auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
   const T* fin = static_cast<const T*>(io.fin);
   T* fout = static_cast<T*>(io.fout);
-  const T* Tf = static_cast<const T*>(io.Tfield);  // thermal variant: local temperature
+  const T* Tf = TH ? static_cast<const T*>(io.Tfield) : nullptr;  // thermal variant: local temperature
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -543,8 +543,8 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       T g[9];
       pull<SW>(st, jh - 1 + H, lo_wall, hi_wall, g);
       const T rh = sum9(g);
-      const T Th = Tf ? Tf[size_t(q) * nx + wrap_x(xa + jh - 1, nx)] : T(0);
-      const V RT = Tf ? k.R * make_f2(Th, Th) : k.RT;
+      const T Th = TH ? Tf[size_t(q) * nx + wrap_x(xa + jh - 1, nx)] : T(0);
+      const V RT = TH ? k.R * make_f2(Th, Th) : k.RT;
       return lo(psi_of<V>(k.rho_ref + make_f2(rh, rh), RT, k, flag));
     };
     // g: the pulled populations of row y, kept in registers since its psi pass
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       if (lane == 0) mbar_arrive(&empty[s]);  // this warp has read everything it needs of row kk
       PsiRow nw;
       if (active) {
-        const V RT = Tf ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
+        const V RT = TH ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
         nw.c = psi_of<V>(k.rho_ref + sum9(g), RT, k, flag);
       } else {
         nw.c = cst<V>(0.0);
@@ -777,11 +777,13 @@ struct VariantF {  // FP32 storage; `paired` variants evaluate two nodes per val
   StepFnF step, step_unit, moments;      // scalar variants
   StepFnP pstep, pstep_unit, pmoments;   // paired variants
   size_t smem;
+  StepFnP th_step = nullptr, th_step_unit = nullptr, th_moments = nullptr;  // thermal (paired)
 };
 struct VariantD {
   int bw, threads;
   StepFnD step, step_unit, moments;
   size_t smem;
+  StepFnD th_step = nullptr, th_step_unit = nullptr, th_moments = nullptr;  // thermal
 };
 
 template <int BW, int NPT, int MINB>
@@ -805,6 +807,15 @@ constexpr VariantD make_d() {
                   step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
 }
+// the same tile with the thermal kernels as well
+template <int BW, int NPT, int MINB>
+constexpr VariantD make_d_th() {
+  VariantD v = make_d<BW, NPT, MINB>();
+  v.th_step = step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB, true>;
+  v.th_step_unit = step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB, true>;
+  v.th_moments = step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB, true>;
+  return v;
+}
 
 template <int NWC, int S, int MINB>
 constexpr VariantF make_ws() {
@@ -812,9 +823,17 @@ constexpr VariantF make_ws() {
                   step_kernel_ws<MODE_STEP, false, NWC, S, MINB>, step_kernel_ws<MODE_STEP, true, NWC, S, MINB>,
                   step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB>, ws_smem<NWC, S>()};
 }
+template <int NWC, int S, int MINB>
+constexpr VariantF make_ws_th() {
+  VariantF v = make_ws<NWC, S, MINB>();
+  v.th_step = step_kernel_ws<MODE_STEP, false, NWC, S, MINB, true>;
+  v.th_step_unit = step_kernel_ws<MODE_STEP, true, NWC, S, MINB, true>;
+  v.th_moments = step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB, true>;
+  return v;
+}
 
 const VariantF kVariantsF[] = {
-    make_ws<8, 4, 2>(),      // barrier-free: 8 consumer warps + producer, 4 stages, 75 KB
+    make_ws_th<8, 4, 2>(),   // barrier-free: 8 consumer warps + producer, 4 stages, 75 KB (+ thermal)
     make_ws<4, 4, 4>(),      // barrier-free: 4 consumer warps + producer, 4 stages, 38 KB
     make_p<256, 2, 5>(),     // pairs, 4 warps, 42 KB shared, one CTA barrier per row
     make_f<256, 2, 5>(),     // scalar, 4 warps, 42 KB shared, one CTA barrier per row
@@ -823,7 +842,7 @@ const VariantF kVariantsF[] = {
     make_ws<2, 6, 6>(),      // barrier-free, 2 consumer warps, 29 KB
 };
 const VariantD kVariantsD[] = {
-    make_d<128, 1, 4>(),
+    make_d_th<128, 1, 4>(),  // (+ thermal)
     make_d<64, 1, 8>(),
 };
 constexpr int kNumF = sizeof(kVariantsF) / sizeof(kVariantsF[0]);
@@ -838,13 +857,13 @@ cudaError_t prepare_variant(const VariantF& v) {
   cudaError_t e = cudaSuccess;
   for (auto fn : {v.step, v.step_unit, v.moments})
     if (e == cudaSuccess) e = set_smem(fn, v.smem);
-  for (auto fn : {v.pstep, v.pstep_unit, v.pmoments})
+  for (auto fn : {v.pstep, v.pstep_unit, v.pmoments, v.th_step, v.th_step_unit, v.th_moments})
     if (e == cudaSuccess) e = set_smem(fn, v.smem);
   return e;
 }
 cudaError_t prepare_variant(const VariantD& v) {
   cudaError_t e = cudaSuccess;
-  for (auto fn : {v.step, v.step_unit, v.moments})
+  for (auto fn : {v.step, v.step_unit, v.moments, v.th_step, v.th_step_unit, v.th_moments})
     if (e == cudaSuccess) e = set_smem(fn, v.smem);
   return e;
 }
@@ -866,6 +885,11 @@ int grid_for(size_t n, int block) {
 int stages() { return kStages; }
 
 int step_num_variants(int precision) { return precision == 1 ? kNumF : kNumD; }
+
+bool step_variant_thermal(int precision, int variant) {
+  if (variant < 0 || variant >= step_num_variants(precision)) return false;
+  return precision == 1 ? kVariantsF[variant].th_step != nullptr : kVariantsD[variant].th_step != nullptr;
+}
 
 bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem) {
   if (variant < 0 || variant >= step_num_variants(precision)) return false;
@@ -909,9 +933,14 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
                         cudaStream_t stream) {
   const dim3 grid(t.nbands * t.nstrips), block(t.threads);
   const bool unit = unit_relaxation(ph);
+  const bool th = io.Tfield != nullptr;
   if (precision == 1) {
     const VariantF& v = kVariantsF[t.variant];
-    if (v.paired) {
+    if (th) {
+      const StepFnP fn = mode == MODE_MOMENTS ? v.th_moments : (unit ? v.th_step_unit : v.th_step);
+      if (!fn) return cudaErrorInvalidValue;  // no thermal kernels for this tile variant
+      fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<f2>(ph), io);
+    } else if (v.paired) {
       const StepFnP fn = mode == MODE_MOMENTS ? v.pmoments : (unit ? v.pstep_unit : v.pstep);
       fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<f2>(ph), io);
     } else {
@@ -920,7 +949,9 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
     }
   } else {
     const VariantD& v = kVariantsD[t.variant];
-    const StepFnD fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
+    const StepFnD fn = th ? (mode == MODE_MOMENTS ? v.th_moments : (unit ? v.th_step_unit : v.th_step))
+                          : (mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step));
+    if (!fn) return cudaErrorInvalidValue;  // no thermal kernels for this tile variant
     fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<double>(ph), io);
   }
   return cudaGetLastError();

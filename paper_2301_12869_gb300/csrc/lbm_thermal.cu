@@ -8,6 +8,11 @@
 // dt = 1, and Dirichlet walls half a link beyond the first and last rows (ghost rows
 // T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top). rho and u come from the
 // moments pass that follows each LBM step.
+//
+// One launch does the whole Heun step. A CTA owns a TX x TY tile of nodes and stages T, u
+// with a halo of two nodes and rho with a halo of one in shared memory: stage 1 (k1,
+// T* = T + k1) runs on the tile plus its one-node ring, stage 2 (k2) on the tile, so no
+// grid-wide barrier separates the stages. The new field goes to a second buffer.
 #include "lbm_internal.h"
 #include "lbm_physics.cuh"
 
@@ -16,75 +21,110 @@
 namespace lbm {
 namespace {
 
-struct EnergyArgs {
-  int nx, ny;
-  double R, b, c_v, kappa, T_bot, T_top;
-};
+constexpr int TX = 32, TY = 8;
+constexpr int W2 = TX + 4, H2 = TY + 4;  // T, u, v: two-node halo
+constexpr int W1 = TX + 2, H1 = TY + 2;  // rho, T*: one-node halo
 
 template <typename T>
-__device__ __forceinline__ T energy_rate(const EnergyArgs& a, const T* src, const double* rho, const double* ux,
-                                         const double* uy, int x, int y) {
-  const int nx = a.nx, ny = a.ny;
-  const size_t node = size_t(y) * nx + x;
-  const T tc = src[node];
+struct EnergyArgs {
+  int nx, ny;
+  T R, b4, c_v, kappa, twoTbot, twoTtop;
+};
+
+// D2Q9 direction i: (cx, cy) in the order of Eq. VelocitySet
+__device__ __forceinline__ int cx_of(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
+
+// Right-hand side of the energy equation at the node whose T sits at Ts[c] (row stride sw)
+// and whose u, v sit at U[cu], V[cu] (row stride uw).
+template <typename T>
+__device__ __forceinline__ T rate(const EnergyArgs<T>& a, const T* Ts, int c, int sw, const T* U, const T* V, int cu,
+                                  int uw, T rho) {
+  const T tc = Ts[c];
   T gx = T(0), gy = T(0), lap = T(0), div = T(0);
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
-    const int cx = i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
-    const int cy = cy_of(i);
-    const int xn = x + cx < 0 ? nx - 1 : (x + cx >= nx ? 0 : x + cx);
-    const int yn = y + cy;
-    T Tn, un_x, un_y;
-    if (yn < 0) {  // ghost row below the bottom wall
-      const size_t m = size_t(xn);
-      Tn = T(2.0 * a.T_bot) - src[m];
-      un_x = -T(ux[m]);
-      un_y = -T(uy[m]);
-    } else if (yn >= ny) {  // ghost row above the top wall
-      const size_t m = size_t(ny - 1) * nx + xn;
-      Tn = T(2.0 * a.T_top) - src[m];
-      un_x = -T(ux[m]);
-      un_y = -T(uy[m]);
-    } else {
-      const size_t m = size_t(yn) * nx + xn;
-      Tn = src[m];
-      un_x = T(ux[m]);
-      un_y = T(uy[m]);
-    }
+    const int cx = cx_of(i), cy = cy_of(i);
     const T w = T(w_of(i));
-    gx += w * T(cx) * Tn;
-    gy += w * T(cy) * Tn;
-    lap += w * (Tn - tc);
-    div += w * (T(cx) * un_x + T(cy) * un_y);
+    const T tn = Ts[c + cy * sw + cx];
+    gx += w * T(cx) * tn;
+    gy += w * T(cy) * tn;
+    lap += w * (tn - tc);
+    div += w * (T(cx) * U[cu + cy * uw + cx] + T(cy) * V[cu + cy * uw + cx]);
   }
-  gx *= T(3);
-  gy *= T(3);
-  lap *= T(6);
-  div *= T(3);
-  const T r = T(rho[node]);
-  const T eta = T(a.b / 4.0) * r;
+  const T eta = a.b4 * rho;
   const T om = T(1) - eta;
   const T Z = (T(1) + eta * (T(1) + eta * (T(1) - eta))) / (om * om * om);
-  const T dpdT = r * T(a.R) * Z;
-  const T inv = T(1) / (r * T(a.c_v));
-  return -(T(ux[node]) * gx + T(uy[node]) * gy) + T(a.kappa) * inv * lap - tc * dpdT * inv * div;
+  const T inv = T(1) / (rho * a.c_v);
+  return -(U[cu] * (T(3) * gx) + V[cu] * (T(3) * gy)) + a.kappa * inv * (T(6) * lap) -
+         tc * (rho * a.R * Z) * inv * (T(3) * div);
 }
 
-// stage 1: k1 = L(T), T* = T + k1; stage 2: T <- T + (k1 + L(T*)) / 2
 template <typename T>
-__global__ void energy_stage_kernel(const EnergyArgs a, int stage, const double* rho, const double* ux,
-                                    const double* uy, T* Tcur, T* Tstar, T* k1buf) {
-  const size_t n = size_t(a.nx) * a.ny;
-  for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < n; q += size_t(gridDim.x) * blockDim.x) {
-    const int x = int(q % a.nx), y = int(q / a.nx);
-    if (stage == 1) {
-      const T k1 = energy_rate(a, Tcur, rho, ux, uy, x, y);
-      k1buf[q] = k1;
-      Tstar[q] = Tcur[q] + k1;
-    } else {
-      const T k2 = energy_rate(a, Tstar, rho, ux, uy, x, y);
-      Tcur[q] = Tcur[q] + T(0.5) * (k1buf[q] + k2);
+__global__ void __launch_bounds__(TX * TY) heun_kernel(const EnergyArgs<T> a, const double* __restrict__ rho,
+                                                      const double* __restrict__ ux, const double* __restrict__ uy,
+                                                      const T* __restrict__ Tin, T* __restrict__ Tout) {
+  __shared__ T sT[H2 * W2], sU[H2 * W2], sV[H2 * W2];
+  __shared__ T sR[H1 * W1], sS[H1 * W1], sK[H1 * W1];  // rho, T* = T + k1, k1
+  const int nx = a.nx, ny = a.ny;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  auto wrap = [nx](int x) { x %= nx; return x < 0 ? x + nx : x; };
+  const int x0 = blockIdx.x * TX;
+  for (int y0 = blockIdx.y * TY; y0 < ny; y0 += gridDim.y * TY) {
+    // T, u, v on rows y0-2 .. y0+TY+1: ghost rows -1 and ny by the wall rules, rows beyond
+    // them are never read
+    for (int k = tid; k < H2 * W2; k += TX * TY) {
+      const int r = k / W2, y = y0 - 2 + r, x = wrap(x0 - 2 + (k - r * W2));
+      T t = T(0), u = T(0), v = T(0);
+      if (y >= 0 && y < ny) {
+        const size_t n = size_t(y) * nx + x;
+        t = Tin[n];
+        u = T(ux[n]);
+        v = T(uy[n]);
+      } else if (y == -1 || y == ny) {
+        const size_t n = size_t(y < 0 ? 0 : ny - 1) * nx + x;
+        t = (y < 0 ? a.twoTbot : a.twoTtop) - Tin[n];
+        u = -T(ux[n]);
+        v = -T(uy[n]);
+      }
+      sT[k] = t;
+      sU[k] = u;
+      sV[k] = v;
     }
+    for (int k = tid; k < H1 * W1; k += TX * TY) {
+      const int r = k / W1, y = y0 - 1 + r, x = wrap(x0 - 1 + (k - r * W1));
+      sR[k] = (y >= 0 && y < ny) ? T(rho[size_t(y) * nx + x]) : T(1);
+    }
+    __syncthreads();
+
+    // stage 1 on the tile and its ring (real rows only): T* = T + k1
+    for (int k = tid; k < H1 * W1; k += TX * TY) {
+      const int r = k / W1, c = k - r * W1, y = y0 - 1 + r;
+      if (y >= 0 && y < ny) {
+        const int c2 = (r + 1) * W2 + (c + 1);
+        sK[k] = rate(a, sT, c2, W2, sU, sV, c2, W2, sR[k]);
+        sS[k] = sT[c2] + sK[k];
+      }
+    }
+    __syncthreads();
+    // ghost rows of T* from its first and last rows
+    for (int k = tid; k < H1 * W1; k += TX * TY) {
+      const int r = k / W1, y = y0 - 1 + r;
+      if (y == -1) sS[k] = a.twoTbot - sS[k + W1];
+      if (y == ny) sS[k] = a.twoTtop - sS[k - W1];
+    }
+    __syncthreads();
+
+    // stage 2 on the tile: T_new = T + (k1 + k2)/2
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x < nx && y < ny) {
+      const int c1 = (threadIdx.y + 1) * W1 + (threadIdx.x + 1);
+      const int c2 = (threadIdx.y + 2) * W2 + (threadIdx.x + 2);
+      const T t = sT[c2];
+      const T k1 = sK[c1];
+      const T k2 = rate(a, sS, c1, W1, sU, sV, c2, W2, sR[c1]);
+      Tout[size_t(y) * nx + x] = t + T(0.5) * (k1 + k2);
+    }
+    __syncthreads();  // the next tile of this CTA overwrites the shared arrays
   }
 }
 
@@ -92,44 +132,38 @@ __global__ void energy_stage_kernel(const EnergyArgs a, int stage, const double*
 // at y = ny - 1/2
 template <typename T>
 __global__ void linear_T_kernel(int nx, int ny, double T_bot, double T_top, T* Tf) {
-  const size_t n = size_t(nx) * ny;
-  for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < n; q += size_t(gridDim.x) * blockDim.x) {
-    const double y = double(q / nx);
-    Tf[q] = T(T_bot + (T_top - T_bot) * (y + 0.5) / ny);
-  }
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int y = blockIdx.y; y < ny; y += gridDim.y)
+    if (x < nx) Tf[size_t(y) * nx + x] = T(T_bot + (T_top - T_bot) * (double(y) + 0.5) / ny);
 }
 
-int grid_of(size_t n) {
-  size_t g = (n + 255) / 256;
-  return int(g > 8192 ? 8192 : (g < 1 ? 1 : g));
-}
+unsigned rows_grid(int rows) { return unsigned(rows < 65535 ? rows : 65535); }
 
 }  // namespace
 
 cudaError_t launch_energy_step(int precision, int nx, int ny, double R, double b, double c_v, double kappa,
                                double T_bot, double T_top, const double* rho, const double* ux, const double* uy,
-                               void* Tcur, void* Tstar, void* k1, cudaStream_t stream) {
-  const EnergyArgs a{nx, ny, R, b, c_v, kappa, T_bot, T_top};
-  const int g = grid_of(size_t(nx) * ny);
-  for (int stage = 1; stage <= 2; ++stage) {
-    if (precision == 1)
-      energy_stage_kernel<float><<<g, 256, 0, stream>>>(a, stage, rho, ux, uy, static_cast<float*>(Tcur),
-                                                        static_cast<float*>(Tstar), static_cast<float*>(k1));
-    else
-      energy_stage_kernel<double><<<g, 256, 0, stream>>>(a, stage, rho, ux, uy, static_cast<double*>(Tcur),
-                                                         static_cast<double*>(Tstar), static_cast<double*>(k1));
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+                               const void* Tin, void* Tout, cudaStream_t stream) {
+  const dim3 grid((nx + TX - 1) / TX, rows_grid((ny + TY - 1) / TY)), block(TX, TY);
+  if (precision == 1) {
+    const EnergyArgs<float> a{nx, ny, float(R), float(b / 4.0), float(c_v), float(kappa), float(2.0 * T_bot),
+                              float(2.0 * T_top)};
+    heun_kernel<float><<<grid, block, 0, stream>>>(a, rho, ux, uy, static_cast<const float*>(Tin),
+                                                   static_cast<float*>(Tout));
+  } else {
+    const EnergyArgs<double> a{nx, ny, R, b / 4.0, c_v, kappa, 2.0 * T_bot, 2.0 * T_top};
+    heun_kernel<double><<<grid, block, 0, stream>>>(a, rho, ux, uy, static_cast<const double*>(Tin),
+                                                    static_cast<double*>(Tout));
   }
-  return cudaSuccess;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, void* Tf, cudaStream_t stream) {
-  const int g = grid_of(size_t(nx) * ny);
+  const dim3 grid((nx + 255) / 256, rows_grid(ny)), block(256);
   if (precision == 1)
-    linear_T_kernel<float><<<g, 256, 0, stream>>>(nx, ny, T_bot, T_top, static_cast<float*>(Tf));
+    linear_T_kernel<float><<<grid, block, 0, stream>>>(nx, ny, T_bot, T_top, static_cast<float*>(Tf));
   else
-    linear_T_kernel<double><<<g, 256, 0, stream>>>(nx, ny, T_bot, T_top, static_cast<double*>(Tf));
+    linear_T_kernel<double><<<grid, block, 0, stream>>>(nx, ny, T_bot, T_top, static_cast<double*>(Tf));
   return cudaGetLastError();
 }
 

@@ -208,3 +208,43 @@ def test_isothermal_handle_has_no_temperature_field():
             lbm.lbm_set_params(h, q)
     finally:
         lbm.lbm_destroy(h)
+
+
+def test_workspace_size_in_a_fresh_process():
+    """lbm_workspace_bytes called before any handle exists (so before the kernels' shared
+    memory limits are set) gives the size lbm_init then requires, for every precision and
+    both variants, on the sizes of the thermal and single-domain workloads."""
+    import subprocess
+    import sys
+
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_2301_12869_gb300 import lbm\n"
+        "lbm.load()\n"
+        "Tc = lbm.lbm_critical_point(0.25, 4.0, 1.0)[1]\n"
+        "for prec in ('fp32', 'fp64'):\n"
+        "    for th in (0, 1):\n"
+        "        for nx, ny in ((512, 2048), (1024, 512)):\n"
+        "            p = lbm.make_params(nx, ny, 0.85 * Tc, prec, a=0.25, thermal=th, T_bot=0.9 * Tc, T_top=0.8 * Tc)\n"
+        "            lat = lbm.Lattice(p, torch.full((ny, nx), 0.1, dtype=torch.float64, device='cuda'))\n"
+        "            lat.close()\n"
+        "print('ok')\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert out.stdout.strip().endswith("ok")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_thermal_handle_keeps_a_thermal_tile(precision):
+    p = thermal_params(16, 16, precision)
+    h = lbm.lbm_init(p, column(16, 16))
+    try:
+        with pytest.raises(lbm.LbmError, match="no thermal kernels"):
+            lbm.lbm_set_tiling(h, 1)
+        assert lbm.lbm_autotune(h, 2)[0] == 0
+        lbm.lbm_step(h, 2)
+        assert lbm.lbm_status(h) == 0
+    finally:
+        lbm.lbm_destroy(h)
