@@ -89,3 +89,23 @@ def perturbed_populations(rho0, amp, seed=DEFAULT_SEED):
         u = uniform_field(seed, nx, ny, stream=100 + i)
         f[i] = LATTICE_WEIGHTS[i] * rho0 * (1.0 + amp * (2.0 * u - 1.0))
     return f
+
+
+def mlp_draws(seed: int = DEFAULT_SEED, width: int = 128, n_in: int = 5) -> dict:
+    """U[0, 1) draws for the warm-start network's initial weights (shapes of W1 (width x
+    n_in), W2, W3 (width x width) and w4 (width)), one SplitMix64 stream per array."""
+    shapes = {"W1": (width, n_in), "W2": (width, width), "W3": (width, width), "w4": (width,)}
+    out = {}
+    for s, (name, shape) in enumerate(shapes.items()):
+        n = int(np.prod(shape))
+        counter = (np.uint64(200 + s) << np.uint64(48)) + np.arange(n, dtype=np.uint64)
+        bits = splitmix64(counter, seed) >> np.uint64(11)
+        out[name] = (bits.astype(np.float64) * (1.0 / 9007199254740992.0)).reshape(shape)
+    return out
+
+
+def minibatch_indices(n: int, batch: int, step: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """Sample indices of minibatch `step`: SplitMix64(step * batch + i) mod n, i < batch
+    (sampling with replacement)."""
+    counter = np.uint64(step) * np.uint64(batch) + np.arange(batch, dtype=np.uint64)
+    return (splitmix64(counter, seed) % np.uint64(n)).astype(np.int64)
