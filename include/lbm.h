@@ -238,6 +238,73 @@ int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out);
 /* Release a batch. NULL is accepted. */
 int lbm_batch_destroy(lbm_batch* b);
 
+/* ---- learned warm start for the liquid columns (no counterpart in the paper)
+ *
+ * A 5 -> 128 -> 128 -> 128 -> 1 network with SiLU activations predicts the steady density
+ * profile rho(z)/rho_c of a column from its descriptors (T/T_c, log10|g|, gravity form,
+ * <rho>/rho_c, z/H) with z = y + 1/2 and H = ny. Its only use is to initialise columns;
+ * the lattice Boltzmann run to the residual target stays the judge of the result.
+ * Arithmetic: bfloat16 inputs, weights and activations as tensor-core operands (tcgen05,
+ * FP32 accumulation in tensor memory), FP32 biases, output layer, loss and Adam; inputs
+ * normalised as x_n = (x - c)/s with c = (0.825, -5, 1.5, 1.4, 0.5), s = (0.125, 1, 0.5,
+ * 1.1, 0.5). Loss: mean squared error of rho/rho_c.
+ *
+ * Parameters: LBM_MLP_NPARAMS FP32 values, packed in this order:
+ *   W1 [128][16] (input j < 5 used; the rest must be 0), b1 [128], W2 [128][128] ([out][in]),
+ *   b2 [128], W3 [128][128], b3 [128], w4 [128], b4 [1].
+ * Feature rows: 5 FP32 values (T/T_c, log10|g|, form, <rho>/rho_c, z/H), raw (the network
+ * normalises them). All feature/target/output arrays of these calls are DEVICE pointers. */
+#define LBM_MLP_WIDTH 128
+#define LBM_MLP_INPUTS 5
+#define LBM_MLP_IN_PAD 16
+#define LBM_MLP_NPARAMS (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 128 + 1)
+
+typedef struct lbm_mlp lbm_mlp;
+
+/* Create a network with the given parameters (host array), Adam state zero. batch_capacity
+ * (a multiple of 128, <= 4194304) bounds the rows of one pass; the library allocates
+ * ~(1.3 KB x batch_capacity + 0.7 MB) of device memory. stream: cudaStream_t or NULL. */
+int lbm_mlp_create(const float* params, int batch_capacity, void* stream, lbm_mlp** out);
+/* Replace the parameters (host array) and reset the Adam state; synchronises. */
+int lbm_mlp_set_params(lbm_mlp* h, const float* params);
+/* Current parameters into a host array; synchronises. */
+int lbm_mlp_get_params(lbm_mlp* h, float* params);
+/* Loss (mean over the n <= batch_capacity rows) and its gradient with respect to every
+ * parameter (host array, packed like the parameters) for feature rows x [n][5] and targets
+ * t [n] (device). No update. Synchronises. */
+int lbm_mlp_gradients(lbm_mlp* h, const float* x, const float* t, int n, float* grads, double* loss);
+/* iters Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr), each on `batch`
+ * rows drawn with replacement from the n rows of x, t (device): row i of step k is
+ * SplitMix64(k batch + i, seed) mod n, k counting every step since create/set_params.
+ * losses (host, iters floats, may be NULL) receives each step's minibatch loss (then every
+ * step synchronises). */
+int lbm_mlp_train(lbm_mlp* h, const float* x, const float* t, long long n, int batch, int iters, float lr,
+                  unsigned long long seed, float* losses);
+/* y[i] = network(x[i]) (predicted rho/rho_c) for n rows (device arrays); synchronises. */
+int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y);
+/* Feature rows of columns: row (c, y) of the concatenation over columns (sum of ny_c rows)
+ * gets (T_c/T_crit, log10|g_c|, form_c, <rho>_c/rho_crit, (y + 1/2)/ny_c), with the critical
+ * point of a, b, R. <rho>_c comes from rho when rho != NULL - the columns' density fields,
+ * DEVICE, concatenated [col][y][x] with nx per column as lbm_batch_moments writes them -
+ * else from mean_rho (host, one value per column). With rho and t != NULL, t receives the
+ * targets rho(y, x = 0)/rho_crit. x, t: DEVICE. Synchronises `stream`. */
+int lbm_mlp_features(const lbm_column* cols, int ncols, int nx, double a, double b, double R, const double* rho,
+                     const double* mean_rho, float* x, float* t, void* stream);
+/* Initial densities for lbm_batch_init: for each column the predicted profile times
+ * rho_crit (floored at 1e-3), scaled so that its mean equals mean_rho[c] (host), the same
+ * on every x; written to rho0 (DEVICE, concatenated [col][y][x]). Synchronises. */
+int lbm_mlp_warm_start(lbm_mlp* h, const lbm_column* cols, int ncols, int nx, double a, double b, double R,
+                       const double* mean_rho, double* rho0);
+/* The network's tensor-core matrix product on its own: C[M x N] = A[M x K] B[N x K]^T with A,
+ * B bfloat16 bit patterns (DEVICE, row-major, K contiguous, lda/ldb multiples of 8, 16-byte
+ * aligned, K a multiple of 16), C FP32 (DEVICE, ldc). accumulate = 0: C is overwritten;
+ * accumulate = 1: C += the product, K split into ranges of k_split (a multiple of 64;
+ * <= 0: no split) summed by atomic adds. Synchronises `stream`. */
+int lbm_mlp_gemm(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N, int K,
+                 int k_split, int accumulate, void* stream);
+/* Release a network. NULL is accepted. */
+int lbm_mlp_destroy(lbm_mlp* h);
+
 /* ---- one step without device allocation (this entry point has no counterpart in the paper)
  *
  * Some callers cannot call cudaMalloc: a host loop that must not stall other streams on

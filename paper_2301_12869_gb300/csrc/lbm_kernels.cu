@@ -32,6 +32,7 @@
 // same-step <rho> of Eq. Gravity_2, because streaming only permutes values.
 #include "lbm_internal.h"
 #include "lbm_physics.cuh"
+#include "lbm_ptx.cuh"
 #include "lbm_vec.cuh"
 
 #include <cuda_runtime.h>
@@ -45,18 +46,7 @@ namespace lbm {
 namespace {
 
 constexpr int kStages = 4;           // pipeline depth (rows of source planes in shared memory)
-constexpr long long kWaitCycles = 4000000000LL;   // bound of an mbarrier wait (about 2 s)
-
-// ---- PTX wrappers: mbarrier and the bulk-copy (TMA) engine
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
+// ---- PTX wrappers of the bulk-copy (TMA) engine; mbarrier helpers are in lbm_ptx.cuh
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
@@ -67,26 +57,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for the phase with the given parity; gives up after kWaitCycles.
-__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > limit) return false;
-  }
-  return true;
 }
 
 template <typename T>

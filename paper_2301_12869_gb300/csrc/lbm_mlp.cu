@@ -1,0 +1,839 @@
+// Learned warm start for the liquid-column runs: a 5 -> 128 -> 128 -> 128 -> 1 SiLU
+// network that predicts the steady density profile rho(z)/rho_c of a column from
+// (T/T_c, log10|g|, gravity form, <rho>/rho_c, z/H). It has no counterpart in the paper;
+// it only initialises lattice Boltzmann runs (Sec. IV set-up), which remain the judge.
+//
+// Arithmetic: bfloat16 inputs, weights and activations as matrix operands, FP32
+// accumulation, FP32 biases, output layer, loss and Adam (FP32 master weights).
+//
+// Every matrix product runs on the tcgen05 tensor cores through one GEMM kernel,
+// C[M x N] = A[M x K] B[N x K]^T with A and B bfloat16, K contiguous:
+//  * a CTA (4 warps) owns a 128 x 128 output tile whose FP32 accumulator lives in 128
+//    TMEM columns; K is consumed in chunks of 64 through two shared-memory stages;
+//  * all threads copy the next chunk into the canonical no-swizzle K-major layout (8-row x
+//    16-byte core matrices: 128 B apart along K, 1024 B apart along M/N) while the tensor
+//    cores work on the current one; one thread issues four 128 x 128 x 16 MMAs per chunk
+//    and commits them to the stage's mbarrier, which the copy into that stage waits for;
+//  * the epilogue reads the accumulator with tcgen05.ld (warp w: rows 32w..32w+31) and
+//    applies a fused operation: store, split-K atomic add, bias + SiLU (forward), or the
+//    SiLU derivative (backward) with the bias gradient as a column sum.
+// Waits are bounded (clock64); a timeout sets the status word and the CTA still waits
+// (bounded) for its MMAs and frees its TMEM before returning.
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_ptx.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+using lbm::kWaitCycles;
+
+constexpr int W = LBM_MLP_WIDTH;      // 128
+constexpr int KIN = LBM_MLP_IN_PAD;   // 16: inputs padded to one MMA K step
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + W * KIN;
+constexpr int OFF_W2 = OFF_B1 + W;
+constexpr int OFF_B2 = OFF_W2 + W * W;
+constexpr int OFF_W3 = OFF_B2 + W;
+constexpr int OFF_B3 = OFF_W3 + W * W;
+constexpr int OFF_W4 = OFF_B3 + W;
+constexpr int OFF_B4 = OFF_W4 + W;
+constexpr int NPARAM = OFF_B4 + 1;
+static_assert(NPARAM == LBM_MLP_NPARAMS, "parameter layout");
+
+// feature normalisation x_norm = (x - c) / s
+__constant__ float kCenter[LBM_MLP_INPUTS] = {0.825f, -5.0f, 1.5f, 1.4f, 0.5f};
+__constant__ float kScale[LBM_MLP_INPUTS] = {0.125f, 1.0f, 0.5f, 1.1f, 0.5f};
+
+// ------------------------------------------------------------------ GEMM
+constexpr int BM = 128, BN = 128, BK = 64, GT = 128;
+constexpr int TILE_BYTES = BM * BK * 2;                 // one operand, one stage: 16 KB
+constexpr int GEMM_SMEM = 4 * TILE_BYTES + 1024 + 64;  // A/B x 2 stages, alignment, barriers
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B bfloat16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+
+enum Epi : int { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_FWD = 2, EPI_BWD = 3 };
+
+struct GemmArgs {
+  const bf16* A;
+  int lda;
+  const bf16* B;
+  int ldb;
+  int M, N, K, k_split;  // k_split: K range per blockIdx.z (multiple of BK)
+  float* C;              // EPI_STORE / EPI_ATOMIC: C[m * ldc + n]
+  int ldc;
+  const float* bias;     // EPI_FWD: z = acc + bias[n]
+  float* Z;              // EPI_FWD: z stored; EPI_BWD: z read (SiLU derivative)
+  int ldz;
+  bf16* H;               // EPI_FWD: silu(z); EPI_BWD: dz = acc silu'(z)  ([m][n], may be NULL)
+  int ldh;
+  bf16* HT;              // the same values transposed ([n][m], may be NULL)
+  int ldht;
+  float* colsum;         // EPI_BWD: colsum[n] += sum over m of dz (may be NULL)
+  int* status;
+};
+
+// shared-memory matrix descriptor: no swizzle, K-major; LBO = 128 B (next core matrix
+// along K), SBO = 1024 B (next 8 rows), descriptor version 1 (bits 46-47)
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint32_t a = lbm::smem_u32(p);
+  return uint64_t((a >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46);
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float s = 1.0f / (1.0f + expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// rows r0.. r0+127 of X (row-major, ld elements, columns [k, kend)) into the core-matrix
+// layout of one stage: 16-byte chunk q (row r = 8 (q >> 6) + (q & 7), column block
+// (q >> 3) & 7) goes to byte 16 q; rows >= rows and columns >= kend read as zero
+__device__ __forceinline__ void load_tile(uint8_t* dst, const bf16* X, int ld, int rows, int r0, int k, int kend) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int q = threadIdx.x + GT * i;
+    const int r = 8 * (q >> 6) + (q & 7), kb = (q >> 3) & 7;
+    const int row = r0 + r, col = k + 8 * kb;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (row < rows && col + 8 <= kend) v = *reinterpret_cast<const uint4*>(X + size_t(row) * ld + col);
+    *reinterpret_cast<uint4*>(dst + 16 * q) = v;
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA[2] = {smem, smem + TILE_BYTES};
+  uint8_t* sB[2] = {smem + 2 * TILE_BYTES, smem + 3 * TILE_BYTES};
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * TILE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * g.k_split;
+  const int kend = min(g.K, kbeg + g.k_split);
+  const int nchunks = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  if (nchunks == 0) return;  // uniform over the CTA, before any allocation
+
+  if (tid == 0) {
+    lbm::mbar_init(&bar[0], 1);
+    lbm::mbar_init(&bar[1], 1);
+    lbm::fence_mbar_init();
+  }
+  if (warp == 0) {
+    lbm::tmem_alloc(tmem_slot, BN);
+    lbm::tmem_relinquish();
+  }
+  lbm::tc_fence_before();
+  __syncthreads();
+  lbm::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  load_tile(sA[0], g.A, g.lda, g.M, m0, kbeg, kend);
+  load_tile(sB[0], g.B, g.ldb, g.N, n0, kbeg, kend);
+  lbm::fence_proxy_async_smem();
+  __syncthreads();
+
+  bool ok = true;
+  int c = 0;
+  for (; c < nchunks; ++c) {
+    const int s = c & 1;
+    if (tid == 0) {
+      lbm::tc_fence_after();
+      const int steps = (min(BK, kend - (kbeg + c * BK)) + 15) / 16;
+      for (int j = 0; j < steps; ++j)
+        lbm::tc_mma_f16(tmem, smem_desc(sA[s] + 256 * j), smem_desc(sB[s] + 256 * j), kIdesc, (c > 0 || j > 0) ? 1u : 0u);
+      lbm::tc_commit(&bar[s]);
+    }
+    if (c + 1 < nchunks) {
+      // stage s^1 was read by the MMAs of chunk c - 1: wait for their commit
+      if (c >= 1) ok = lbm::mbar_wait_bounded(&bar[(c - 1) & 1], uint32_t(((c - 1) >> 1) & 1)) && ok;
+      if (ok) {
+        const int k = kbeg + (c + 1) * BK;
+        load_tile(sA[s ^ 1], g.A, g.lda, g.M, m0, k, kend);
+        load_tile(sB[s ^ 1], g.B, g.ldb, g.N, n0, k, kend);
+        lbm::fence_proxy_async_smem();
+      }
+    }
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      ++c;
+      break;
+    }
+  }
+  // the last chunk issued (c - 1) completes after every earlier one
+  const int last = c - 1;
+  const bool done = lbm::mbar_wait_bounded(&bar[last & 1], uint32_t((last >> 1) & 1), ok ? kWaitCycles : kWaitCycles / 4);
+  ok = __syncthreads_and(ok && done);
+  lbm::tc_fence_after();
+  if (!ok) {
+    if (tid == 0) atomicOr(g.status, lbm::STATUS_TIMEOUT);
+  } else {
+    const int m = m0 + 32 * warp + lane;
+    const bool row_ok = m < g.M;
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 32; ++cc) {
+      float v[32];
+      lbm::tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(32 * cc), v);
+      const int nb = n0 + 32 * cc;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int n = nb + i;
+        const bool in = row_ok && n < g.N;
+        if constexpr (EPI == EPI_STORE) {
+          if (in) g.C[size_t(m) * g.ldc + n] = v[i];
+        } else if constexpr (EPI == EPI_ATOMIC) {
+          if (in) atomicAdd(g.C + size_t(m) * g.ldc + n, v[i]);
+        } else if constexpr (EPI == EPI_FWD) {
+          if (in) {
+            const float z = v[i] + g.bias[n];
+            g.Z[size_t(m) * g.ldz + n] = z;
+            const bf16 h = __float2bfloat16_rn(silu_f(z));
+            if (g.H) g.H[size_t(m) * g.ldh + n] = h;
+            if (g.HT) g.HT[size_t(n) * g.ldht + m] = h;
+          }
+        } else {  // EPI_BWD
+          const float dz = in ? v[i] * dsilu_f(g.Z[size_t(m) * g.ldz + n]) : 0.0f;
+          if (in) {
+            const bf16 d = __float2bfloat16_rn(dz);
+            if (g.H) g.H[size_t(m) * g.ldh + n] = d;
+            if (g.HT) g.HT[size_t(n) * g.ldht + m] = d;
+          }
+          if (g.colsum) {
+            const float sum = warp_sum_f(dz);
+            if (lane == 0 && n < g.N) atomicAdd(g.colsum + n, sum);
+          }
+        }
+      }
+    }
+  }
+  lbm::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) lbm::tmem_dealloc(tmem, BN);
+}
+
+// ------------------------------------------------------------------ other kernels
+__device__ __forceinline__ uint64_t splitmix64(uint64_t counter, uint64_t seed) {
+  uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// network inputs of Bc rows: rows < count take sample first + i (or a SplitMix64 draw when
+// random), the rest are zero; X [Bc][16] and XT [16][Bc] bfloat16, targets FP32
+__global__ void gather_kernel(const float* __restrict__ feat, const float* __restrict__ tgt, long long n,
+                              long long first, int count, int random, unsigned long long seed, long long step,
+                              int Bc, bf16* __restrict__ X, bf16* __restrict__ XT, float* __restrict__ tout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Bc) return;
+  float x[KIN];
+#pragma unroll
+  for (int j = 0; j < KIN; ++j) x[j] = 0.0f;
+  float t = 0.0f;
+  if (i < count) {
+    const long long idx =
+        random ? (long long)(splitmix64((unsigned long long)step * (unsigned long long)count + i, seed) % (unsigned long long)n)
+               : first + i;
+#pragma unroll
+    for (int j = 0; j < LBM_MLP_INPUTS; ++j) x[j] = (feat[idx * LBM_MLP_INPUTS + j] - kCenter[j]) / kScale[j];
+    if (tgt) t = tgt[idx];
+  }
+#pragma unroll
+  for (int j = 0; j < KIN; ++j) {
+    const bf16 b = __float2bfloat16_rn(x[j]);
+    X[size_t(i) * KIN + j] = b;
+    XT[size_t(j) * Bc + i] = b;
+  }
+  if (tout) tout[i] = t;
+}
+
+// output layer y = silu(Z3) . w4 + b4; with train: loss, dy = 2 (y - t)/count, the
+// gradients of w4, b4, b3 and dZ3 = dy w4 silu'(Z3) (bfloat16, [Bc][128] and [128][Bc])
+__global__ void __launch_bounds__(128) head_kernel(const float* __restrict__ Z3, const float* __restrict__ P,
+                                                   const float* __restrict__ tgt, int count, int Bc, int train,
+                                                   float* __restrict__ y_out, float* __restrict__ grad,
+                                                   double* __restrict__ loss, bf16* __restrict__ dZ,
+                                                   bf16* __restrict__ dZT) {
+  __shared__ float w4[W];
+  for (int j = threadIdx.x; j < W; j += blockDim.x) w4[j] = P[OFF_W4 + j];
+  __syncthreads();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;  // Bc is a multiple of 128: every thread has a row
+  const int lane = threadIdx.x & 31;
+  const float* z = Z3 + size_t(s) * W;
+  float y = P[OFF_B4];
+  for (int j = 0; j < W; ++j) y += silu_f(z[j]) * w4[j];
+  const bool valid = s < count;
+  if (!train) {
+    if (valid) y_out[s] = y;
+    return;
+  }
+  const float e = valid ? y - tgt[s] : 0.0f;
+  const float dy = 2.0f * e / float(count);
+  double e2 = double(e) * double(e);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+  const float sdy = warp_sum_f(dy);
+  if (lane == 0) {
+    atomicAdd(loss, e2);
+    atomicAdd(grad + OFF_B4, sdy);
+  }
+  for (int j = 0; j < W; ++j) {
+    const float zj = z[j];
+    const float dz = dy * w4[j] * dsilu_f(zj);
+    const bf16 d = __float2bfloat16_rn(dz);
+    dZ[size_t(s) * W + j] = d;
+    dZT[size_t(j) * Bc + s] = d;
+    const float a = warp_sum_f(dz), b = warp_sum_f(silu_f(zj) * dy);
+    if (lane == 0) {
+      atomicAdd(grad + OFF_B3 + j, a);
+      atomicAdd(grad + OFF_W4 + j, b);
+    }
+  }
+}
+
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+// bfloat16 operand copies of the master weights: W1 [128][16], W2, W3 [out][in] and the
+// transposes W2t, W3t [in][out]
+__global__ void cast_kernel(const float* __restrict__ P, bf16* __restrict__ W1, bf16* __restrict__ W2,
+                            bf16* __restrict__ W3, bf16* __restrict__ W2t, bf16* __restrict__ W3t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < W * KIN) W1[i] = __float2bfloat16_rn(P[OFF_W1 + i]);
+  if (i < W * W) {
+    const int o = i / W, k = i % W;
+    const bf16 a = __float2bfloat16_rn(P[OFF_W2 + i]), b = __float2bfloat16_rn(P[OFF_W3 + i]);
+    W2[i] = a;
+    W3[i] = b;
+    W2t[size_t(k) * W + o] = a;
+    W3t[size_t(k) * W + o] = b;
+  }
+}
+
+struct ColFeat {
+  int ny;
+  long long row_off;   // first row of this column in the concatenated row list
+  long long node_off;  // first node of this column in the concatenated [col][y][x] fields
+  float t, lg, form, mean;  // T/T_c, log10|g|, form, <rho>/rho_c (NaN: from rho)
+};
+
+// raw features (T/T_c, log10|g|, form, <rho>/rho_c, z/H) of every row of every column;
+// with rho != NULL also the targets rho(y, x = 0)/rho_c and <rho> from rho itself
+__global__ void features_kernel(const ColFeat* __restrict__ cols, int ncols, int nx, const double* __restrict__ rho,
+                                double rho_c, float* __restrict__ feat, float* __restrict__ tgt) {
+  const int c = blockIdx.x;
+  if (c >= ncols) return;
+  const ColFeat cf = cols[c];
+  __shared__ double part[32];
+  float mean = cf.mean;
+  if (rho) {  // column mean of rho (every node)
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < (long long)cf.ny * nx; q += blockDim.x) s += rho[cf.node_off + q];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += part[w];
+    mean = float(tot / (double(cf.ny) * nx) / rho_c);
+  }
+  for (int y = threadIdx.x; y < cf.ny; y += blockDim.x) {
+    float* f = feat + (cf.row_off + y) * LBM_MLP_INPUTS;
+    f[0] = cf.t;
+    f[1] = cf.lg;
+    f[2] = cf.form;
+    f[3] = mean;
+    f[4] = (float(y) + 0.5f) / float(cf.ny);
+    if (rho && tgt) tgt[cf.row_off + y] = float(rho[cf.node_off + (long long)y * nx] / rho_c);
+  }
+}
+
+// warm start: rho0 of column c = the predicted profile (times rho_c, floored at rho_min),
+// scaled so that its mean is the column's <rho>, the same on every x
+__global__ void warm_profile_kernel(const ColFeat* __restrict__ cols, int ncols, int nx, const float* __restrict__ yhat,
+                                    const double* __restrict__ mean_rho, double rho_c, double rho_min,
+                                    double* __restrict__ rho0) {
+  const int c = blockIdx.x;
+  if (c >= ncols) return;
+  const ColFeat cf = cols[c];
+  __shared__ double part[32];
+  __shared__ double scale;
+  double s = 0.0;
+  for (int y = threadIdx.x; y < cf.ny; y += blockDim.x) s += fmax(double(yhat[cf.row_off + y]) * rho_c, rho_min);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += part[w];
+    scale = mean_rho[c] * double(cf.ny) / tot;
+  }
+  __syncthreads();
+  for (long long q = threadIdx.x; q < (long long)cf.ny * nx; q += blockDim.x) {
+    const int y = int(q / nx);
+    rho0[cf.node_off + q] = fmax(double(yhat[cf.row_off + y]) * rho_c, rho_min) * scale;
+  }
+}
+
+thread_local char g_err[512] = "";
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  lbm::set_last_error(g_err);
+  return code;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct lbm_mlp {
+  cudaStream_t stream = nullptr;
+  int Bc = 0;  // batch capacity (multiple of 128)
+  void* mem = nullptr;
+  float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
+  bf16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2t = nullptr, *W3t = nullptr;
+  bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *H2 = nullptr, *H1T = nullptr, *H2T = nullptr;
+  bf16 *dZa = nullptr, *dZb = nullptr, *dZTa = nullptr, *dZTb = nullptr;
+  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *tgt = nullptr, *y = nullptr;
+  double* loss = nullptr;
+  int* status = nullptr;
+  long long adam_t = 0;
+};
+
+namespace {
+
+#define MLP_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaError_t gemm_prepare() {
+  cudaError_t e = cudaSuccess;
+  for (const void* fn : {(const void*)gemm_kernel<EPI_STORE>, (const void*)gemm_kernel<EPI_ATOMIC>,
+                         (const void*)gemm_kernel<EPI_FWD>, (const void*)gemm_kernel<EPI_BWD>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+  return e;
+}
+
+template <int EPI>
+cudaError_t gemm(const GemmArgs& a, int splits, cudaStream_t s) {
+  const dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, splits);
+  gemm_kernel<EPI><<<grid, GT, GEMM_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+GemmArgs gargs(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, int* status) {
+  GemmArgs a{};
+  a.A = A;
+  a.lda = lda;
+  a.B = B;
+  a.ldb = ldb;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.k_split = (K + BK - 1) / BK * BK;
+  a.status = status;
+  return a;
+}
+
+int status_of(lbm_mlp* h) {
+  int st = 0;
+  MLP_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MLP_CUDA(cudaStreamSynchronize(h->stream));
+  if (st & lbm::STATUS_TIMEOUT) return fail(LBM_ETIMEOUT, "a tensor-core wait timed out");
+  return LBM_OK;
+}
+
+// forward of rows [0, Bc) of X (count valid), then the head (train: loss and all gradients)
+int run_pass(lbm_mlp* h, int count, bool train) {
+  const int Bc = h->Bc;
+  cudaStream_t s = h->stream;
+  GemmArgs a = gargs(h->X, KIN, h->W1, KIN, Bc, W, KIN, h->status);
+  a.bias = h->P + OFF_B1;
+  a.Z = h->Z1;
+  a.ldz = W;
+  a.H = h->H1;
+  a.ldh = W;
+  a.HT = train ? h->H1T : nullptr;
+  a.ldht = Bc;
+  MLP_CUDA(gemm<EPI_FWD>(a, 1, s));
+  a = gargs(h->H1, W, h->W2, W, Bc, W, W, h->status);
+  a.bias = h->P + OFF_B2;
+  a.Z = h->Z2;
+  a.ldz = W;
+  a.H = h->H2;
+  a.ldh = W;
+  a.HT = train ? h->H2T : nullptr;
+  a.ldht = Bc;
+  MLP_CUDA(gemm<EPI_FWD>(a, 1, s));
+  a = gargs(h->H2, W, h->W3, W, Bc, W, W, h->status);
+  a.bias = h->P + OFF_B3;
+  a.Z = h->Z3;
+  a.ldz = W;
+  MLP_CUDA(gemm<EPI_FWD>(a, 1, s));
+  if (train) {
+    MLP_CUDA(cudaMemsetAsync(h->G, 0, sizeof(float) * NPARAM, s));
+    MLP_CUDA(cudaMemsetAsync(h->loss, 0, sizeof(double), s));
+  }
+  head_kernel<<<Bc / 128, 128, 0, s>>>(h->Z3, h->P, h->tgt, count, Bc, train ? 1 : 0, h->y, h->G, h->loss, h->dZa,
+                                       h->dZTa);
+  MLP_CUDA(cudaGetLastError());
+  if (!train) return LBM_OK;
+  // weight gradients are sums over the batch (K = Bc): split K over CTAs, atomic epilogue
+  const int ksplit = 1024, splits = (Bc + ksplit - 1) / ksplit;
+  auto wgrad = [&](const bf16* dZT, const bf16* HTm, int N, float* C, int ldc) {
+    GemmArgs w = gargs(dZT, Bc, HTm, Bc, W, N, Bc, h->status);
+    w.k_split = ksplit;
+    w.C = C;
+    w.ldc = ldc;
+    return gemm<EPI_ATOMIC>(w, splits, s);
+  };
+  auto dgrad = [&](const bf16* dZ, const bf16* Wt, const float* Z, bf16* dZo, bf16* dZTo, float* colsum) {
+    GemmArgs d = gargs(dZ, W, Wt, W, Bc, W, W, h->status);
+    d.Z = const_cast<float*>(Z);
+    d.ldz = W;
+    d.H = dZo;
+    d.ldh = W;
+    d.HT = dZTo;
+    d.ldht = Bc;
+    d.colsum = colsum;
+    return gemm<EPI_BWD>(d, 1, s);
+  };
+  MLP_CUDA(wgrad(h->dZTa, h->H2T, W, h->G + OFF_W3, W));                          // dW3
+  MLP_CUDA(dgrad(h->dZa, h->W3t, h->Z2, h->dZb, h->dZTb, h->G + OFF_B2));           // dZ2, db2
+  MLP_CUDA(wgrad(h->dZTb, h->H1T, W, h->G + OFF_W2, W));                          // dW2
+  MLP_CUDA(dgrad(h->dZb, h->W2t, h->Z1, h->dZa, h->dZTa, h->G + OFF_B1));           // dZ1, db1
+  MLP_CUDA(wgrad(h->dZTa, h->XT, KIN, h->G + OFF_W1, KIN));                        // dW1
+  return LBM_OK;
+}
+
+int cast_weights(lbm_mlp* h) {
+  cast_kernel<<<(W * W + 255) / 256, 256, 0, h->stream>>>(h->P, h->W1, h->W2, h->W3, h->W2t, h->W3t);
+  MLP_CUDA(cudaGetLastError());
+  return LBM_OK;
+}
+
+int gather(lbm_mlp* h, const float* x, const float* t, long long n, long long first, int count, bool random,
+           unsigned long long seed, long long step) {
+  gather_kernel<<<h->Bc / 128, 128, 0, h->stream>>>(x, t, n, first, count, random ? 1 : 0, seed, step, h->Bc, h->X,
+                                                   h->XT, h->tgt);
+  MLP_CUDA(cudaGetLastError());
+  return LBM_OK;
+}
+
+bool device_pointer(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int column_table(const lbm_column* cols, int ncols, int nx, double a, double b, double R, const double* mean_rho,
+                 std::vector<ColFeat>& out, double* rho_c, long long* rows) {
+  double rc, Tc, pc;
+  if (lbm_critical_point(a, b, R, &rc, &Tc, &pc) != LBM_OK) return fail(LBM_EINVAL, "need a, b, R > 0");
+  out.resize(ncols);
+  long long r = 0, q = 0;
+  for (int c = 0; c < ncols; ++c) {
+    const lbm_column& in = cols[c];
+    if (in.ny <= 0) return fail(LBM_EINVAL, "column %d has ny <= 0", c);
+    const double gmag = std::sqrt(in.gx * in.gx + in.gy * in.gy);
+    ColFeat& f = out[c];
+    f.ny = in.ny;
+    f.row_off = r;
+    f.node_off = q;
+    f.t = float(in.T / Tc);
+    f.lg = float(gmag > 0 ? std::log10(gmag) : -12.0);
+    f.form = float(in.gravity_form);
+    f.mean = mean_rho ? float(mean_rho[c] / rc) : NAN;
+    r += in.ny;
+    q += (long long)in.ny * nx;
+  }
+  *rho_c = rc;
+  *rows = r;
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ================================================================== public ABI
+extern "C" {
+
+int lbm_mlp_create(const float* params, int batch_capacity, void* stream, lbm_mlp** out) {
+  if (!params || !out) return fail(LBM_EINVAL, "params and out must not be NULL");
+  if (batch_capacity < 128 || batch_capacity % 128 || batch_capacity > (1 << 22))
+    return fail(LBM_EINVAL, "batch_capacity must be a multiple of 128 in [128, 4194304]");
+  *out = nullptr;
+  cudaError_t e = gemm_prepare();
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  lbm_mlp* h = new (std::nothrow) lbm_mlp();
+  if (!h) return fail(LBM_ENOMEM, "out of host memory");
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->Bc = batch_capacity;
+  const size_t Bc = size_t(batch_capacity);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t at = off; off = (off + bytes + 255) / 256 * 256; return at; };
+  const size_t oP = take(4 * NPARAM), oG = take(4 * NPARAM), oM = take(4 * NPARAM), oV = take(4 * NPARAM);
+  const size_t oW1 = take(2 * W * KIN), oW2 = take(2 * W * W), oW3 = take(2 * W * W), oW2t = take(2 * W * W),
+               oW3t = take(2 * W * W);
+  const size_t oX = take(2 * Bc * KIN), oXT = take(2 * Bc * KIN);
+  const size_t oH1 = take(2 * Bc * W), oH2 = take(2 * Bc * W), oH1T = take(2 * Bc * W), oH2T = take(2 * Bc * W);
+  const size_t odZa = take(2 * Bc * W), odZb = take(2 * Bc * W), odZTa = take(2 * Bc * W), odZTb = take(2 * Bc * W);
+  const size_t oZ1 = take(4 * Bc * W), oZ2 = take(4 * Bc * W), oZ3 = take(4 * Bc * W);
+  const size_t oT = take(4 * Bc), oY = take(4 * Bc), oL = take(8), oS = take(4);
+  e = cudaMalloc(&h->mem, off);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(LBM_ENOMEM, "cudaMalloc %zu bytes: %s", off, cudaGetErrorString(e));
+  }
+  char* base = static_cast<char*>(h->mem);
+  h->P = reinterpret_cast<float*>(base + oP);
+  h->G = reinterpret_cast<float*>(base + oG);
+  h->Mo = reinterpret_cast<float*>(base + oM);
+  h->Vo = reinterpret_cast<float*>(base + oV);
+  h->W1 = reinterpret_cast<bf16*>(base + oW1);
+  h->W2 = reinterpret_cast<bf16*>(base + oW2);
+  h->W3 = reinterpret_cast<bf16*>(base + oW3);
+  h->W2t = reinterpret_cast<bf16*>(base + oW2t);
+  h->W3t = reinterpret_cast<bf16*>(base + oW3t);
+  h->X = reinterpret_cast<bf16*>(base + oX);
+  h->XT = reinterpret_cast<bf16*>(base + oXT);
+  h->H1 = reinterpret_cast<bf16*>(base + oH1);
+  h->H2 = reinterpret_cast<bf16*>(base + oH2);
+  h->H1T = reinterpret_cast<bf16*>(base + oH1T);
+  h->H2T = reinterpret_cast<bf16*>(base + oH2T);
+  h->dZa = reinterpret_cast<bf16*>(base + odZa);
+  h->dZb = reinterpret_cast<bf16*>(base + odZb);
+  h->dZTa = reinterpret_cast<bf16*>(base + odZTa);
+  h->dZTb = reinterpret_cast<bf16*>(base + odZTb);
+  h->Z1 = reinterpret_cast<float*>(base + oZ1);
+  h->Z2 = reinterpret_cast<float*>(base + oZ2);
+  h->Z3 = reinterpret_cast<float*>(base + oZ3);
+  h->tgt = reinterpret_cast<float*>(base + oT);
+  h->y = reinterpret_cast<float*>(base + oY);
+  h->loss = reinterpret_cast<double*>(base + oL);
+  h->status = reinterpret_cast<int*>(base + oS);
+  int rc = lbm_mlp_set_params(h, params);
+  if (rc) {
+    lbm_mlp_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_mlp_set_params(lbm_mlp* h, const float* params) {
+  if (!h || !params) return fail(LBM_EINVAL, "handle and params must not be NULL");
+  MLP_CUDA(cudaMemcpyAsync(h->P, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice, h->stream));
+  MLP_CUDA(cudaMemsetAsync(h->Mo, 0, sizeof(float) * NPARAM, h->stream));
+  MLP_CUDA(cudaMemsetAsync(h->Vo, 0, sizeof(float) * NPARAM, h->stream));
+  MLP_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  h->adam_t = 0;
+  int rc = cast_weights(h);
+  if (rc) return rc;
+  MLP_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_mlp_get_params(lbm_mlp* h, float* params) {
+  if (!h || !params) return fail(LBM_EINVAL, "handle and params must not be NULL");
+  MLP_CUDA(cudaMemcpyAsync(params, h->P, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, h->stream));
+  MLP_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_mlp_gradients(lbm_mlp* h, const float* x, const float* t, int n, float* grads, double* loss) {
+  if (!h || !x || !t || !grads) return fail(LBM_EINVAL, "handle, x, t and grads must not be NULL");
+  if (n < 1 || n > h->Bc) return fail(LBM_EINVAL, "n must be in [1, batch_capacity]");
+  if (!device_pointer(x) || !device_pointer(t)) return fail(LBM_EINVAL, "x and t must be device pointers");
+  int rc = gather(h, x, t, n, 0, n, false, 0, 0);
+  if (!rc) rc = run_pass(h, n, true);
+  if (rc) return rc;
+  MLP_CUDA(cudaMemcpyAsync(grads, h->G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, h->stream));
+  double l = 0.0;
+  MLP_CUDA(cudaMemcpyAsync(&l, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  rc = status_of(h);
+  if (loss) *loss = l / n;
+  return rc;
+}
+
+int lbm_mlp_train(lbm_mlp* h, const float* x, const float* t, long long n, int batch, int iters, float lr,
+                  unsigned long long seed, float* losses) {
+  if (!h || !x || !t) return fail(LBM_EINVAL, "handle, x and t must not be NULL");
+  if (n < 1 || batch < 1 || batch > h->Bc || iters < 0 || !(lr > 0))
+    return fail(LBM_EINVAL, "need n >= 1, 1 <= batch <= batch_capacity, iters >= 0, lr > 0");
+  if (!device_pointer(x) || !device_pointer(t)) return fail(LBM_EINVAL, "x and t must be device pointers");
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int it = 0; it < iters; ++it) {
+    int rc = gather(h, x, t, n, 0, batch, true, seed, h->adam_t);
+    if (!rc) rc = run_pass(h, batch, true);
+    if (rc) return rc;
+    ++h->adam_t;
+    const float bc1 = 1.0f - std::pow(b1, float(h->adam_t)), bc2 = 1.0f - std::pow(b2, float(h->adam_t));
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, h->stream>>>(h->P, h->G, h->Mo, h->Vo, NPARAM, lr, b1, b2, eps, bc1,
+                                                             bc2);
+    MLP_CUDA(cudaGetLastError());
+    rc = cast_weights(h);
+    if (rc) return rc;
+    if (losses) {
+      double l = 0.0;
+      MLP_CUDA(cudaMemcpyAsync(&l, h->loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      MLP_CUDA(cudaStreamSynchronize(h->stream));
+      losses[it] = float(l / batch);
+    }
+  }
+  return status_of(h);
+}
+
+int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y) {
+  if (!h || !x || !y) return fail(LBM_EINVAL, "handle, x and y must not be NULL");
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  if (!device_pointer(x) || !device_pointer(y)) return fail(LBM_EINVAL, "x and y must be device pointers");
+  for (long long first = 0; first < n; first += h->Bc) {
+    const int count = int(std::min<long long>(h->Bc, n - first));
+    int rc = gather(h, x, nullptr, n, first, count, false, 0, 0);
+    if (!rc) rc = run_pass(h, count, false);
+    if (rc) return rc;
+    MLP_CUDA(cudaMemcpyAsync(y + first, h->y, sizeof(float) * count, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return status_of(h);
+}
+
+int lbm_mlp_features(const lbm_column* cols, int ncols, int nx, double a, double b, double R, const double* rho,
+                     const double* mean_rho, float* x, float* t, void* stream) {
+  if (!cols || ncols < 1 || nx < 1 || !x) return fail(LBM_EINVAL, "cols, ncols >= 1, nx >= 1 and x are required");
+  if (!rho && !mean_rho) return fail(LBM_EINVAL, "one of rho (device) and mean_rho (host) is required");
+  if (!device_pointer(x) || (t && !device_pointer(t)) || (rho && !device_pointer(rho)))
+    return fail(LBM_EINVAL, "x, t and rho must be device pointers");
+  std::vector<ColFeat> tab;
+  double rho_c;
+  long long rows;
+  int rc = column_table(cols, ncols, nx, a, b, R, rho ? nullptr : mean_rho, tab, &rho_c, &rows);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ColFeat* dtab = nullptr;
+  MLP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dtab), sizeof(ColFeat) * ncols, s));
+  cudaError_t e = cudaMemcpyAsync(dtab, tab.data(), sizeof(ColFeat) * ncols, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    features_kernel<<<ncols, 256, 0, s>>>(dtab, ncols, nx, rho, rho_c, x, t);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(dtab, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "features: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_mlp_warm_start(lbm_mlp* h, const lbm_column* cols, int ncols, int nx, double a, double b, double R,
+                       const double* mean_rho, double* rho0) {
+  if (!h || !cols || ncols < 1 || nx < 1 || !mean_rho || !rho0)
+    return fail(LBM_EINVAL, "handle, cols, ncols >= 1, nx >= 1, mean_rho and rho0 are required");
+  if (!device_pointer(rho0)) return fail(LBM_EINVAL, "rho0 must be a device pointer");
+  std::vector<ColFeat> tab;
+  double rho_c;
+  long long rows;
+  int rc = column_table(cols, ncols, nx, a, b, R, mean_rho, tab, &rho_c, &rows);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  char* mem = nullptr;
+  const size_t b_tab = (sizeof(ColFeat) * ncols + 255) / 256 * 256, b_mean = (8 * size_t(ncols) + 255) / 256 * 256;
+  const size_t b_feat = (4 * LBM_MLP_INPUTS * size_t(rows) + 255) / 256 * 256;
+  MLP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&mem), b_tab + b_mean + b_feat + 4 * size_t(rows), s));
+  ColFeat* dtab = reinterpret_cast<ColFeat*>(mem);
+  double* dmean = reinterpret_cast<double*>(mem + b_tab);
+  float* feat = reinterpret_cast<float*>(mem + b_tab + b_mean);
+  float* yhat = reinterpret_cast<float*>(mem + b_tab + b_mean + b_feat);
+  cudaError_t e = cudaMemcpyAsync(dtab, tab.data(), sizeof(ColFeat) * ncols, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dmean, mean_rho, 8 * size_t(ncols), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    features_kernel<<<ncols, 256, 0, s>>>(dtab, ncols, nx, nullptr, rho_c, feat, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) rc = lbm_mlp_predict(h, feat, rows, yhat);
+  if (e == cudaSuccess && rc == LBM_OK) {
+    // floor: a tenth of the smallest coexistence vapour density the inputs cover
+    warm_profile_kernel<<<ncols, 256, 0, s>>>(dtab, ncols, nx, yhat, dmean, rho_c, 1e-3, rho0);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(mem, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "warm start: %s", cudaGetErrorString(e));
+  return rc;
+}
+
+int lbm_mlp_gemm(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N, int K,
+                 int k_split, int accumulate, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 16 || K % 16) return fail(LBM_EINVAL, "need M, N >= 1 and K a multiple of 16");
+  if (lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N) return fail(LBM_EINVAL, "lda, ldb multiples of 8 and >= K; ldc >= N");
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return fail(LBM_EINVAL, "A and B 16-byte aligned");
+  if (k_split <= 0) k_split = K;
+  if (k_split % BK && k_split < K) return fail(LBM_EINVAL, "k_split must be a multiple of 64");
+  if (!accumulate && k_split < K) return fail(LBM_EINVAL, "split K needs accumulate");
+  cudaError_t e = gemm_prepare();
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  int* status = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MLP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int), s));
+  MLP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+  GemmArgs a = gargs(reinterpret_cast<const bf16*>(A), lda, reinterpret_cast<const bf16*>(B), ldb, M, N, K, status);
+  a.k_split = std::min(K, (k_split + BK - 1) / BK * BK);
+  a.C = C;
+  a.ldc = ldc;
+  const int splits = (K + a.k_split - 1) / a.k_split;
+  e = accumulate ? gemm<EPI_ATOMIC>(a, splits, s) : gemm<EPI_STORE>(a, 1, s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(status, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  if (st & lbm::STATUS_TIMEOUT) return fail(LBM_ETIMEOUT, "a tensor-core wait timed out");
+  return LBM_OK;
+}
+
+int lbm_mlp_destroy(lbm_mlp* h) {
+  if (!h) return LBM_OK;
+  int rc = LBM_OK;
+  if (h->mem) {
+    cudaStreamSynchronize(h->stream);
+    if (cudaFree(h->mem) != cudaSuccess) rc = LBM_ECUDA;
+  }
+  delete h;
+  return rc;
+}
+
+}  // extern "C"

@@ -41,7 +41,15 @@ EXPORTS = (
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
     "lbm_batch_init", "lbm_batch_run", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
     "lbm_batch_convert", "lbm_batch_destroy",
+    "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
+    "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_destroy",
 )
+
+MLP_WIDTH, MLP_INPUTS, MLP_IN_PAD = 128, 5, 16
+#: packed parameter layout of the warm-start network: (name, shape) in order
+MLP_LAYOUT = (("W1", (128, 16)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 128)),
+              ("b3", (128,)), ("w4", (128,)), ("b4", (1,)))
+MLP_NPARAMS = sum(int(np.prod(sh)) for _, sh in MLP_LAYOUT)
 
 
 class lbm_params(ctypes.Structure):
@@ -111,6 +119,16 @@ def load(path: str = LIB_PATH):
         "lbm_batch_get_state": (i32, [vp, vp, i32]),
         "lbm_batch_convert": (i32, [vp, i32, P(vp)]),
         "lbm_batch_destroy": (i32, [vp]),
+        "lbm_mlp_create": (i32, [vp, i32, vp, P(vp)]),
+        "lbm_mlp_set_params": (i32, [vp, vp]),
+        "lbm_mlp_get_params": (i32, [vp, vp]),
+        "lbm_mlp_gradients": (i32, [vp, vp, vp, i32, vp, P(d)]),
+        "lbm_mlp_train": (i32, [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_ulonglong, vp]),
+        "lbm_mlp_predict": (i32, [vp, vp, i64, vp]),
+        "lbm_mlp_features": (i32, [vp, i32, i32, d, d, d, vp, vp, vp, vp, vp]),
+        "lbm_mlp_warm_start": (i32, [vp, vp, i32, i32, d, d, d, vp, vp]),
+        "lbm_mlp_gemm": (i32, [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp]),
+        "lbm_mlp_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -396,3 +414,110 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- warm-start network
+def mlp_pack(params):
+    """Packed FP32 parameter array from a dict of arrays (W1 may be 128 x 5: padded to 16)."""
+    out = np.zeros(MLP_NPARAMS, dtype=np.float32)
+    off = 0
+    for name, shape in MLP_LAYOUT:
+        n = int(np.prod(shape))
+        a = np.zeros(shape)
+        src = np.asarray(params[name], dtype=np.float64)
+        a[tuple(slice(0, k) for k in src.shape)] = src
+        out[off:off + n] = a.ravel()
+        off += n
+    return out
+
+
+def mlp_unpack(packed):
+    """Dict of FP64 arrays from a packed parameter array (W1 cut to its 5 used inputs)."""
+    out, off = {}, 0
+    for name, shape in MLP_LAYOUT:
+        n = int(np.prod(shape))
+        out[name] = np.asarray(packed[off:off + n], dtype=np.float64).reshape(shape)
+        off += n
+    out["W1"] = out["W1"][:, :MLP_INPUTS].copy()
+    return out
+
+
+def _dev(t):
+    if not (hasattr(t, "data_ptr") and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def lbm_mlp_create(packed, batch_capacity, stream=None):
+    p = np.ascontiguousarray(packed, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(load().lbm_mlp_create(p.ctypes.data, int(batch_capacity), stream, ctypes.byref(h)))
+    return h
+
+
+def lbm_mlp_set_params(h, packed):
+    p = np.ascontiguousarray(packed, dtype=np.float32)
+    _check(load().lbm_mlp_set_params(h, p.ctypes.data))
+
+
+def lbm_mlp_get_params(h):
+    out = np.empty(MLP_NPARAMS, dtype=np.float32)
+    _check(load().lbm_mlp_get_params(h, out.ctypes.data))
+    return out
+
+
+def lbm_mlp_gradients(h, x, t):
+    """x: CUDA float32 tensor (n, 5); t: (n,). Returns (loss, packed gradient array)."""
+    g = np.empty(MLP_NPARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(load().lbm_mlp_gradients(h, _dev(x), _dev(t), int(t.numel()), g.ctypes.data, ctypes.byref(loss)))
+    return loss.value, g
+
+
+def lbm_mlp_train(h, x, t, batch, iters, lr, seed, record=True):
+    losses = np.empty(max(1, iters), dtype=np.float32) if record else None
+    _check(load().lbm_mlp_train(h, _dev(x), _dev(t), int(t.numel()), int(batch), int(iters), float(lr),
+                                int(seed) & 0xFFFFFFFFFFFFFFFF, losses.ctypes.data if record else None))
+    return losses[:iters] if record else None
+
+
+def lbm_mlp_predict(h, x, y):
+    _check(load().lbm_mlp_predict(h, _dev(x), int(x.shape[0]), _dev(y)))
+
+
+def _columns_array(cols):
+    arr = (lbm_column * len(cols))()
+    for i, c in enumerate(cols):
+        arr[i].ny = int(c["ny"])
+        arr[i].gravity_form = int(c.get("form", c.get("gravity_form", 1)))
+        arr[i].T = float(c["T"])
+        arr[i].gx = float(c.get("gx", 0.0))
+        arr[i].gy = float(c.get("gy", 0.0))
+    return arr
+
+
+def lbm_mlp_features(cols, nx, a, b, R, x, t=None, rho=None, mean_rho=None, stream=None):
+    arr = _columns_array(cols)
+    mr = None if mean_rho is None else np.ascontiguousarray(mean_rho, dtype=np.float64)
+    _check(load().lbm_mlp_features(arr, len(cols), int(nx), a, b, R, None if rho is None else _dev(rho),
+                                   None if mr is None else mr.ctypes.data, _dev(x),
+                                   None if t is None else _dev(t), stream))
+
+
+def lbm_mlp_warm_start(h, cols, nx, a, b, R, mean_rho, rho0):
+    arr = _columns_array(cols)
+    mr = np.ascontiguousarray(mean_rho, dtype=np.float64)
+    _check(load().lbm_mlp_warm_start(h, arr, len(cols), int(nx), a, b, R, mr.ctypes.data, _dev(rho0)))
+
+
+def lbm_mlp_gemm(A, B, C, k_split=0, accumulate=False, stream=None):
+    """C (+)= A B^T on the tensor cores; A (M, K), B (N, K): CUDA int16/uint16 tensors holding
+    bfloat16 bit patterns (or torch.bfloat16); C (M, N) CUDA float32."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load().lbm_mlp_gemm(_dev(A), A.stride(0), _dev(B), B.stride(0), _dev(C), C.stride(0), M, N, K,
+                               int(k_split), 1 if accumulate else 0, stream))
+
+
+def lbm_mlp_destroy(h):
+    _check(load().lbm_mlp_destroy(h))

@@ -1,0 +1,205 @@
+"""GPU tests of the warm-start network (lbm_mlp_*) against the FP64 oracle (oracle/mlp.py).
+
+Tolerances:
+* tensor-core GEMM: products of bfloat16 values are exact in FP32 and the FP32 sum of K
+  of them is within K 2^-24 sum|a b| of the exact sum; checked at 2 K 2^-24 sum|a b|;
+* gradients and predictions against the oracle in its bfloat16-storage mode: the two
+  differ by FP32 vs FP64 accumulation and by the rare value that sits on a bfloat16
+  rounding boundary and rounds the other way; 2e-3 relative in norm per parameter block;
+  against the plain FP64 oracle (bfloat16 rounding of every operand): 5e-2.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import eos
+from oracle import mlp as omlp
+from paper_2301_12869_gb300 import _build, inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    if not os.path.exists(lbm.LIB_PATH):
+        _build.build()
+    lbm.load()
+
+
+def bf16_bits(a):
+    """bfloat16 bit patterns (int16 tensor on the GPU) of the bfloat16 rounding of a."""
+    import torch
+
+    r = omlp.to_bf16(a).astype(np.float32)
+    bits = (r.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+    return torch.from_numpy(np.ascontiguousarray(bits)).cuda(), r.astype(np.float64)
+
+
+@pytest.mark.parametrize("M, N, K, k_split, acc", [
+    (128, 128, 64, 0, False),
+    (200, 128, 16, 0, False),     # ragged M, one K step
+    (300, 200, 192, 0, False),    # ragged M and N (two N tiles), three K chunks through both stages
+    (128, 16, 1024, 256, True),   # split K with atomic accumulation, N = 16
+    (256, 128, 640, 0, False),    # ten K chunks
+])
+def test_tensor_core_gemm_matches_exact_product(M, N, K, k_split, acc):
+    import torch
+
+    rng = np.random.default_rng(M + N + K)
+    A, Ar = bf16_bits(rng.normal(size=(M, K)))
+    B, Br = bf16_bits(rng.normal(size=(N, K)))
+    C0 = rng.normal(size=(M, N)).astype(np.float32) if acc else np.zeros((M, N), np.float32)
+    C = torch.from_numpy(C0.copy()).cuda()
+    lbm.lbm_mlp_gemm(A, B, C, k_split=k_split, accumulate=acc)
+    want = Ar @ Br.T + (C0 if acc else 0.0)
+    bound = 2 * K * 2.0**-24 * (np.abs(Ar) @ np.abs(Br).T) + 1e-6 * np.abs(C0)
+    assert np.all(np.abs(C.cpu().numpy() - want) <= bound + 1e-30)
+
+
+def params_for_test(seed=1):
+    P = omlp.init_params(inputs.mlp_draws(seed))
+    rng = np.random.default_rng(seed)
+    for k in ("b1", "b2", "b3"):
+        P[k] = 0.2 * (rng.random(128) - 0.5)
+    P["b4"] = np.array([0.7])
+    return P
+
+
+def features(n, seed):
+    rng = np.random.default_rng(seed)
+    raw = np.column_stack([rng.uniform(0.7, 0.95, n), rng.uniform(-6, -4, n), rng.integers(1, 3, n),
+                           rng.uniform(0.3, 2.5, n), rng.random(n)])
+    t = 1.3 - 1.0 * np.tanh(8.0 * (raw[:, 4] - 0.5)) + 0.2 * (raw[:, 0] - 0.8)
+    return raw.astype(np.float32), t.astype(np.float32)
+
+
+def to_gpu(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_err(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-30)
+
+
+@pytest.mark.parametrize("n", [128, 300])
+def test_gradients_match_oracle(n):
+    P = params_for_test()
+    raw, t = features(n, 5)
+    h = lbm.lbm_mlp_create(lbm.mlp_pack(P), 384)
+    try:
+        # the oracle sees what the network sees: FP32 parameters and FP32 feature rows
+        Pf = lbm.mlp_unpack(lbm.lbm_mlp_get_params(h))
+        x = omlp.normalise(raw.astype(np.float64)).astype(np.float32).astype(np.float64)
+        loss, g = lbm.lbm_mlp_gradients(h, to_gpu(raw), to_gpu(t))
+        G = lbm.mlp_unpack(g)
+        assert np.all(g[:128 * 16].reshape(128, 16)[:, 5:] == 0)  # padded inputs get no gradient
+        l16, g16 = omlp.loss_and_grads(x, t.astype(np.float64), Pf, bf16=True)
+        l64, g64 = omlp.loss_and_grads(x, t.astype(np.float64), Pf)
+        assert loss == pytest.approx(l16, rel=2e-3)
+        for k in g16:
+            assert rel_err(G[k], g16[k]) <= 2e-3, k
+            assert rel_err(G[k], g64[k]) <= 5e-2, k
+    finally:
+        lbm.lbm_mlp_destroy(h)
+
+
+def test_prediction_matches_oracle():
+    import torch
+
+    P = params_for_test(2)
+    raw, _ = features(1000, 6)  # three passes of 384 rows, the last one partial
+    h = lbm.lbm_mlp_create(lbm.mlp_pack(P), 384)
+    try:
+        Pf = lbm.mlp_unpack(lbm.lbm_mlp_get_params(h))
+        y = torch.empty(1000, dtype=torch.float32, device="cuda")
+        lbm.lbm_mlp_predict(h, to_gpu(raw), y)
+        x = omlp.normalise(raw.astype(np.float64)).astype(np.float32).astype(np.float64)
+        want, _ = omlp.forward(x, Pf, bf16=True)
+        assert rel_err(y.cpu().numpy(), want) <= 2e-3
+        assert np.max(np.abs(y.cpu().numpy() - want)) <= 1e-2 * np.max(np.abs(want))
+    finally:
+        lbm.lbm_mlp_destroy(h)
+
+
+def test_adam_steps_match_oracle():
+    """Three training steps with the SplitMix64 minibatches of the input module: the
+    parameters follow the oracle's Adam (bfloat16 mode) to a small fraction of lr."""
+    P = params_for_test(3)
+    raw, t = features(500, 7)
+    lr, batch, seed = 1e-3, 256, 99
+    h = lbm.lbm_mlp_create(lbm.mlp_pack(P), 256)
+    try:
+        Pf = lbm.mlp_unpack(lbm.lbm_mlp_get_params(h))
+        losses = lbm.lbm_mlp_train(h, to_gpu(raw), to_gpu(t), batch, 3, lr, seed)
+        Pg = lbm.mlp_unpack(lbm.lbm_mlp_get_params(h))
+        x = omlp.normalise(raw.astype(np.float64)).astype(np.float32).astype(np.float64)
+        Po = Pf
+        m = {k: np.zeros_like(v) for k, v in Po.items()}
+        v = {k: np.zeros_like(v) for k, v in Po.items()}
+        for step in range(3):
+            idx = inputs.minibatch_indices(500, batch, step, seed)
+            lo, g = omlp.loss_and_grads(x[idx], t[idx].astype(np.float64), Po, bf16=True)
+            assert losses[step] == pytest.approx(lo, rel=5e-3)
+            Po, m, v = omlp.adam_step(Po, g, m, v, step + 1, lr=lr)
+        for k in Po:
+            d = np.abs(Pg[k] - Po[k]).ravel()
+            # a component whose gradient is within rounding of zero may take the opposite sign
+            assert np.mean(d > 0.1 * lr) <= 0.01, k
+            assert np.max(d) <= 6 * lr, k
+    finally:
+        lbm.lbm_mlp_destroy(h)
+
+
+def test_training_lowers_the_loss():
+    raw, t = features(4096, 8)
+    h = lbm.lbm_mlp_create(lbm.mlp_pack(params_for_test(4)), 512)
+    try:
+        losses = lbm.lbm_mlp_train(h, to_gpu(raw), to_gpu(t), 512, 300, 3e-3, 1)
+        assert np.all(np.isfinite(losses))
+        assert np.mean(losses[-20:]) < 0.05 * np.mean(losses[:5])
+    finally:
+        lbm.lbm_mlp_destroy(h)
+
+
+def test_features_and_warm_start_profile():
+    import torch
+
+    a, b, R = 0.25, 4.0, 1.0
+    rho_c, T_c, _ = eos.critical_point(a, b, R)
+    cols = [dict(ny=64, T=0.8 * T_c, gy=-1e-5, form=1), dict(ny=128, T=0.9 * T_c, gy=-3e-6, form=2),
+            dict(ny=16, T=0.75 * T_c, gy=-1e-4, form=1)]
+    mean = np.array([0.12, 0.15, 0.2])
+    nx = 4
+    rows = sum(c["ny"] for c in cols)
+    x = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    lbm.lbm_mlp_features(cols, nx, a, b, R, x, mean_rho=mean)
+    want = np.concatenate([np.column_stack([np.full(c["ny"], c["T"] / T_c), np.full(c["ny"], np.log10(abs(c["gy"]))),
+                                            np.full(c["ny"], c["form"]), np.full(c["ny"], m / rho_c),
+                                            (np.arange(c["ny"]) + 0.5) / c["ny"]]) for c, m in zip(cols, mean)])
+    np.testing.assert_allclose(x.cpu().numpy(), want, rtol=1e-6)
+    h = lbm.lbm_mlp_create(lbm.mlp_pack(params_for_test(5)), 128)
+    try:
+        rho0 = torch.empty(nx * rows, dtype=torch.float64, device="cuda")
+        lbm.lbm_mlp_warm_start(h, cols, nx, a, b, R, mean, rho0)
+        r = rho0.cpu().numpy()
+        off = 0
+        for c, m in zip(cols, mean):
+            blk = r[off:off + nx * c["ny"]].reshape(c["ny"], nx)
+            off += nx * c["ny"]
+            assert np.all(blk == blk[:, :1])              # the same on every x
+            assert blk.mean() == pytest.approx(m, rel=1e-12)  # mass of the column kept exactly
+            assert np.all(blk > 0)
+        # features from the columns' own density fields: <rho> from the field, targets rho/rho_c
+        t = torch.empty(rows, dtype=torch.float32, device="cuda")
+        lbm.lbm_mlp_features(cols, nx, a, b, R, x, t=t, rho=rho0)
+        np.testing.assert_allclose(x.cpu().numpy()[:, 3], want[:, 3], rtol=1e-6)
+        np.testing.assert_allclose(t.cpu().numpy(), r.reshape(-1, nx)[:, 0] / rho_c, rtol=1e-6)
+    finally:
+        lbm.lbm_mlp_destroy(h)
