@@ -250,6 +250,39 @@ def run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot):
 
 
 # ---------------------------------------------------------------- batched columns
+def column_set(n, seed, heights, lbm, inputs):
+    """n seeded 4 x H columns of the batched generator with H in heights: descriptors and
+    the concatenated tanh initial densities."""
+    import numpy as np
+
+    gen = [c for c in inputs.batched_columns(4 * n, seed=seed) if c["ny"] in heights][:n]
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    cols, rhos = [], []
+    for c in gen:
+        T = c["Tr"] * Tc
+        rv, rl, _ = lbm.lbm_coexistence(A, B, R, T)
+        rhos.append(inputs.column_rho0(4, c["ny"], rl, rv, max(1, int(round(c["liquid_fraction"] * c["ny"])))))
+        cols.append(dict(ny=c["ny"], T=T, gy=c["gy"], form=c["form"]))
+    return cols, np.concatenate([r.ravel() for r in rhos])
+
+
+def run_to_steady(lbm, cols, rho0, cap, fp32_first):
+    """FP64 alone, or FP32 to 1e-7 then FP64 from that state, to residual 1e-10 (checked
+    every 100 steps). Returns (device seconds, steps, residual, status, batch handle)."""
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    if fp32_first:
+        b32 = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols, rho0)
+        t32 = lbm.lbm_batch_run(b32, 1e-7, cap, 100)
+        b = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
+        lbm.lbm_batch_destroy(b32)
+    else:
+        t32 = 0.0
+        b = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp64", a=A, b=B, R=R), cols, rho0)
+    t64 = lbm.lbm_batch_run(b, 1e-10, cap, 100)
+    st, res, status = lbm.lbm_batch_results(b, len(cols), check=False)
+    return t32 + t64, st, res, status, b
+
+
 def run_columns(args):
     """Time to steady state of independent liquid columns (the batched workload): seeded
     4 x H columns from the batched-column generator (T/T_c ~ U[0.70, 0.95], |g| log-uniform
@@ -261,15 +294,8 @@ def run_columns(args):
     from paper_2301_12869_gb300 import inputs, lbm
 
     heights = tuple(int(h) for h in args.column_heights.split(","))
-    gen = [c for c in inputs.batched_columns(4 * args.columns, seed=SEED) if c["ny"] in heights][: args.columns]
+    cols, rho = column_set(args.columns, SEED, heights, lbm, inputs)
     _, Tc, _ = lbm.lbm_critical_point(A, B, R)
-    cols, rhos = [], []
-    for c in gen:
-        T = c["Tr"] * Tc
-        rv, rl, _ = lbm.lbm_coexistence(A, B, R, T)
-        rhos.append(inputs.column_rho0(4, c["ny"], rl, rv, max(1, int(round(c["liquid_fraction"] * c["ny"])))))
-        cols.append(dict(ny=c["ny"], T=T, gy=c["gy"], form=c["form"]))
-    rho = np.concatenate([r.ravel() for r in rhos])
     nodes = rho.size
     cap = args.column_max_steps
     out = {}
@@ -443,6 +469,104 @@ def run_thermal(args, torch, lbm, inputs):
     return 0 if status == 0 else 2
 
 
+# ---------------------------------------------------------------- learned warm start
+def run_warmstart(args):
+    """Config 5: steady columns generated by the batch runner train the warm-start network
+    on the GPU; held-out seeded columns then run to residual 1e-10 from the tanh profile and
+    from the network's (mass-corrected) profile, in FP64 alone and FP32 then FP64."""
+    import numpy as np
+    import torch
+
+    from paper_2301_12869_gb300 import inputs, lbm
+
+    heights = tuple(int(h) for h in args.column_heights.split(","))
+    rho_c, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    cap = args.column_max_steps
+    out = {"metric": "time to steady state (residual 1e-10), batched columns, FP32 + warm start vs plain FP64",
+           "unit": "s", "higher_is_better": False, "impl": "gb300", "n_gpus": 1}
+    # ---- training data: steady profiles of the method (FP32 to its rounding floor)
+    cols_tr, rho_tr = column_set(args.train_columns, SEED + 1, heights, lbm, inputs)
+    b = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols_tr, rho_tr)
+    t_gen = lbm.lbm_batch_run(b, 1e-7, cap, 100)
+    _, res, status = lbm.lbm_batch_results(b, len(cols_tr), check=False)
+    rho_dev = torch.empty(rho_tr.size, dtype=torch.float64, device="cuda")
+    lbm.lbm_batch_moments(b, rho=rho_dev)
+    lbm.lbm_batch_destroy(b)
+    rows = sum(c["ny"] for c in cols_tr)
+    x_all = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    t_all = torch.empty(rows, dtype=torch.float32, device="cuda")
+    lbm.lbm_mlp_features(cols_tr, 4, A, B, R, x_all, t=t_all, rho=rho_dev)
+    good = (res <= 1e-7) & (status == 0)
+    row_mask = torch.from_numpy(np.repeat(good, [c["ny"] for c in cols_tr])).cuda()
+    x, t = x_all[row_mask].contiguous(), t_all[row_mask].contiguous()
+    del rho_dev, x_all, t_all
+    # ---- training
+    h = lbm.lbm_mlp_create(lbm.mlp_initial_params(SEED), args.mlp_batch)
+    t0 = time.perf_counter()
+    losses = []
+    for frac, lr in ((0.5, 1e-3), (0.3, 3e-4), (0.2, 1e-4)):
+        losses.append(lbm.lbm_mlp_train(h, x, t, args.mlp_batch, int(frac * args.mlp_iters), lr, SEED + len(losses)))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    losses = np.concatenate(losses)
+    out["training"] = {"columns": len(cols_tr), "converged_columns": int(good.sum()), "rows": int(x.shape[0]),
+                       "generation_s": t_gen, "train_s": t_train, "iters": int(losses.size), "batch": args.mlp_batch,
+                       "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-200:]))}
+    # ---- held-out columns: tanh start vs warm start
+    cols, rho0 = column_set(args.columns, SEED + 2, heights, lbm, inputs)
+    sizes = [4 * c["ny"] for c in cols]
+    mean = np.array([blk.mean() for blk in np.split(rho0, np.cumsum(sizes)[:-1])])
+    rho_ml = torch.empty(rho0.size, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_mlp_warm_start(h, cols, 4, A, B, R, mean, rho_ml)
+    t_inf = time.perf_counter() - t0
+    lbm.lbm_mlp_destroy(h)
+    runs = {}
+    final = {}
+    for name, init, fp32_first in (("fp64_tanh", rho0, False), ("fp32_fp64_tanh", rho0, True),
+                                   ("fp64_warm", rho_ml, False), ("fp32_fp64_warm", rho_ml, True)):
+        sec, st, res, status, bb = run_to_steady(lbm, cols, init, cap, fp32_first)
+        final[name] = torch.empty(rho0.size, dtype=torch.float64, device="cuda")
+        lbm.lbm_batch_moments(bb, rho=final[name])
+        lbm.lbm_batch_destroy(bb)
+        runs[name] = dict(seconds=sec + (t_inf if "warm" in name else 0.0), steps=st, ok=(res <= 1e-10) & (status == 0),
+                          nonphysical=int((status != 0).sum()))
+    ok = np.logical_and.reduce([r["ok"] for r in runs.values()])
+    def per_column_max(v):
+        return np.array([blk.max() for blk in np.split(np.abs(v), np.cumsum(sizes)[:-1])])
+
+    # profile error of the network's start against the converged plain-FP64 profile
+    ref = final["fp64_tanh"]
+    per_col = per_column_max((rho_ml - ref).cpu().numpy())
+    per_col_tanh = per_column_max(rho0 - ref.cpu().numpy())
+    # final profiles against the plain FP64 run: FP32 mass rounding moves the FP32 paths'
+    # steady states slightly; a start that settles in another basin (a column's steady
+    # state need not be unique) differs by O(0.1): counted above 1e-3
+    diff = {}
+    for k in final:
+        d = per_column_max((final[k] - ref).cpu().numpy())[ok]
+        diff[k] = {"median": float(np.median(d)), "p90": float(np.percentile(d, 90)), "max": float(d.max()),
+                   "columns_over_1e-3": int(np.sum(d > 1e-3))}
+    out["config"] = {"workload": f"{len(cols)} held-out seeded 4xH liquid columns, H in {heights}; network trained on "
+                                 f"{len(cols_tr)} steady columns of another seed", "max_steps": cap, "check_every": 100}
+    out["runs"] = {k: {"seconds": v["seconds"], "converged": int(v["ok"].sum()), "nonphysical": v["nonphysical"],
+                       "steps_all_converged": int(v["steps"][ok].sum())} for k, v in runs.items()}
+    out["columns_converged_in_all_runs"] = int(ok.sum())
+    out["warm_start_inference_s"] = t_inf
+    out["final_profile_difference_vs_plain_fp64"] = diff
+    out["start_profile_error"] = {"network_max_abs_median": float(np.median(per_col[ok])),
+                                  "tanh_max_abs_median": float(np.median(per_col_tanh[ok])),
+                                  "network_max_abs_p90": float(np.percentile(per_col[ok], 90)),
+                                  "tanh_max_abs_p90": float(np.percentile(per_col_tanh[ok], 90))}
+    out["value"] = runs["fp32_fp64_warm"]["seconds"]
+    out["speedup_vs_plain_fp64"] = runs["fp64_tanh"]["seconds"] / runs["fp32_fp64_warm"]["seconds"]
+    out["steps_ratio_warm_vs_tanh_fp64"] = out["runs"]["fp64_warm"]["steps_all_converged"] / max(
+        1, out["runs"]["fp64_tanh"]["steps_all_converged"])
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- main
 def run_reference(args, world, rank):
     if rank != 0:
@@ -473,7 +597,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
-    ap.add_argument("--workload", choices=["domain", "columns", "thermal"], default="domain",
+    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart"], default="domain",
                     help="domain: the 1024 x 4096 single-domain throughput line (default); "
                          "columns: time to steady state of batched columns; "
                          "thermal: the 512 x 2048 thermal column")
@@ -483,6 +607,9 @@ def main(argv=None):
     ap.add_argument("--columns", type=int, default=1024)
     ap.add_argument("--column-heights", default="64,128")
     ap.add_argument("--column-max-steps", type=int, default=200000)
+    ap.add_argument("--train-columns", type=int, default=16384)
+    ap.add_argument("--mlp-iters", type=int, default=6000)
+    ap.add_argument("--mlp-batch", type=int, default=8192)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -492,6 +619,8 @@ def main(argv=None):
         return run_reference(args, world, rank)
     if args.workload == "columns":
         return run_columns(args) if rank == 0 else 0
+    if args.workload == "warmstart":
+        return run_warmstart(args) if rank == 0 else 0
 
     import numpy as np
     import torch

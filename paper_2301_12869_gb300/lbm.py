@@ -442,6 +442,19 @@ def mlp_unpack(packed):
     return out
 
 
+def mlp_initial_params(seed):
+    """Initial packed parameters: every weight uniform in +-sqrt(6/(fan_in + fan_out)) from the
+    seeded draws of the input module, biases zero."""
+    from . import inputs
+
+    u = inputs.mlp_draws(seed, MLP_WIDTH, MLP_INPUTS)
+    fan = {"W1": (MLP_INPUTS, MLP_WIDTH), "W2": (MLP_WIDTH, MLP_WIDTH), "W3": (MLP_WIDTH, MLP_WIDTH),
+           "w4": (MLP_WIDTH, 1)}
+    P = {k: (2.0 * u[k] - 1.0) * np.sqrt(6.0 / sum(fan[k])) for k in fan}
+    P.update(b1=np.zeros(MLP_WIDTH), b2=np.zeros(MLP_WIDTH), b3=np.zeros(MLP_WIDTH), b4=np.zeros(1))
+    return mlp_pack(P)
+
+
 def _dev(t):
     if not (hasattr(t, "data_ptr") and t.is_cuda and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA tensor")

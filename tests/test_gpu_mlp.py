@@ -203,3 +203,72 @@ def test_features_and_warm_start_profile():
         np.testing.assert_allclose(t.cpu().numpy(), r.reshape(-1, nx)[:, 0] / rho_c, rtol=1e-6)
     finally:
         lbm.lbm_mlp_destroy(h)
+
+
+def test_warm_start_gain_on_held_out_columns():
+    """What the trained network gains over the method without it, on held-out columns:
+    trained on the steady profiles of 512 seeded 4 x 64 columns (FP32 runs of the method),
+    its mass-corrected start is closer to the converged profile than the tanh start, and the
+    lattice Boltzmann run from it reaches the tanh start's steady state on most columns (the
+    network only initialises; the FP64 run to 1e-10 is the judge)."""
+    import torch
+
+    a, b, R = 0.25, 4.0, 1.0
+    rho_c, T_c, _ = eos.critical_point(a, b, R)
+
+    def columns(n, seed):
+        gen = [c for c in inputs.batched_columns(8 * n, seed=seed) if c["ny"] == 64][:n]
+        cols, rhos = [], []
+        for c in gen:
+            rv, rl, _ = eos.maxwell(c["Tr"] * T_c, a, b, R)
+            rhos.append(inputs.column_rho0(4, 64, rl, rv, max(1, int(round(c["liquid_fraction"] * 64)))))
+            cols.append(dict(ny=64, T=c["Tr"] * T_c, gy=c["gy"], form=c["form"]))
+        return cols, np.concatenate([r.ravel() for r in rhos])
+
+    p32 = lbm.make_params(4, 8, 0.8 * T_C_of(a, b, R), "fp32", a=a)
+    p64 = lbm.make_params(4, 8, 0.8 * T_C_of(a, b, R), "fp64", a=a)
+    cols, rho = columns(512, 11)
+    bt = lbm.lbm_batch_init(p32, cols, rho)
+    lbm.lbm_batch_run(bt, 1e-7, 100000, 100)
+    _, res, status = lbm.lbm_batch_results(bt, len(cols), check=False)
+    rho_dev = torch.empty(rho.size, dtype=torch.float64, device="cuda")
+    lbm.lbm_batch_moments(bt, rho=rho_dev)
+    lbm.lbm_batch_destroy(bt)
+    x = torch.empty((64 * len(cols), 5), dtype=torch.float32, device="cuda")
+    t = torch.empty(64 * len(cols), dtype=torch.float32, device="cuda")
+    lbm.lbm_mlp_features(cols, 4, a, b, R, x, t=t, rho=rho_dev)
+    keep = torch.from_numpy(np.repeat((res <= 1e-7) & (status == 0), 64)).cuda()
+    h = lbm.lbm_mlp_create(lbm.mlp_initial_params(3), 4096)
+    try:
+        lbm.lbm_mlp_train(h, x[keep].contiguous(), t[keep].contiguous(), 4096, 1500, 1e-3, 5, record=False)
+        ev, rho0 = columns(128, 12)
+        mean = rho0.reshape(len(ev), -1).mean(axis=1)
+        warm = torch.empty(rho0.size, dtype=torch.float64, device="cuda")
+        lbm.lbm_mlp_warm_start(h, ev, 4, a, b, R, mean, warm)
+    finally:
+        lbm.lbm_mlp_destroy(h)
+    finals = []
+    for start in (rho0, warm):
+        bb = lbm.lbm_batch_init(p64, ev, start)
+        lbm.lbm_batch_run(bb, 1e-10, 200000, 100)
+        _, res, status = lbm.lbm_batch_results(bb, len(ev), check=False)
+        f = np.empty(rho0.size)
+        lbm.lbm_batch_moments(bb, rho=f)
+        lbm.lbm_batch_destroy(bb)
+        finals.append((f, (res <= 1e-10) & (status == 0)))
+    ok = finals[0][1] & finals[1][1]
+    assert ok.sum() >= 0.8 * len(ev)
+    per = lambda v: np.abs(v).reshape(len(ev), -1).max(axis=1)  # noqa: E731
+    err_tanh = per(rho0 - finals[0][0])[ok]
+    err_warm = per(warm.cpu().numpy() - finals[0][0])[ok]
+    assert np.median(err_warm) < np.median(err_tanh)
+    # a column's steady state need not be unique: a start can settle in another basin (a
+    # "miss", which only the plain run reveals). Runs stopped at a per-step change of 1e-10
+    # are within 1e-10 / (1 - r) of their fixed point, r the per-step decay factor of the
+    # slowest mode (1 - r ~ 5e-4 here): same state = within 1e-5. Most columns agree.
+    same = per(finals[1][0] - finals[0][0])[ok] <= 1e-5
+    assert np.mean(same) >= 0.9
+
+
+def T_C_of(a, b, R):
+    return eos.critical_point(a, b, R)[1]
