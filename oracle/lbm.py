@@ -123,6 +123,7 @@ class Params:
     tau_nu: float = 1.0
     g: tuple = (0.0, 0.0)
     form: int = 1
+    wall: str = "bounce-back"   # or "zou-he" (wet-node walls on rows 0 and ny-1, Sec. III)
 
     def Lambda(self):
         """Eq. RelaxationMatrix."""
@@ -182,6 +183,43 @@ def stream(fstar):
         else:
             f[i, :-1] = shifted[1:]          # from row y + 1
             f[i, -1] = fstar[OPP[i], -1]     # link from above the top wall
+    return f
+
+
+def zou_he(f, p, mean_rho):
+    """Wet-node no-slip walls on rows 0 and ny - 1 (Sec. III cites Zou and He for the solid
+    walls): after streaming, the populations that would enter each wall node from outside
+    (bottom: c_y = +1, i = 2, 5, 6; top: c_y = -1, i = 4, 7, 8) are set so that the node's
+    velocity of Eq. Momentum - including the half force - vanishes, with the non-equilibrium
+    part of the normal population bounced back (f_2 - f_2^eq = f_4 - f_4^eq at u = 0).
+    At the wall nodes F_int = 0 (Sec. III boundary rule), so F = F_g, whose rho dependence
+    makes the wall density the solution of a linear equation: bottom
+    rho = K - F_y/2, K = f0 + f1 + f3 + 2 (f4 + f7 + f8); top rho = K + F_y/2,
+    K = f0 + f1 + f3 + 2 (f2 + f5 + f6). Modifies f in place."""
+    gx, gy = p.g
+    for row, sgn in ((0, 1.0), (-1, -1.0)):
+        q = f[:, row]
+        if sgn > 0:
+            K = q[0] + q[1] + q[3] + 2.0 * (q[4] + q[7] + q[8])
+        else:
+            K = q[0] + q[1] + q[3] + 2.0 * (q[2] + q[5] + q[6])
+        # rho (1 + sgn gy / 2) = K (form 1); = K + sgn <rho> gy / 2 (form 2)
+        if p.form == 1:
+            rho = K / (1.0 + sgn * 0.5 * gy)
+            base = rho
+        else:
+            rho = (K + sgn * 0.5 * mean_rho * gy) / (1.0 + sgn * 0.5 * gy)
+            base = rho - mean_rho
+        Fx, Fy = base * gx, base * gy
+        d13 = q[1] - q[3]
+        if sgn > 0:
+            q[2] = q[4]
+            q[5] = q[7] - 0.5 * d13 - 0.25 * (Fx + Fy)
+            q[6] = q[8] + 0.5 * d13 + 0.25 * (Fx - Fy)
+        else:
+            q[4] = q[2]
+            q[7] = q[5] + 0.5 * d13 + 0.25 * (Fx + Fy)
+            q[8] = q[6] - 0.5 * d13 + 0.25 * (Fy - Fx)
     return f
 
 
@@ -298,6 +336,14 @@ def macroscopic(fstar, p, mean_rho=None):
     passes a patch cut out of a larger domain (whose mean it computed itself).
     """
     f = stream(fstar)
+    if p.wall == "zou-he":
+        # <rho> of Eq. Gravity_2: the mass of the stored state (the wall nodes' densities
+        # are rebuilt below; with bounce-back the two definitions coincide)
+        if mean_rho is None:
+            mean_rho = float(np.sum(fstar)) / fstar[0].size
+        zou_he(f, p, mean_rho)
+    elif p.wall != "bounce-back":
+        raise ValueError(f"wall {p.wall}")
     rho = density(f)
     psi, bad = interaction_potential(rho, p)
     if mean_rho is None:
