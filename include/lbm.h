@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 2
+#define LBM_ABI_VERSION 3
 
 /* ---- status codes */
 enum {
@@ -50,6 +50,14 @@ enum {
 enum { LBM_FP64 = 0, LBM_FP32 = 1 };                              /* storage and arithmetic */
 enum { LBM_GRAVITY_RHO_G = 1, LBM_GRAVITY_RHO_MINUS_MEAN_G = 2 }; /* Eq. Gravity_1 / _2 */
 enum { LBM_HOST = 0, LBM_DEVICE = 1 };                            /* where a buffer lives */
+/* walls below row 0 and above row ny-1 */
+enum {
+  LBM_WALL_BOUNCE_BACK = 0, /* halfway bounce-back: walls half a link beyond rows 0 and ny-1,
+                               exact mass conservation */
+  LBM_WALL_ZOU_HE = 1       /* Zou-He wet nodes (Sec. III): rows 0 and ny-1 are wall nodes
+                               whose incoming populations give zero velocity (half force
+                               included); mass is conserved only up to the wall closure */
+};
 enum {
   LBM_REDUCE_MASS = 0,        /* out[0] = sum over nodes of rho (FP64)                      */
   LBM_REDUCE_MEAN_RHO = 1,    /* out[0] = <rho> = mass / (nx ny), as used by Eq. Gravity_2   */
@@ -87,12 +95,15 @@ typedef struct lbm_params {
   double kappa;           /* thermal conductivity (>= 0) */
   double T_bot, T_top;    /* wall temperatures below row 0 and above row ny-1 (> 0), imposed
                              half a link beyond the rows like the bounce-back walls */
+  int32_t wall;           /* LBM_WALL_BOUNCE_BACK (default) or LBM_WALL_ZOU_HE (ny >= 3); with
+                             Zou-He, <rho> of Eq. Gravity_2 is the stored state's mass / (nx ny) */
+  int32_t reserved1;      /* must be 0 */
 } lbm_params;
 
 typedef struct lbm_handle lbm_handle;
 
 /* Paper defaults: a = 0.5, b = 4, R = 1 (Sec. IV), G = -1, sigma = 1.385, all tau = 1
- * (Sec. IV), gravity off, form 1, FP64, rho_ref = NaN, no workspace, isothermal, with
+ * (Sec. IV), gravity off, form 1, FP64, rho_ref = NaN, no workspace, bounce-back walls, isothermal, with
  * c_v = 5 and kappa = 0.02 (Sec. IV) ready for thermal = 1. nx, ny, T, T_bot, T_top unset (0). */
 void lbm_params_default(lbm_params* p);
 
@@ -172,8 +183,8 @@ int lbm_launch_info(const lbm_handle* h, int* grid, int* block, int* smem_bytes,
  * CTA) for `steps` launches on this lattice - every candidate reads the current state and
  * writes the spare buffer, so the state is unchanged - and keeps the fastest for later
  * lbm_step / lbm_moments calls. variant, ms (mean time per step of the winner): may be NULL.
- * A thermal handle considers only the variants that carry thermal kernels (variant 0 of
- * each precision). Synchronises the handle's stream. */
+ * A thermal or Zou-He handle considers only the variants that carry those kernels (variant 0
+ * of each precision). Synchronises the handle's stream. */
 int lbm_autotune(lbm_handle* h, int steps, int* variant, double* ms);
 
 /* Number of tile variants of the fused kernel for a precision (LBM_EINVAL otherwise). */
@@ -181,7 +192,8 @@ int lbm_tile_variants(int precision);
 
 /* Use tile variant `variant` (0 = default, as chosen by lbm_init) for later steps, e.g. a
  * result of lbm_autotune saved from an earlier run. LBM_EINVAL if out of range, or if the
- * handle is thermal and the variant has no thermal kernels (only variant 0 has). */
+ * handle is thermal or has Zou-He walls and the variant lacks those kernels (only variant 0
+ * has them). */
 int lbm_set_tiling(lbm_handle* h, int variant);
 
 /* ---- batched independent columns: the 1-D liquid-column problem of Sec. IV for many
@@ -199,7 +211,7 @@ typedef struct lbm_column {
 
 typedef struct lbm_batch lbm_batch;
 
-/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->thermal must be 0;
+/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->thermal and p->wall must be 0;
  * p->ny, p->T, p->gx, p->gy, p->gravity_form and p->workspace are ignored; p->rho_ref NaN means: each column's
  * mean rho0 in FP32, 0 in FP64). cols: ncols descriptors (host). rho0: the columns' initial
  * densities concatenated, column c holding nx * ny_c doubles [y][x], in host or device
@@ -316,7 +328,7 @@ int lbm_mlp_destroy(lbm_mlp* h);
  * f_in, f_out: distinct DEVICE arrays of 9*nx*ny reals (float for LBM_FP32, double for
  *   LBM_FP64), layout [i][y][x] in the order of Eq. VelocitySet, holding the deviations
  *   f_i - w_i rho_ref with rho_ref = p->rho_ref (NaN means 0). Caller-owned; read / written.
- * p: as for lbm_init, isothermal (thermal = 0); p->workspace is ignored. stream: a cudaStream_t (NULL = default).
+ * p: as for lbm_init, isothermal (thermal = 0), any wall; p->workspace is ignored. stream: a cudaStream_t (NULL = default).
  * Scratch: the FP64 partial mass sums that give <rho> (Eq. Gravity_2) and a status word
  *   live in a file-scope __device__ array of 65 792 bytes inside liblbm, held by every
  *   device that loads the library until the process exits. Its 4096 partial slots bound

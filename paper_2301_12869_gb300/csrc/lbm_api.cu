@@ -155,8 +155,8 @@ int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int
     set_err(err, "unknown tile variant %d", variant);
     return LBM_EINVAL;
   }
-  if (p.thermal && !lbm::step_variant_thermal(p.precision, variant)) {
-    set_err(err, "tile variant %d has no thermal kernels", variant);
+  if ((p.thermal || p.wall == LBM_WALL_ZOU_HE) && !lbm::step_variant_extended(p.precision, variant)) {
+    set_err(err, "tile variant %d has no thermal or Zou-He kernels", variant);
     return LBM_EINVAL;
   }
   t->variant = variant;
@@ -184,7 +184,7 @@ int max_partials(const lbm_params& p, int nsm, char* err) {
   int P = 0;
   for (int v = 0; v < lbm::step_num_variants(p.precision); ++v) {
     lbm::StepTiling t;
-    if (p.thermal && !lbm::step_variant_thermal(p.precision, v)) continue;
+    if ((p.thermal || p.wall == LBM_WALL_ZOU_HE) && !lbm::step_variant_extended(p.precision, v)) continue;
     if (plan_tiling(p, nsm, &t, err, v)) return -1;
     P = std::max(P, t.nbands * t.nstrips);
   }
@@ -238,6 +238,11 @@ int validate(const lbm_params* p, char* err) {
     set_err(err, "gravity_form must be LBM_GRAVITY_RHO_G or LBM_GRAVITY_RHO_MINUS_MEAN_G"); return LBM_EINVAL;
   }
   if (p->thermal != 0 && p->thermal != 1) { set_err(err, "thermal must be 0 or 1"); return LBM_EINVAL; }
+  if (p->wall != LBM_WALL_BOUNCE_BACK && p->wall != LBM_WALL_ZOU_HE) {
+    set_err(err, "wall must be LBM_WALL_BOUNCE_BACK or LBM_WALL_ZOU_HE"); return LBM_EINVAL;
+  }
+  if (p->wall == LBM_WALL_ZOU_HE && p->ny < 3) { set_err(err, "Zou-He walls need ny >= 3"); return LBM_EINVAL; }
+  if (p->reserved1 != 0) { set_err(err, "reserved1 must be 0"); return LBM_EINVAL; }
   if (p->thermal && !(p->c_v > 0 && p->kappa >= 0 && p->T_bot > 0 && p->T_top > 0 && std::isfinite(p->c_v) &&
                       std::isfinite(p->kappa) && std::isfinite(p->T_bot) && std::isfinite(p->T_top))) {
     set_err(err, "thermal variant needs c_v > 0, kappa >= 0, T_bot > 0, T_top > 0");
@@ -264,6 +269,7 @@ lbm::StepPhys phys_of(const lbm_params& p, double rho_ref) {
   k.gx = p.gx;
   k.gy = p.gy;
   k.form = p.gravity_form;
+  k.wall = p.wall;
   return k;
 }
 
@@ -641,8 +647,8 @@ int lbm_set_params(lbm_handle* h, const lbm_params* p) {
   int rc = validate(p, h->err);
   if (rc) return rc;
   if (p->nx != h->p.nx || p->ny != h->p.ny || p->precision != h->p.precision || p->a != h->p.a || p->b != h->p.b ||
-      p->R != h->p.R || p->thermal != h->p.thermal) {
-    set_err(h->err, "nx, ny, precision, a, b, R and thermal cannot change on a live handle");
+      p->R != h->p.R || p->thermal != h->p.thermal || p->wall != h->p.wall) {
+    set_err(h->err, "nx, ny, precision, a, b, R, thermal and wall cannot change on a live handle");
     return LBM_EINVAL;
   }
   const double rho_ref = h->p.rho_ref;

@@ -379,6 +379,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   int rc = lbm::validate_params(&q, err);
   if (rc) return bfail(rc, err);
   if (p->thermal) return bfail(LBM_EINVAL, "batched columns are isothermal (thermal must be 0)");
+  if (p->wall != LBM_WALL_BOUNCE_BACK) return bfail(LBM_EINVAL, "batched columns use bounce-back walls (wall must be 0)");
   if (p->nx > 64) return bfail(LBM_EINVAL, "batched columns are at most 64 nodes wide");
   if (rho0_where != LBM_HOST && rho0_where != LBM_DEVICE) return bfail(LBM_EINVAL, "rho0_where must be LBM_HOST or LBM_DEVICE");
   lbm_batch* b = new (std::nothrow) lbm_batch();

@@ -23,6 +23,7 @@ struct StepPhys {
   double sig_e, sig_vs;    // sigma/(tau_e - 1/2), sigma/(tau_varsigma - 1/2) of Eq. LiFS
   double gx, gy;           // gravity
   int form;                // 1: rho g (Eq. Gravity_1), 2: (rho - <rho>) g (Eq. Gravity_2)
+  int wall;                // LBM_WALL_BOUNCE_BACK or LBM_WALL_ZOU_HE
 };
 
 // Tiling of the fused step: CTA b covers band (b % nbands) of width band_w along x
@@ -52,7 +53,8 @@ struct StepIO {
 // ---- launch wrappers (lbm_kernels.cu). All are asynchronous on `stream`.
 int stages();  // pipeline depth of the fused kernel
 int step_num_variants(int precision);
-bool step_variant_thermal(int precision, int variant);  // has thermal kernels (io.Tfield set)
+// has the thermal and Zou-He wall kernels (io.Tfield set, StepPhys::wall = LBM_WALL_ZOU_HE)
+bool step_variant_extended(int precision, int variant);
 // widest x band one CTA covers, threads per CTA, dynamic shared bytes of a tile variant
 bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem);
 int step_max_ctas_per_sm(int precision, int variant, int threads, int smem_bytes);

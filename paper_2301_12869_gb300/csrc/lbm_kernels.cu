@@ -115,11 +115,12 @@ __device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (
 // Template parameters: storage type T, value type V (T, or f2 for pairs of FP32 nodes),
 // mode, all-unit relaxation, band width BW (nodes along x per CTA), nodes per thread NPT
 // (threads = BW / NPT; a thread owns NPT / width(V) values), CTAs per SM the launch
-// bounds aim for; TH: thermal variant, psi uses R T(x) of the field io.Tfield (else R T).
+// bounds aim for; TH: thermal variant, psi uses R T(x) of the field io.Tfield (else R T);
+// ZH: Zou-He wet-node walls on rows 0 and ny - 1 (else halfway bounce-back).
 // CTA b: x band (b % nbands) of width tl.band_w (<= BW), strip (b / nbands) of
 // tl.strip_h rows. Even strips walk their rows upward, odd strips downward, so two
 // neighbouring strips reach their common halo rows at the same time (L2 reuse).
-template <typename T, typename V, int MODE, bool UNIT, int BW, int NPT, int MINB, bool TH = false>
+template <typename T, typename V, int MODE, bool UNIT, int BW, int NPT, int MINB, bool TH = false, bool ZH = false>
 __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling tl, const PhysT<V> k, const StepIO io) {
   constexpr int NT = BW / NPT;
   constexpr int VW = VecTraits<V>::width;  // nodes per value
@@ -232,6 +233,9 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
       if (!FULL && j > w) continue;
       V g[9];
       pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+      if constexpr (ZH) {
+        if (!interior) zou_he(g, lo_wall, dmean, k);
+      }
       V Sx = cst<V>(0.0), Sy = cst<V>(0.0), psi_c;
       const V c13 = cst<V>(1.0 / 3.0), c112 = cst<V>(1.0 / 12.0);
       if constexpr (VW == 1) {
@@ -296,6 +300,9 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
           if (FULL || j <= w) {
             V g[9];
             pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+            if constexpr (ZH) {
+              if (lo_wall || hi_wall) zou_he(g, lo_wall, dmean, k);
+            }
             const V RT = TH ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
             const V psi = psi_of<V>(k.rho_ref + sum9(g), RT, k, flag);
             if constexpr (VW == 1) {
@@ -315,7 +322,18 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
         const int j = lane ? w + 1 : 0;
         T g[9];
         pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
-        const T rho_h = sum9(g);
+        T rho_h;
+        if constexpr (ZH) {
+          V gv[9];
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            if constexpr (VW == 1) gv[i] = g[i]; else gv[i] = make_f2(g[i], g[i]);
+          }
+          if (lo_wall || hi_wall) zou_he(gv, lo_wall, dmean, k);
+          if constexpr (VW == 1) rho_h = sum9(gv); else rho_h = lo(sum9(gv));
+        } else {
+          rho_h = sum9(g);
+        }
         const T Th = TH ? Tf[size_t(q) * nx + wrap_x(xa + j - 1, nx)] : T(0);
         V rho_v, T_v;
         if constexpr (VW == 1) {
@@ -397,7 +415,7 @@ struct PsiRow {  // psi at the left neighbour, the lane's own pair, the right ne
   float r;
 };
 
-template <int MODE, bool UNIT, int NWC, int S, int MINB, bool TH = false>
+template <int MODE, bool UNIT, int NWC, int S, int MINB, bool TH = false, bool ZH = false>
 __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     step_kernel_ws(const StepTiling tl, const PhysT<f2> k, const StepIO io) {
   using T = float;
@@ -512,7 +530,16 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     auto scalar_psi = [&](const T* st, int q, int jh, bool lo_wall, bool hi_wall) {
       T g[9];
       pull<SW>(st, jh - 1 + H, lo_wall, hi_wall, g);
-      const T rh = sum9(g);
+      T rh;
+      if constexpr (ZH) {
+        V gv[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gv[i] = make_f2(g[i], g[i]);
+        if (lo_wall || hi_wall) zou_he(gv, lo_wall, dmean, k);
+        rh = lo(sum9(gv));
+      } else {
+        rh = sum9(g);
+      }
       const T Th = TH ? Tf[size_t(q) * nx + wrap_x(xa + jh - 1, nx)] : T(0);
       const V RT = TH ? k.R * make_f2(Th, Th) : k.RT;
       return lo(psi_of<V>(k.rho_ref + make_f2(rh, rh), RT, k, flag));
@@ -561,6 +588,9 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = cst<V>(0.0);
       if (active) pull<SW>(st, j - 1 + H, lo_wall, hi_wall, g);
+      if constexpr (ZH) {
+        if (active && (lo_wall || hi_wall)) zou_he(g, lo_wall, dmean, k);
+      }
       float el = 0.f, er = 0.f;  // psi of the warp-edge neighbours (another warp's or the halo)
       if (need_l || need_r) {
         const float v = scalar_psi(st, q, need_l ? j - 1 : j + 2, lo_wall, hi_wall);
@@ -741,19 +771,27 @@ using StepFnF = void (*)(StepTiling, PhysT<float>, StepIO);
 using StepFnP = void (*)(StepTiling, PhysT<f2>, StepIO);
 using StepFnD = void (*)(StepTiling, PhysT<double>, StepIO);
 
+template <typename Fn>
+struct ExtFns {  // kernels of one extension of a tile variant (nullptr: not built)
+  Fn step = nullptr, step_unit = nullptr, moments = nullptr;
+};
+// extensions: [0] thermal, [1] Zou-He walls, [2] thermal with Zou-He walls
+constexpr int kExt = 3;
+__host__ __device__ constexpr int ext_index(bool th, bool zh) { return th && zh ? 2 : (zh ? 1 : 0); }
+
 struct VariantF {  // FP32 storage; `paired` variants evaluate two nodes per value
   int bw, threads;
   bool paired;
   StepFnF step, step_unit, moments;      // scalar variants
   StepFnP pstep, pstep_unit, pmoments;   // paired variants
   size_t smem;
-  StepFnP th_step = nullptr, th_step_unit = nullptr, th_moments = nullptr;  // thermal (paired)
+  ExtFns<StepFnP> ext[kExt] = {};        // paired extensions (variant 0 only)
 };
 struct VariantD {
   int bw, threads;
   StepFnD step, step_unit, moments;
   size_t smem;
-  StepFnD th_step = nullptr, th_step_unit = nullptr, th_moments = nullptr;  // thermal
+  ExtFns<StepFnD> ext[kExt] = {};
 };
 
 template <int BW, int NPT, int MINB>
@@ -777,13 +815,19 @@ constexpr VariantD make_d() {
                   step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
 }
-// the same tile with the thermal kernels as well
+// the same tile with the thermal and Zou-He kernels as well
+template <int BW, int NPT, int MINB, bool TH, bool ZH>
+constexpr ExtFns<StepFnD> ext_d() {
+  return {step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB, TH, ZH>,
+          step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB, TH, ZH>,
+          step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB, TH, ZH>};
+}
 template <int BW, int NPT, int MINB>
-constexpr VariantD make_d_th() {
+constexpr VariantD make_d_ext() {
   VariantD v = make_d<BW, NPT, MINB>();
-  v.th_step = step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB, true>;
-  v.th_step_unit = step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB, true>;
-  v.th_moments = step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB, true>;
+  v.ext[0] = ext_d<BW, NPT, MINB, true, false>();
+  v.ext[1] = ext_d<BW, NPT, MINB, false, true>();
+  v.ext[2] = ext_d<BW, NPT, MINB, true, true>();
   return v;
 }
 
@@ -793,17 +837,22 @@ constexpr VariantF make_ws() {
                   step_kernel_ws<MODE_STEP, false, NWC, S, MINB>, step_kernel_ws<MODE_STEP, true, NWC, S, MINB>,
                   step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB>, ws_smem<NWC, S>()};
 }
+template <int NWC, int S, int MINB, bool TH, bool ZH>
+constexpr ExtFns<StepFnP> ext_ws() {
+  return {step_kernel_ws<MODE_STEP, false, NWC, S, MINB, TH, ZH>, step_kernel_ws<MODE_STEP, true, NWC, S, MINB, TH, ZH>,
+          step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB, TH, ZH>};
+}
 template <int NWC, int S, int MINB>
-constexpr VariantF make_ws_th() {
+constexpr VariantF make_ws_ext() {
   VariantF v = make_ws<NWC, S, MINB>();
-  v.th_step = step_kernel_ws<MODE_STEP, false, NWC, S, MINB, true>;
-  v.th_step_unit = step_kernel_ws<MODE_STEP, true, NWC, S, MINB, true>;
-  v.th_moments = step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB, true>;
+  v.ext[0] = ext_ws<NWC, S, MINB, true, false>();
+  v.ext[1] = ext_ws<NWC, S, MINB, false, true>();
+  v.ext[2] = ext_ws<NWC, S, MINB, true, true>();
   return v;
 }
 
 const VariantF kVariantsF[] = {
-    make_ws_th<8, 4, 2>(),   // barrier-free: 8 consumer warps + producer, 4 stages, 75 KB (+ thermal)
+    make_ws_ext<8, 4, 2>(),  // barrier-free: 8 consumer warps + producer, 4 stages, 75 KB (+ thermal, Zou-He)
     make_ws<4, 4, 4>(),      // barrier-free: 4 consumer warps + producer, 4 stages, 38 KB
     make_p<256, 2, 5>(),     // pairs, 4 warps, 42 KB shared, one CTA barrier per row
     make_f<256, 2, 5>(),     // scalar, 4 warps, 42 KB shared, one CTA barrier per row
@@ -812,7 +861,7 @@ const VariantF kVariantsF[] = {
     make_ws<2, 6, 6>(),      // barrier-free, 2 consumer warps, 29 KB
 };
 const VariantD kVariantsD[] = {
-    make_d_th<128, 1, 4>(),  // (+ thermal)
+    make_d_ext<128, 1, 4>(),  // (+ thermal, Zou-He)
     make_d<64, 1, 8>(),
 };
 constexpr int kNumF = sizeof(kVariantsF) / sizeof(kVariantsF[0]);
@@ -827,14 +876,20 @@ cudaError_t prepare_variant(const VariantF& v) {
   cudaError_t e = cudaSuccess;
   for (auto fn : {v.step, v.step_unit, v.moments})
     if (e == cudaSuccess) e = set_smem(fn, v.smem);
-  for (auto fn : {v.pstep, v.pstep_unit, v.pmoments, v.th_step, v.th_step_unit, v.th_moments})
+  for (auto fn : {v.pstep, v.pstep_unit, v.pmoments})
     if (e == cudaSuccess) e = set_smem(fn, v.smem);
+  for (const auto& x : v.ext)
+    for (auto fn : {x.step, x.step_unit, x.moments})
+      if (e == cudaSuccess) e = set_smem(fn, v.smem);
   return e;
 }
 cudaError_t prepare_variant(const VariantD& v) {
   cudaError_t e = cudaSuccess;
-  for (auto fn : {v.step, v.step_unit, v.moments, v.th_step, v.th_step_unit, v.th_moments})
+  for (auto fn : {v.step, v.step_unit, v.moments})
     if (e == cudaSuccess) e = set_smem(fn, v.smem);
+  for (const auto& x : v.ext)
+    for (auto fn : {x.step, x.step_unit, x.moments})
+      if (e == cudaSuccess) e = set_smem(fn, v.smem);
   return e;
 }
 
@@ -856,9 +911,9 @@ int stages() { return kStages; }
 
 int step_num_variants(int precision) { return precision == 1 ? kNumF : kNumD; }
 
-bool step_variant_thermal(int precision, int variant) {
+bool step_variant_extended(int precision, int variant) {
   if (variant < 0 || variant >= step_num_variants(precision)) return false;
-  return precision == 1 ? kVariantsF[variant].th_step != nullptr : kVariantsD[variant].th_step != nullptr;
+  return precision == 1 ? kVariantsF[variant].ext[0].step != nullptr : kVariantsD[variant].ext[0].step != nullptr;
 }
 
 bool step_variant_info(int precision, int variant, int* band_w, int* threads, int* smem) {
@@ -903,12 +958,13 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
                         cudaStream_t stream) {
   const dim3 grid(t.nbands * t.nstrips), block(t.threads);
   const bool unit = unit_relaxation(ph);
-  const bool th = io.Tfield != nullptr;
+  const bool th = io.Tfield != nullptr, zh = ph.wall == LBM_WALL_ZOU_HE;
   if (precision == 1) {
     const VariantF& v = kVariantsF[t.variant];
-    if (th) {
-      const StepFnP fn = mode == MODE_MOMENTS ? v.th_moments : (unit ? v.th_step_unit : v.th_step);
-      if (!fn) return cudaErrorInvalidValue;  // no thermal kernels for this tile variant
+    if (th || zh) {
+      const ExtFns<StepFnP>& x = v.ext[ext_index(th, zh)];
+      const StepFnP fn = mode == MODE_MOMENTS ? x.moments : (unit ? x.step_unit : x.step);
+      if (!fn) return cudaErrorInvalidValue;  // no extension kernels for this tile variant
       fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<f2>(ph), io);
     } else if (v.paired) {
       const StepFnP fn = mode == MODE_MOMENTS ? v.pmoments : (unit ? v.pstep_unit : v.pstep);
@@ -919,9 +975,12 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
     }
   } else {
     const VariantD& v = kVariantsD[t.variant];
-    const StepFnD fn = th ? (mode == MODE_MOMENTS ? v.th_moments : (unit ? v.th_step_unit : v.th_step))
-                          : (mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step));
-    if (!fn) return cudaErrorInvalidValue;  // no thermal kernels for this tile variant
+    StepFnD fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
+    if (th || zh) {
+      const ExtFns<StepFnD>& x = v.ext[ext_index(th, zh)];
+      fn = mode == MODE_MOMENTS ? x.moments : (unit ? x.step_unit : x.step);
+    }
+    if (!fn) return cudaErrorInvalidValue;  // no extension kernels for this tile variant
     fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<double>(ph), io);
   }
   return cudaGetLastError();

@@ -147,6 +147,38 @@ __device__ __forceinline__ V psi_of(V rho, const PhysT<V>& k, int& flag) {
   return psi_of(rho, k.RT, k, flag);
 }
 
+// Zou-He wet-node wall (Sec. III: no-slip condition of Zou and He on the solid walls) at a
+// node of row 0 (bottom) or ny - 1: the populations entering from outside the lattice
+// (bottom: i = 2, 5, 6; top: i = 4, 7, 8) are set so that the velocity of Eq. Momentum,
+// half force included, vanishes, with the normal population's non-equilibrium part
+// bounced back. F_int = 0 on wall rows, so F = F_g; its rho dependence makes the wall
+// density the solution of rho (1 + s g_y/2) = K (+ s <rho> g_y/2 for Eq. Gravity_2), with
+// s = +1 (bottom) / -1 (top) and K the sum of the known populations counted as the moment
+// condition requires. Works on deviations g_i = f_i - w_i rho_ref (the weights of the
+// formulas cancel pairwise); dmean = <rho> - rho_ref.
+template <typename V>
+__device__ __forceinline__ void zou_he(V (&g)[9], bool bottom, V dmean, const PhysT<V>& k) {
+  const V half = cst<V>(0.5), quarter = cst<V>(0.25), one = cst<V>(1.0);
+  const V s_half_gy = bottom ? half * k.gy : cst<V>(-0.5) * k.gy;  // s g_y / 2
+  const V Kg = bottom ? (g[0] + g[1] + g[3]) + cst<V>(2.0) * (g[4] + g[7] + g[8])
+                      : (g[0] + g[1] + g[3]) + cst<V>(2.0) * (g[2] + g[5] + g[6]);
+  // rho - rho_ref: form 1 (Kg - s gy/2 rho_ref)/(1 + s gy/2); form 2 (Kg + s gy/2 dmean)/(1 + s gy/2)
+  const V num = (k.form == 2) ? fmadd(s_half_gy, dmean, Kg) : Kg - s_half_gy * k.rho_ref;
+  const V dr = fast_div(num, one + s_half_gy);
+  const V base = (k.form == 2) ? (dr - dmean) : (k.rho_ref + dr);
+  const V Fx = base * k.gx, Fy = base * k.gy;
+  const V d13 = half * (g[1] - g[3]);
+  if (bottom) {
+    g[2] = g[4];
+    g[5] = g[7] - d13 - quarter * (Fx + Fy);
+    g[6] = g[8] + d13 + quarter * (Fx - Fy);
+  } else {
+    g[4] = g[2];
+    g[7] = g[5] + d13 + quarter * (Fx + Fy);
+    g[8] = g[6] - d13 + quarter * (Fy - Fx);
+  }
+}
+
 template <typename V>
 __device__ __forceinline__ V sum9(const V (&g)[9]) {
   return ((g[0] + (g[1] + g[3])) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]));

@@ -25,6 +25,7 @@ LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENONPHYS, LBM_ETIMEOUT, LBM_ENOMEM = 0, -1, -
 LBM_FP64, LBM_FP32 = 0, 1
 LBM_GRAVITY_RHO_G, LBM_GRAVITY_RHO_MINUS_MEAN_G = 1, 2
 LBM_HOST, LBM_DEVICE = 0, 1
+LBM_WALL_BOUNCE_BACK, LBM_WALL_ZOU_HE = 0, 1
 (LBM_REDUCE_MASS, LBM_REDUCE_MEAN_RHO, LBM_REDUCE_RESIDUAL, LBM_REDUCE_MAX_U,
  LBM_REDUCE_INTERFACE_Y, LBM_REDUCE_RHO_LV) = range(6)
 
@@ -63,6 +64,7 @@ class lbm_params(ctypes.Structure):
         ("gravity_form", ctypes.c_int32), ("thermal", ctypes.c_int32),
         ("rho_ref", ctypes.c_double), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
         ("c_v", ctypes.c_double), ("kappa", ctypes.c_double), ("T_bot", ctypes.c_double), ("T_top", ctypes.c_double),
+        ("wall", ctypes.c_int32), ("reserved1", ctypes.c_int32),
     ]
 
 

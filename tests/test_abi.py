@@ -57,6 +57,8 @@ def test_params_struct_layout_matches(lib):
         (dict(size=8), "params.size"),
         (dict(T=-1.0), "T > 0"),
         (dict(thermal=2), "thermal must be 0 or 1"),
+        (dict(wall=2), "wall must be"),
+        (dict(reserved1=1), "reserved1"),
         (dict(thermal=1), "T_bot > 0"),  # wall temperatures unset
         (dict(thermal=1, T_bot=0.02, T_top=0.02, c_v=0.0), "c_v > 0"),
         (dict(thermal=1, T_bot=0.02, T_top=0.02, kappa=-1.0), "kappa >= 0"),

@@ -241,7 +241,7 @@ def test_thermal_handle_keeps_a_thermal_tile(precision):
     p = thermal_params(16, 16, precision)
     h = lbm.lbm_init(p, column(16, 16))
     try:
-        with pytest.raises(lbm.LbmError, match="no thermal kernels"):
+        with pytest.raises(lbm.LbmError, match="no thermal or Zou-He kernels"):
             lbm.lbm_set_tiling(h, 1)
         assert lbm.lbm_autotune(h, 2)[0] == 0
         lbm.lbm_step(h, 2)
