@@ -125,7 +125,8 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
  * launch gives rho and u of the new populations (as the next step evaluates them) and two
  * launches advance T by Heun's second-order Runge-Kutta (dt = 1) on Eq. Energy_Equation,
  * with isotropic D2Q9-weighted central differences and the wall temperatures T_bot, T_top
- * (ghost rows T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top). */
+ * (ghost rows T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top; with Zou-He walls
+ * the wall rows 0 and ny-1 hold T_bot and T_top). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
 
 /* Macroscopic fields of the current state, as the next step evaluates them: the stored
@@ -151,7 +152,8 @@ int lbm_set_params(lbm_handle* h, const lbm_params* p);
 
 /* Thermal variant: the temperature field, nx*ny doubles [y][x] in host or device memory
  * per `where` (stored in the handle's precision). lbm_init sets the steady conduction
- * profile T(y) = T_bot + (T_top - T_bot)(y + 1/2)/ny (Eq. Temp_Profile with constant kappa).
+ * profile T(y) = T_bot + (T_top - T_bot)(y + 1/2)/ny (Eq. Temp_Profile with constant kappa;
+ * T_bot + (T_top - T_bot) y/(ny - 1) with Zou-He walls, whose wall rows keep T_bot, T_top).
  * The caller keeps T > 0. LBM_EINVAL on an isothermal handle. get synchronises when
  * where == LBM_HOST; set synchronises always. */
 int lbm_set_temperature(lbm_handle* h, const double* T, int where);

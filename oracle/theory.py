@@ -175,10 +175,11 @@ def solve(c: Column, dh=0.02, tol=1e-10, scan=64):
     return integrate(c, 0.5 * (lo + hi), dh)
 
 
-def at_nodes(sol: Solution, ny):
-    """rho and p at the node centres y = j + 1/2 of an ny-row lattice (H = ny), by linear
-    interpolation within each phase."""
-    yc = np.arange(ny) + 0.5
+def at_nodes(sol: Solution, ny, offset=0.5):
+    """rho and p at the nodes y = j + offset of an ny-row lattice, by linear interpolation
+    within each phase: offset 1/2 with halfway bounce-back walls (H = ny), 0 with wet-node
+    walls on the rows 0 and ny - 1 (H = ny - 1)."""
+    yc = np.arange(ny) + offset
     liq = yc < sol.h_i
     rho = np.where(liq, np.interp(yc, sol.y_l, sol.rho_l), np.interp(yc, sol.y_v, sol.rho_v))
     p = np.where(liq, np.interp(yc, sol.y_l, sol.p_l), np.interp(yc, sol.y_v, sol.p_v))

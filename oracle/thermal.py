@@ -21,7 +21,9 @@ printing them; each is listed in the design notes):
 * walls: T = T_bot on the wall below row 0 and T_top above row ny-1 (half a link
   beyond the last rows, as for the populations), by ghost rows
   T(-1) = 2 T_bot - T(0), T(ny) = 2 T_top - T(ny-1); velocity ghosts vanish at the
-  wall the same way (u(-1) = -u(0)); x is periodic.
+  wall the same way (u(-1) = -u(0)); x is periodic. With Zou-He wet-node walls the
+  walls are the rows 0 and ny-1 themselves: T is held at T_bot and T_top there and only
+  the rows between are advanced (the wall nodes' velocity is zero by construction).
 """
 from __future__ import annotations
 
@@ -83,14 +85,21 @@ def divergence(ux_p, uy_p):
 
 
 def rate(T, rho, ux, uy, p, th):
-    """Right-hand side of Eq. Energy_Equation on the lattice."""
-    Tp = with_ghosts(T, lambda r: 2.0 * th.T_bot - r, lambda r: 2.0 * th.T_top - r)
+    """Right-hand side of Eq. Energy_Equation on the lattice (zero on wet-node wall rows)."""
+    if p.wall == "zou-he":
+        Tp = with_ghosts(T, lambda r: r, lambda r: r)  # ghosts unused: the wall rows do not move
+    else:
+        Tp = with_ghosts(T, lambda r: 2.0 * th.T_bot - r, lambda r: 2.0 * th.T_top - r)
     uxp = with_ghosts(ux, lambda r: -r, lambda r: -r)
     uyp = with_ghosts(uy, lambda r: -r, lambda r: -r)
     gx, gy = gradient(Tp)
     lap = laplacian(Tp)
     div_u = divergence(uxp, uyp)
-    return -(ux * gx + uy * gy) + th.kappa / (rho * th.c_v) * lap - T * dp_dT(rho, p) / (rho * th.c_v) * div_u
+    out = -(ux * gx + uy * gy) + th.kappa / (rho * th.c_v) * lap - T * dp_dT(rho, p) / (rho * th.c_v) * div_u
+    if p.wall == "zou-he":
+        out[0] = 0.0
+        out[-1] = 0.0
+    return out
 
 
 def energy_step(T, rho, ux, uy, p, th):
@@ -109,8 +118,11 @@ def thermal_step(fstar, T, p, th):
     return f_new, energy_step(T, mac.rho, mac.u[0], mac.u[1], p, th)
 
 
-def linear_profile(ny, nx, T_bot, T_top):
+def linear_profile(ny, nx, T_bot, T_top, wall="bounce-back"):
     """Steady conduction profile between the walls (Eq. Temp_Profile with constant kappa):
-    linear in y with T = T_bot at y = -1/2 and T_top at y = ny - 1/2."""
+    linear in y with T = T_bot at y = -1/2 and T_top at y = ny - 1/2 (bounce-back), or at the
+    wall nodes y = 0 and ny - 1 (Zou-He)."""
     y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    if wall == "zou-he":
+        return T_bot + (T_top - T_bot) * y / (ny - 1)
     return T_bot + (T_top - T_bot) * (y + 0.5) / ny

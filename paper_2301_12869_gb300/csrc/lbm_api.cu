@@ -466,7 +466,8 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
   e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = lbm::launch_init(p->precision, rho_dev, h->f[0], p->nx, p->ny, rho_ref, h->stream);
   if (e == cudaSuccess && p->thermal)
-    e = lbm::launch_linear_T(p->precision, p->nx, p->ny, p->T_bot, p->T_top, h->Tf, h->stream);
+    e = lbm::launch_linear_T(p->precision, p->nx, p->ny, p->T_bot, p->T_top, p->wall == LBM_WALL_ZOU_HE ? 1 : 0, h->Tf,
+                             h->stream);
   if (e != cudaSuccess) { cuda_fail(h, e, "init kernel"); return fail(LBM_ECUDA); }
   h->cur = 0;
   h->pcur = 0;
@@ -499,8 +500,9 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
       // rho, u of the new populations with the force of T^n, then T^n -> T^(n+1)
       int rc = run_moments(h, h->rho_now, h->ux, h->uy);
       if (rc) return rc;
-      LBM_CUDA(h, lbm::launch_energy_step(p.precision, p.nx, p.ny, p.R, p.b, p.c_v, p.kappa, p.T_bot, p.T_top,
-                                          h->rho_now, h->ux, h->uy, h->Tf, h->Tnext, h->stream));
+      LBM_CUDA(h, lbm::launch_energy_step(p.precision, p.nx, p.ny, p.wall == LBM_WALL_ZOU_HE ? 1 : 0, p.R, p.b, p.c_v,
+                                          p.kappa, p.T_bot, p.T_top, h->rho_now, h->ux, h->uy, h->Tf, h->Tnext,
+                                          h->stream));
       std::swap(h->Tf, h->Tnext);
     }
   }

@@ -83,11 +83,13 @@ cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, dou
 // ---- thermal variant (lbm_thermal.cu): Eq. Energy_Equation on a real[ny][nx] field
 // One Heun step in one launch: Tout = Tin + (k1 + k2)/2 with k1 = L(Tin), k2 = L(Tin + k1),
 // rho, ux, uy ([y][x] doubles) held fixed. Tin and Tout are distinct real[ny][nx] fields.
-cudaError_t launch_energy_step(int precision, int nx, int ny, double R, double b, double c_v, double kappa,
-                               double T_bot, double T_top, const double* rho, const double* ux, const double* uy,
-                               const void* Tin, void* Tout, cudaStream_t stream);
-// Tf = T_bot + (T_top - T_bot)(y + 1/2)/ny
-cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, void* Tf, cudaStream_t stream);
+// wall_nodes: rows 0 and ny - 1 keep their temperature (Zou-He walls); else wall ghosts.
+cudaError_t launch_energy_step(int precision, int nx, int ny, int wall_nodes, double R, double b, double c_v,
+                               double kappa, double T_bot, double T_top, const double* rho, const double* ux,
+                               const double* uy, const void* Tin, void* Tout, cudaStream_t stream);
+// Tf = T_bot + (T_top - T_bot)(y + 1/2)/ny, or T_bot + (T_top - T_bot) y/(ny - 1) with wall nodes
+cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, int wall_nodes, void* Tf,
+                            cudaStream_t stream);
 
 // ---- host helpers of lbm_api.cu shared with other entry points (same behaviour as lbm_init's)
 int validate_params(const lbm_params* p, char* err);  // err: 512 bytes

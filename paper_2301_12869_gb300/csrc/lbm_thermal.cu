@@ -6,8 +6,9 @@
 // D2Q9-weighted central differences (d_a phi = 3 sum_i w_i c_ia phi(x + c_i),
 // lap phi = 6 sum_i w_i (phi(x + c_i) - phi(x))), Heun's second-order Runge-Kutta with
 // dt = 1, and Dirichlet walls half a link beyond the first and last rows (ghost rows
-// T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top). rho and u come from the
-// moments pass that follows each LBM step.
+// T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top) - or, with Zou-He wet-node
+// walls, T held at T_bot and T_top on the wall rows 0 and ny - 1 themselves. rho and u come
+// from the moments pass that follows each LBM step.
 //
 // One launch does the whole Heun step. A CTA owns a TX x TY tile of nodes and stages T, u
 // with a halo of two nodes and rho with a halo of one in shared memory: stage 1 (k1,
@@ -28,6 +29,7 @@ constexpr int W1 = TX + 2, H1 = TY + 2;  // rho, T*: one-node halo
 template <typename T>
 struct EnergyArgs {
   int nx, ny;
+  int wall_nodes;  // 1: rows 0 and ny - 1 are wall nodes at fixed temperature (Zou-He walls)
   T R, b4, c_v, kappa, twoTbot, twoTtop;
 };
 
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(TX * TY) heun_kernel(const EnergyArgs<T> a, co
       const int r = k / W1, c = k - r * W1, y = y0 - 1 + r;
       if (y >= 0 && y < ny) {
         const int c2 = (r + 1) * W2 + (c + 1);
-        sK[k] = rate(a, sT, c2, W2, sU, sV, c2, W2, sR[k]);
+        sK[k] = (a.wall_nodes && (y == 0 || y == ny - 1)) ? T(0) : rate(a, sT, c2, W2, sU, sV, c2, W2, sR[k]);
         sS[k] = sT[c2] + sK[k];
       }
     }
@@ -109,8 +111,8 @@ __global__ void __launch_bounds__(TX * TY) heun_kernel(const EnergyArgs<T> a, co
     // ghost rows of T* from its first and last rows
     for (int k = tid; k < H1 * W1; k += TX * TY) {
       const int r = k / W1, y = y0 - 1 + r;
-      if (y == -1) sS[k] = a.twoTbot - sS[k + W1];
-      if (y == ny) sS[k] = a.twoTtop - sS[k - W1];
+      if (y == -1 && !a.wall_nodes) sS[k] = a.twoTbot - sS[k + W1];
+      if (y == ny && !a.wall_nodes) sS[k] = a.twoTtop - sS[k - W1];
     }
     __syncthreads();
 
@@ -121,49 +123,56 @@ __global__ void __launch_bounds__(TX * TY) heun_kernel(const EnergyArgs<T> a, co
       const int c2 = (threadIdx.y + 2) * W2 + (threadIdx.x + 2);
       const T t = sT[c2];
       const T k1 = sK[c1];
-      const T k2 = rate(a, sS, c1, W1, sU, sV, c2, W2, sR[c1]);
-      Tout[size_t(y) * nx + x] = t + T(0.5) * (k1 + k2);
+      if (a.wall_nodes && (y == 0 || y == ny - 1)) {
+        Tout[size_t(y) * nx + x] = t;  // wall node: fixed temperature
+      } else {
+        const T k2 = rate(a, sS, c1, W1, sU, sV, c2, W2, sR[c1]);
+        Tout[size_t(y) * nx + x] = t + T(0.5) * (k1 + k2);
+      }
     }
     __syncthreads();  // the next tile of this CTA overwrites the shared arrays
   }
 }
 
 // the steady conduction profile (Eq. Temp_Profile): linear from T_bot at y = -1/2 to T_top
-// at y = ny - 1/2
+// at y = ny - 1/2 (bounce-back walls), or from row 0 to row ny - 1 (wall nodes)
 template <typename T>
-__global__ void linear_T_kernel(int nx, int ny, double T_bot, double T_top, T* Tf) {
+__global__ void linear_T_kernel(int nx, int ny, double T_bot, double T_top, int wall_nodes, T* Tf) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   for (int y = blockIdx.y; y < ny; y += gridDim.y)
-    if (x < nx) Tf[size_t(y) * nx + x] = T(T_bot + (T_top - T_bot) * (double(y) + 0.5) / ny);
+    if (x < nx)
+      Tf[size_t(y) * nx + x] = T(wall_nodes ? T_bot + (T_top - T_bot) * double(y) / double(ny - 1)
+                                            : T_bot + (T_top - T_bot) * (double(y) + 0.5) / ny);
 }
 
 unsigned rows_grid(int rows) { return unsigned(rows < 65535 ? rows : 65535); }
 
 }  // namespace
 
-cudaError_t launch_energy_step(int precision, int nx, int ny, double R, double b, double c_v, double kappa,
-                               double T_bot, double T_top, const double* rho, const double* ux, const double* uy,
-                               const void* Tin, void* Tout, cudaStream_t stream) {
+cudaError_t launch_energy_step(int precision, int nx, int ny, int wall_nodes, double R, double b, double c_v,
+                               double kappa, double T_bot, double T_top, const double* rho, const double* ux,
+                               const double* uy, const void* Tin, void* Tout, cudaStream_t stream) {
   const dim3 grid((nx + TX - 1) / TX, rows_grid((ny + TY - 1) / TY)), block(TX, TY);
   if (precision == 1) {
-    const EnergyArgs<float> a{nx, ny, float(R), float(b / 4.0), float(c_v), float(kappa), float(2.0 * T_bot),
-                              float(2.0 * T_top)};
+    const EnergyArgs<float> a{nx, ny, wall_nodes, float(R), float(b / 4.0), float(c_v), float(kappa),
+                              float(2.0 * T_bot), float(2.0 * T_top)};
     heun_kernel<float><<<grid, block, 0, stream>>>(a, rho, ux, uy, static_cast<const float*>(Tin),
                                                    static_cast<float*>(Tout));
   } else {
-    const EnergyArgs<double> a{nx, ny, R, b / 4.0, c_v, kappa, 2.0 * T_bot, 2.0 * T_top};
+    const EnergyArgs<double> a{nx, ny, wall_nodes, R, b / 4.0, c_v, kappa, 2.0 * T_bot, 2.0 * T_top};
     heun_kernel<double><<<grid, block, 0, stream>>>(a, rho, ux, uy, static_cast<const double*>(Tin),
                                                     static_cast<double*>(Tout));
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, void* Tf, cudaStream_t stream) {
+cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, int wall_nodes, void* Tf,
+                            cudaStream_t stream) {
   const dim3 grid((nx + 255) / 256, rows_grid(ny)), block(256);
   if (precision == 1)
-    linear_T_kernel<float><<<grid, block, 0, stream>>>(nx, ny, T_bot, T_top, static_cast<float*>(Tf));
+    linear_T_kernel<float><<<grid, block, 0, stream>>>(nx, ny, T_bot, T_top, wall_nodes, static_cast<float*>(Tf));
   else
-    linear_T_kernel<double><<<grid, block, 0, stream>>>(nx, ny, T_bot, T_top, static_cast<double*>(Tf));
+    linear_T_kernel<double><<<grid, block, 0, stream>>>(nx, ny, T_bot, T_top, wall_nodes, static_cast<double*>(Tf));
   return cudaGetLastError();
 }
 

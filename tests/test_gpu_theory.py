@@ -62,11 +62,9 @@ def steady(form, T, g, mean, h_i, rv, rl):
     return rho[:, 0]
 
 
-@pytest.fixture(scope="module")
-def coexistence_deviation():
-    """Relative deviation of the model's bulk densities from the Maxwell rule at g = 0,
-    T = 0.75 T_c (liquid, vapour)."""
-    T = 0.75 * T_C
+def deviation_at(T):
+    """Relative deviation of the model's bulk densities from the Maxwell rule at g = 0 and
+    temperature T (liquid, vapour): the method's known coexistence error there."""
     rv, rl, _ = eos.maxwell(T, A, B, R)
     mean = 1.3344 * RHO_C
     h_i = NY * (mean - rv) / (rl - rv)
@@ -75,8 +73,20 @@ def coexistence_deviation():
     bulk = (np.abs(y - h_i) >= 8) & (y >= 3) & (y <= NY - 3)
     d_l = np.max(np.abs(r[bulk & (y < h_i)] / rl - 1))
     d_v = np.max(np.abs(r[bulk & (y > h_i)] / rv - 1))
-    print(f"g = 0: liquid {d_l:.2e}, vapour {d_v:.2e} from Maxwell")
+    print(f"g = 0, T/T_c = {T / T_C:.2f}: liquid {d_l:.2e}, vapour {d_v:.2e} from Maxwell")
     return d_l, d_v
+
+
+@pytest.fixture(scope="module")
+def coexistence_deviation():
+    return deviation_at(0.75 * T_C)
+
+
+@pytest.fixture(scope="module")
+def cold_deviation():
+    """At the coldest wall temperature of the thermal example (0.65 T_c), where the vapour's
+    deviation is largest (it grows as T falls)."""
+    return deviation_at(0.65 * T_C)
 
 
 @pytest.mark.parametrize("form", [1, 2])
@@ -104,3 +114,58 @@ def test_steady_column_matches_theory(form, coexistence_deviation):
     assert e_v <= d_v + 0.01
     assert abs(y_lbm - sol.h_i) <= 1.0
     assert e_p <= (0.01 if form == 1 else 0.10)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_steady_thermal_column_matches_theory(form, coexistence_deviation, cold_deviation):
+    """The paper's first worked example with its own walls: Zou-He wet nodes on rows 0 and
+    100 (h = 100, 101 nodes, Sec. IV) holding T_bot = 0.85 T_c and T_top = 0.65 T_c, the
+    energy equation live (c_v = 5, kappa = 0.02). Run to a per-step change of 1e-11; bulk
+    densities against the theory within the model's coexistence deviation plus 1 % - for
+    the liquid the larger of its values at 0.75 T_c and 0.65 T_c, for the vapour its value
+    at the coldest wall (0.65 T_c), which bounds the vapour's over the column; with
+    Eq. Gravity_2 the vapour margin is the ~5 % offset the paper reports for that form - the
+    interface within one node, and T linear to 1e-6 relative (u = 0 at rest)."""
+    ny = 101
+    T_bot, T_top, g, mean = 0.85 * T_C, 0.65 * T_C, -2e-5, 1.3344 * RHO_C
+    c = theory.Column(H=float(ny - 1), T_bot=T_bot, T_top=T_top, mean_rho=mean, g_y=g, form=form, a=A, b=B, R=R)
+    sol = theory.solve(c, dh=0.05, tol=1e-9, scan=16)
+    rho_th, _ = theory.at_nodes(sol, ny, offset=0.0)
+    rho0 = inputs.column_rho0(NX, ny, sol.rho_l_i, sol.rho_v_i, int(round(sol.h_i)))
+    rho0 *= mean / rho0.mean()
+    p = lbm.make_params(NX, ny, 0.75 * T_C, "fp64", a=A, form=form, g=(0.0, g), thermal=1, T_bot=T_bot, T_top=T_top,
+                        wall=lbm.LBM_WALL_ZOU_HE)
+    h = lbm.lbm_init(p, rho0)
+    try:
+        res = np.inf
+        for _ in range(60):
+            lbm.lbm_step(h, 49999)
+            lbm.lbm_reduce(h, lbm.LBM_REDUCE_RESIDUAL)
+            lbm.lbm_step(h, 1)
+            res = lbm.lbm_reduce(h, lbm.LBM_REDUCE_RESIDUAL)[0]
+            if res < 1e-11:
+                break
+        rho = np.empty((ny, NX))
+        T = np.empty((ny, NX))
+        lbm.lbm_moments(h, rho)
+        lbm.lbm_get_temperature(h, T)
+    finally:
+        lbm.lbm_destroy(h)
+    r, y = rho[:, 0], np.arange(ny, dtype=float)
+    bulk = (np.abs(y - sol.h_i) >= 8) & (y >= 3) & (y <= ny - 4)
+    liq, vap = bulk & (y < sol.h_i), bulk & (y > sol.h_i)
+    e_l = np.max(np.abs(r[liq] / rho_th[liq] - 1))
+    e_v = np.max(np.abs(r[vap] / rho_th[vap] - 1))
+    mid = 0.5 * (sol.rho_v_i + sol.rho_l_i)
+    k = int(np.nonzero((r[:-1] - mid) * (r[1:] - mid) <= 0)[0][0])
+    y_lbm = y[k] + (r[k] - mid) / (r[k] - r[k + 1])
+    T_dev = np.max(np.abs(T[:, 0] / (T_bot + (T_top - T_bot) * y / (ny - 1)) - 1))
+    print(f"thermal form {form}: res {res:.1e}, liquid {e_l:.2e}, vapour {e_v:.2e}, interface {y_lbm:.3f} vs "
+          f"{sol.h_i:.3f}, T dev {T_dev:.1e}")
+    assert res < 1e-11
+    assert e_l <= max(coexistence_deviation[0], cold_deviation[0]) + 0.01
+    # Eq. Gravity_2: the paper reports a constant offset of about 5 % between LBM and theory
+    # (Sec. IV, pressure profile), which the nearly ideal vapour's density follows
+    assert e_v <= cold_deviation[1] + (0.01 if form == 1 else 0.05)
+    assert abs(y_lbm - sol.h_i) <= 1.0
+    assert T_dev <= 1e-6

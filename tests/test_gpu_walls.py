@@ -100,6 +100,12 @@ def test_thermal_zou_he_matches_oracle():
     op = oracle_params(p)
     th = oth.Thermal(c_v=p.c_v, kappa=p.kappa, T_bot=p.T_bot, T_top=p.T_top)
     rho0 = column(nx, ny)
+    # the wet-node walls hold T_bot and T_top; the initial field is linear between them
+    h0 = lbm.lbm_init(p, rho0)
+    T0 = np.empty((ny, nx))
+    lbm.lbm_get_temperature(h0, T0)
+    lbm.lbm_destroy(h0)
+    np.testing.assert_allclose(T0, oth.linear_profile(ny, nx, p.T_bot, p.T_top, wall="zou-he"), rtol=0, atol=1e-15)
     f = inputs.perturbed_populations(rho0, 1e-3)
     h = lbm.lbm_init(p, rho0)
     try:
@@ -113,6 +119,7 @@ def test_thermal_zou_he_matches_oracle():
             lbm.lbm_get_temperature(h, Tg)
             assert np.max(np.abs(state(h, p) - f)) <= 1e-14, n
             assert np.max(np.abs(Tg - T)) <= 1e-14, n
+            assert np.all(Tg[0] == p.T_bot) and np.all(Tg[-1] == p.T_top)
     finally:
         lbm.lbm_destroy(h)
 

@@ -75,3 +75,20 @@ def test_diffusing_mode_decays_at_the_discrete_rate():
     Tn = thermal.energy_step(T, rho, z, z, params(nx, ny), th)
     sel = np.abs(mode) > 0.5
     np.testing.assert_allclose((Tn[4, sel] - T0) / (amp * mode[sel]), 1 + zz + zz**2 / 2, rtol=1e-10)
+
+
+def test_zou_he_walls_hold_the_wall_temperatures():
+    """Wet-node walls: the wall rows keep T_bot, T_top, and the linear profile between the
+    wall nodes is steady at rest (every term of Eq. Energy_Equation vanishes)."""
+    from dataclasses import replace
+
+    p = replace(params(6, 14), wall="zou-he")
+    th = thermal.Thermal(T_bot=0.9 * T_C, T_top=0.8 * T_C)
+    T = thermal.linear_profile(14, 6, th.T_bot, th.T_top, wall="zou-he")
+    assert np.all(T[0] == th.T_bot) and np.all(T[-1] == th.T_top)
+    rho = np.full((14, 6), 0.2)
+    z = np.zeros((14, 6))
+    np.testing.assert_allclose(thermal.rate(T, rho, z, z, p, th), 0.0, atol=1e-18)
+    rng = np.random.default_rng(2)
+    T2 = thermal.energy_step(T, rho, 1e-3 * rng.random((14, 6)), 1e-3 * rng.random((14, 6)), p, th)
+    assert np.all(T2[0] == th.T_bot) and np.all(T2[-1] == th.T_top)
