@@ -567,6 +567,71 @@ def run_warmstart(args):
     return 0
 
 
+# ---------------------------------------------------------------- boiling example
+def run_boiling(args):
+    """The paper's phase-formation example (Sec. V): a 1-D column of 101 wet nodes (h = 100,
+    Zou-He walls), a = 0.5, <rho> = 1.3344 rho_c, rho g with g = 1.5e-5, T_med = 0.75 T_c,
+    c_v = 5, kappa = 0.02. For each Delta T/T_c: equilibrate with the top wall at
+    0.6213 T_c, lower it to T_med - Delta T/2 (lbm_set_params), and follow the rows next to
+    the hot bottom wall: a vapour layer has formed once the density two nodes above the
+    wall falls below the midpoint of the coexistence densities at its temperature."""
+    import numpy as np
+
+    from paper_2301_12869_gb300 import inputs, lbm
+
+    a, ny, nx = 0.5, 101, 4
+    rho_c, Tc, _ = lbm.lbm_critical_point(a, B, R)
+    mean, g = 1.3344 * rho_c, -1.5e-5
+    out = {"metric": "vapour layer formation at the hot wall (Sec. V example)", "impl": "gb300", "n_gpus": 1,
+           "config": {"workload": "1-D thermal column, 101 wet nodes, Zou-He walls", "a": a, "mean_rho_reduced": 1.3344,
+                      "g_y": g, "T_med_over_Tc": 0.75, "T_top_prerun_over_Tc": 0.6213, "c_v": 5.0, "kappa": 0.02,
+                      "post_steps": args.boiling_steps, "check_every": 10000},
+           "cases": []}
+    cases = [(float(d), "fp64") for d in args.boiling_dT.split(",")]
+    cases.append((cases[-1][0], "fp32"))
+    for dT, prec in cases:
+        T_bot, T_top = (0.75 + dT / 2) * Tc, (0.75 - dT / 2) * Tc
+        rv, rl, _ = lbm.lbm_coexistence(a, B, R, 0.75 * Tc)
+        rho0 = inputs.column_rho0(nx, ny, rl, rv, 54)
+        rho0 *= mean / rho0.mean()
+        p = lbm.make_params(nx, ny, 0.75 * Tc, prec, a=a, b=B, R=R, form=1, g=(0.0, g), thermal=1, T_bot=T_bot,
+                            T_top=0.6213 * Tc, wall=lbm.LBM_WALL_ZOU_HE)
+        h = lbm.lbm_init(p, rho0)
+        t0 = time.perf_counter()
+        pre, res = 0, math.inf
+        tol = 1e-10 if prec == "fp64" else 1e-7
+        while pre < args.boiling_prerun_cap and not res < tol:
+            lbm.lbm_step(h, 49999)
+            lbm.lbm_reduce(h, lbm.LBM_REDUCE_RESIDUAL)
+            lbm.lbm_step(h, 1)
+            res = lbm.lbm_reduce(h, lbm.LBM_REDUCE_RESIDUAL)[0]
+            pre += 50000
+        p.T_top = T_top
+        lbm.lbm_set_params(h, p)
+        rho = np.empty((ny, nx))
+        T = np.empty((ny, nx))
+        layer_step, samples = None, []
+        for k in range(args.boiling_steps // 10000):
+            lbm.lbm_step(h, 10000)
+            lbm.lbm_moments(h, rho)
+            lbm.lbm_get_temperature(h, T)
+            Ty = T[:, 0]
+            level = np.array([0.5 * sum(lbm.lbm_coexistence(a, B, R, min(t, 0.999 * Tc))[:2]) for t in Ty[:4]])
+            vapour_at_wall = rho[2, 0] < level[2]
+            if vapour_at_wall and layer_step is None:
+                layer_step = (k + 1) * 10000
+            if (k + 1) % 10 == 0 or (vapour_at_wall and len(samples) < 200):
+                samples.append({"step": (k + 1) * 10000, "rho_row2": float(rho[2, 0]), "level_row2": float(level[2]),
+                                "rho_max": float(rho[:, 0].max()), "argmax_y": int(np.argmax(rho[:, 0]))})
+        out["cases"].append({"dT_over_Tc": dT, "precision": prec, "T_bot_over_Tc": 0.75 + dT / 2,
+                             "T_top_over_Tc": 0.75 - dT / 2, "prerun_steps": pre, "prerun_residual": res,
+                             "vapour_layer_step": layer_step, "status": lbm.lbm_status(h),
+                             "seconds": time.perf_counter() - t0, "samples": samples[-12:]})
+        lbm.lbm_destroy(h)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- main
 def run_reference(args, world, rank):
     if rank != 0:
@@ -597,7 +662,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
-    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart"], default="domain",
+    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling"], default="domain",
                     help="domain: the 1024 x 4096 single-domain throughput line (default); "
                          "columns: time to steady state of batched columns; "
                          "thermal: the 512 x 2048 thermal column")
@@ -608,6 +673,9 @@ def main(argv=None):
     ap.add_argument("--column-heights", default="64,128")
     ap.add_argument("--column-max-steps", type=int, default=200000)
     ap.add_argument("--train-columns", type=int, default=16384)
+    ap.add_argument("--boiling-dT", default="0.3166,0.3381,0.3382")
+    ap.add_argument("--boiling-steps", type=int, default=1000000)
+    ap.add_argument("--boiling-prerun-cap", type=int, default=4000000)
     ap.add_argument("--mlp-iters", type=int, default=6000)
     ap.add_argument("--mlp-batch", type=int, default=8192)
     args = ap.parse_args(argv)
@@ -621,6 +689,8 @@ def main(argv=None):
         return run_columns(args) if rank == 0 else 0
     if args.workload == "warmstart":
         return run_warmstart(args) if rank == 0 else 0
+    if args.workload == "boiling":
+        return run_boiling(args) if rank == 0 else 0
 
     import numpy as np
     import torch

@@ -103,10 +103,15 @@ def rate(T, rho, ux, uy, p, th):
 
 
 def energy_step(T, rho, ux, uy, p, th):
-    """Heun's RK2 with dt = 1."""
+    """Heun's RK2 with dt = 1 (wet-node walls: the wall rows take T_bot and T_top, which may
+    have changed since the last step)."""
     k1 = rate(T, rho, ux, uy, p, th)
     k2 = rate(T + k1, rho, ux, uy, p, th)
-    return T + 0.5 * (k1 + k2)
+    out = T + 0.5 * (k1 + k2)
+    if p.wall == "zou-he":
+        out[0] = th.T_bot
+        out[-1] = th.T_top
+    return out
 
 
 def thermal_step(fstar, T, p, th):

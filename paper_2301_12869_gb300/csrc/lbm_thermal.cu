@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(TX * TY) heun_kernel(const EnergyArgs<T> a, co
       const T t = sT[c2];
       const T k1 = sK[c1];
       if (a.wall_nodes && (y == 0 || y == ny - 1)) {
-        Tout[size_t(y) * nx + x] = t;  // wall node: fixed temperature
+        Tout[size_t(y) * nx + x] = T(0.5) * (y == 0 ? a.twoTbot : a.twoTtop);  // wall node: T_bot / T_top
       } else {
         const T k2 = rate(a, sS, c1, W1, sU, sV, c2, W2, sR[c1]);
         Tout[size_t(y) * nx + x] = t + T(0.5) * (k1 + k2);

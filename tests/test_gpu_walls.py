@@ -158,3 +158,28 @@ def test_zou_he_handles_keep_variant_zero_and_batches_reject_it():
         lbm.lbm_destroy(h)
     with pytest.raises(lbm.LbmError, match="bounce-back"):
         lbm.lbm_batch_init(p, [dict(ny=12, T=0.85 * T_C, form=1)], np.full(16 * 12, 0.1))
+
+
+def test_changed_wall_temperature_reaches_the_wall_rows():
+    """lbm_set_params with a new T_top: the next step's wall row holds it (as the oracle's)."""
+    nx, ny = 8, 12
+    p = lbm.make_params(nx, ny, 0.85 * T_C, "fp64", a=A, wall=lbm.LBM_WALL_ZOU_HE, thermal=1, T_bot=0.9 * T_C,
+                        T_top=0.8 * T_C)
+    h = lbm.lbm_init(p, column(nx, ny))
+    try:
+        lbm.lbm_step(h, 3)
+        f = state(h, p)
+        T = np.empty((ny, nx))
+        lbm.lbm_get_temperature(h, T)
+        p.T_top = 0.75 * T_C
+        lbm.lbm_set_params(h, p)
+        lbm.lbm_step(h, 1)
+        Tg = np.empty((ny, nx))
+        lbm.lbm_get_temperature(h, Tg)
+        op = oracle_params(p)
+        th = oth.Thermal(c_v=p.c_v, kappa=p.kappa, T_bot=p.T_bot, T_top=p.T_top)
+        _, Tw = oth.thermal_step(f, T, op, th)
+        assert np.all(Tg[-1] == 0.75 * T_C)
+        assert np.max(np.abs(Tg - Tw)) <= 1e-14
+    finally:
+        lbm.lbm_destroy(h)
