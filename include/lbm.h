@@ -13,7 +13,13 @@
  * (Eq. Gravity_1) or (rho - <rho>) g (Eq. Gravity_2).
  *
  * Geometry: nx x ny nodes, x periodic, walls below row 0 and above row ny-1
- * (halfway bounce-back); the Shan-Chen force is zero on rows 0 and ny-1.
+ * (halfway bounce-back, the default) or on rows 0 and ny-1 (Zou-He wet nodes,
+ * LBM_WALL_ZOU_HE); the Shan-Chen force is zero on rows 0 and ny-1.
+ *
+ * Beyond the step: the thermal variant (temperature field and the energy equation,
+ * Eq. Energy_Equation), batched independent columns in one persistent launch
+ * (lbm_batch_*), and a learned warm start for the columns (lbm_mlp_*, no counterpart in
+ * the paper).
  *
  * Conventions for every function:
  *  - returns LBM_OK (0) or a negative LBM_E* code; lbm_last_error() gives text;
@@ -118,8 +124,8 @@ int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes);
 int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stream, lbm_handle** out);
 
 /* Advance nsteps >= 0 time steps (asynchronous on the handle's stream). Each step is
- * one launch of the fused kernel: stream, rho, psi, <rho>, F_int, F_g, u, MRT + Li
- * forcing, store. Device-side faults (non-physical state, timeouts) are recorded in a
+ * one launch of the fused kernel: stream (and, with Zou-He walls, rebuild the wall nodes'
+ * incoming populations), rho, psi, <rho>, F_int, F_g, u, MRT + Li forcing, store. Device-side faults (non-physical state, timeouts) are recorded in a
  * sticky status returned by the next synchronising call.
  * Thermal variant: psi uses R T(x) of the current temperature field; then a moments
  * launch gives rho and u of the new populations (as the next step evaluates them) and two

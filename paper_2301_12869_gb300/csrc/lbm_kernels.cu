@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
 // a warp's edges evaluate one extra psi value from the stage (which holds the whole band
 // plus halos). One producer warp refills a stage once every consumer warp has arrived on
 // that stage's `empty` mbarrier. Template: mode, all-unit relaxation, consumer warps,
-// stages, CTAs per SM the launch bounds aim for.
+// stages, CTAs per SM the launch bounds aim for, thermal (psi from R T(x)), Zou-He walls.
 template <int NWC, int S>
 __host__ __device__ constexpr size_t ws_smem() {
   constexpr int SW = 64 * NWC + 8;
