@@ -74,8 +74,16 @@ def workload_config(precision):
 
 
 def kernel_source_hash():
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """sha256[:16] of the kernel source with comments and blank space removed: a profile
+    stays valid across comment edits and goes stale with any change to the code."""
+    import re
+
+    with open(KERNEL_SRC) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = "\n".join(line.strip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def measured_peaks():
