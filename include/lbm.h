@@ -224,19 +224,27 @@ typedef struct lbm_batch lbm_batch;
  * mean rho0 in FP32, 0 in FP64). cols: ncols descriptors (host). rho0: the columns' initial
  * densities concatenated, column c holding nx * ny_c doubles [y][x], in host or device
  * memory per rho0_where; the state is the rest equilibrium f_i^eq(rho0, 0). Each column
- * needs 2 nx ny_c sizeof(real) <= 200 KiB. stream: a cudaStream_t or NULL (the batch then
+ * needs nx ny_c (sizeof(real) + 8) <= 200 KiB. stream: a cudaStream_t or NULL (the batch then
  * uses a private non-blocking stream). The library allocates the device memory.
  * Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const double* rho0, int rho0_where,
                    void* stream, lbm_batch** out);
 
 /* Advance every column until its residual max_x |rho_t(x) - rho_(t-1)(x)|, evaluated every
- * check_every (>= 2) steps, is <= tol, or until it has taken max_steps more steps. One
+ * check_every (>= 2) steps in FP64 from the stored populations, is <= tol, or until it has taken max_steps more steps. One
  * persistent launch over all columns (each CTA takes the tallest remaining column), issued
  * as a CUDA graph captured at the first run. Synchronises; seconds (may be NULL) receives
  * the device time of the launch. Per-column non-physical states are reported by
  * lbm_batch_results. */
 int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, double* seconds);
+
+/* As lbm_batch_run; a column also stops once stall_checks (> 0) consecutive checks have not
+ * lowered its smallest residual of this run by 1 % - its precision's rounding floor (FP32
+ * columns floor near 1e-8). stall_checks = 0 is lbm_batch_run. The usual way to finish:
+ * FP32 with tol = the final target and stall_checks ~10, then lbm_batch_convert to FP64 and
+ * lbm_batch_run to the target. */
+int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_every, int stall_checks,
+                        double* seconds);
 
 /* Per column (host arrays of ncols, any may be NULL): total steps taken, last residual
  * (+inf before the first check), status (LBM_OK or LBM_ENONPHYS). Returns LBM_ENONPHYS if

@@ -10,7 +10,9 @@
 // phases over all nodes of the column with one CTA barrier after each: (A) pull, rho and
 // psi; (B) pull, Shan-Chen stencil, collision, store, and a CTA-wide FP64 reduction of
 // the stored mass that gives the next step's <rho> (Eq. Gravity_2). Every `check_every`
-// steps the residual max |rho_t - rho_(t-1)| decides whether the column has converged.
+// steps the residual max |rho_t - rho_(t-1)| decides whether the column has converged; it
+// is evaluated in FP64 from the stored populations (an FP32 density rounds at 3e-8 and
+// would hide the FP32 state's changes below that).
 // The launch (counter reset + kernel) is captured once per batch into a CUDA graph; the
 // run parameters live in device memory so the graph is reused by every run.
 #include "lbm.h"
@@ -42,6 +44,7 @@ struct RunParams {
   double tol;
   long long max_steps;
   int check_every;
+  int stall_checks;  // > 0: a column also stops after this many checks without a 1 % gain
 };
 
 struct BatchArgs {
@@ -107,6 +110,15 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// sum of the stored (deviation) populations of a node in FP64, in a fixed order
+template <typename T>
+__device__ __forceinline__ double sum9_fp64(const T (&g)[9]) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s += double(g[i]);
+  return s;
+}
+
 template <typename T, int MODE, bool UNIT>
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -127,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
     const BatchCol col = a.cols[c];
     const int nx = a.nx, ny = col.ny, N = nx * ny;
     T* psi_s = reinterpret_cast<T*>(sm_raw);
-    T* rho_prev = psi_s + N;
+    double* rho_prev = reinterpret_cast<double*>(sm_raw + ((size_t(N) * sizeof(T) + 15) & ~size_t(15)));
     const lbm::PhysT<T> k = column_phys<T>(a, col);
     T* cur = static_cast<T*>(a.fA) + 9 * col.node_off;
     T* nxt = static_cast<T*>(a.fB) + 9 * col.node_off;
@@ -147,6 +159,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
 
     int flag = 0;
     double res = MODE == lbm::MODE_STEP ? a.resid[c] : 0.0;
+    double best = INFINITY;  // smallest residual of this run, for the stall test
+    int stalled = 0;
     long long it = 0;
     const long long iters = MODE == lbm::MODE_STEP ? run.max_steps : 1;
     for (; it < iters; ++it) {
@@ -163,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
         pull_col(cur, nx, ny, N, x, y, g);
         const T rho = k.rho_ref + lbm::sum9(g);
         psi_s[n] = lbm::psi_of<T>(rho, k, flag);
-        if (save) rho_prev[n] = rho;
+        if (save) rho_prev[n] = sum9_fp64(g);
       }
       __syncthreads();
       // (B) forces, velocity, collision, store (Eqs. ShanChenForce, Gravity_1/2, Momentum,
@@ -191,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) nxt[i * N + n] = o[i];
           acc.add9(o);
-          if (chk) rm = fmax(rm, fabs(double(rho) - double(rho_prev[n])));
+          if (chk) rm = fmax(rm, fabs(sum9_fp64(g) - rho_prev[n]));
         } else {
           const long long idx = col.node_off + n;
           if (a.rho_out) a.rho_out[idx] = double(rho);
@@ -215,6 +229,13 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
         for (int w2 = 0; w2 < kWarps; ++w2) r = fmax(r, rmax[w2]);
         res = r;
         if (!(r > run.tol)) {  // converged (uniform decision)
+          ++it;
+          break;
+        }
+        if (r < 0.99 * best) {
+          best = r;
+          stalled = 0;
+        } else if (run.stall_checks > 0 && ++stalled >= run.stall_checks) {  // at its rounding floor
           ++it;
           break;
         }
@@ -402,8 +423,8 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
     q.gy = in.gy;
     q.gravity_form = in.gravity_form;
     if ((rc = lbm::validate_params(&q, err))) return fail(rc, err);
-    if (2.0 * p->nx * in.ny * (p->precision == LBM_FP32 ? 4 : 8) > 200.0 * 1024)
-      return fail(LBM_EINVAL, "column too large for the batch kernel's shared memory (2 nx ny sizeof(real) <= 200 KiB)");
+    if (double(p->nx) * in.ny * ((p->precision == LBM_FP32 ? 4 : 8) + 8) + 16 > 200.0 * 1024)
+      return fail(LBM_EINVAL, "column too large for the batch kernel's shared memory (nx ny (sizeof(real) + 8) <= 200 KiB)");
     BatchCol& bc = b->cols[c];
     bc.ny = in.ny;
     bc.form = in.gravity_form;
@@ -488,7 +509,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  b->smem = size_t(2) * size_t(b->nx) * size_t(b->max_ny) * b->s;
+  b->smem = ((size_t(b->nx) * size_t(b->max_ny) * b->s + 15) & ~size_t(15)) + size_t(b->nx) * size_t(b->max_ny) * 8;
   for (int mode : {lbm::MODE_STEP, lbm::MODE_MOMENTS})
     for (bool u : {false, true}) {
       e = cudaFuncSetAttribute(pick_kernel(p->precision, mode, u), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -505,9 +526,15 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
 }
 
 int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, double* seconds) {
+  return lbm_batch_run_stall(b, tol, max_steps, check_every, 0, seconds);
+}
+
+int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_every, int stall_checks,
+                        double* seconds) {
   if (!b) return bfail(LBM_EINVAL, "batch is NULL");
-  if (max_steps < 0 || check_every < 2 || !(tol >= 0)) return bfail(LBM_EINVAL, "need max_steps >= 0, check_every >= 2, tol >= 0");
-  RunParams rp{tol, (long long)max_steps, check_every};
+  if (max_steps < 0 || check_every < 2 || !(tol >= 0) || stall_checks < 0)
+    return bfail(LBM_EINVAL, "need max_steps >= 0, check_every >= 2, tol >= 0, stall_checks >= 0");
+  RunParams rp{tol, (long long)max_steps, check_every, stall_checks};
   cudaError_t e = cudaMemcpyAsync(b->run_d, &rp, sizeof(rp), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess && !b->graph) {  // capture [counter reset -> persistent kernel] once
     cudaGraph_t g = nullptr;

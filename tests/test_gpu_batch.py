@@ -174,3 +174,19 @@ def test_batch_rejects_oversized_columns():
     p = batch_params("fp64")
     with pytest.raises(lbm.LbmError, match="shared memory"):
         lbm.lbm_batch_init(p, [dict(ny=4000, T=0.8 * T_C, form=1)], np.full(4 * 4000, 0.1))
+
+
+def test_fp32_columns_stop_at_their_rounding_floor():
+    """With a target below FP32 reach, lbm_batch_run_stall stops each FP32 column once ten
+    checks have not lowered its residual by 1 %: well before max_steps, at a floor of a few
+    1e-9 to a few 1e-8 (the FP64-evaluated change per step of the FP32 state)."""
+    cols, rhos = make_columns(8, seed=21, heights=(16, 24))
+    b = lbm.lbm_batch_init(batch_params("fp32"), cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_run_stall(b, 1e-13, 400000, 100, 10)
+        st, res, status = lbm.lbm_batch_results(b, len(cols))
+        assert np.all(status == 0)
+        assert np.all(st < 400000)
+        assert np.all((res > 1e-10) & (res < 1e-7))
+    finally:
+        lbm.lbm_batch_destroy(b)
