@@ -258,7 +258,9 @@ def run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot):
 
 
 # ---------------------------------------------------------------- batched columns
-FP32_STALL_CHECKS = 10  # an FP32 column hands over to FP64 after 10 checks (1000 steps) without a 1 % gain
+# FP32 phase of the FP32 -> FP64 runs: each column runs in FP32 to --fp32-tol, or until
+# --fp32-stall checks below the FP32 floor region bring no 1 % gain, then hands over to FP64
+FP32_TOL, FP32_STALL_CHECKS = 1e-8, 50
 
 
 def column_set(n, seed, heights, lbm, inputs):
@@ -278,13 +280,13 @@ def column_set(n, seed, heights, lbm, inputs):
 
 
 def run_to_steady(lbm, cols, rho0, cap, fp32_first):
-    """FP64 alone, or FP32 until each column reaches 1e-10 or its FP32 rounding floor (no 1 %
-    gain in FP32_STALL_CHECKS checks) then FP64 from that state, to residual 1e-10 (checked
-    every 100 steps). Returns (device seconds, steps, residual, status, batch handle)."""
+    """FP64 alone, or FP32 until each column reaches FP32_TOL or its FP32 rounding floor (no
+    1 % gain in FP32_STALL_CHECKS checks) then FP64 from that state, to residual 1e-10
+    (checked every 100 steps). Returns (device seconds, steps, residual, status, batch)."""
     _, Tc, _ = lbm.lbm_critical_point(A, B, R)
     if fp32_first:
         b32 = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols, rho0)
-        t32 = lbm.lbm_batch_run_stall(b32, 1e-10, cap, 100, FP32_STALL_CHECKS)
+        t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
         b = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
         lbm.lbm_batch_destroy(b32)
     else:
@@ -319,7 +321,7 @@ def run_columns(args):
     lbm.lbm_batch_destroy(b64)
     p32 = lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R)
     b32 = lbm.lbm_batch_init(p32, cols, rho)
-    t32 = lbm.lbm_batch_run_stall(b32, 1e-10, cap, 100, FP32_STALL_CHECKS)
+    t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
     st32, _, _ = lbm.lbm_batch_results(b32, len(cols), check=False)
     bc = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
     lbm.lbm_batch_destroy(b32)
@@ -686,12 +688,19 @@ def main(argv=None):
     ap.add_argument("--column-heights", default="64,128")
     ap.add_argument("--column-max-steps", type=int, default=200000)
     ap.add_argument("--train-columns", type=int, default=16384)
+    ap.add_argument("--fp32-tol", type=float, default=None, help="FP32 target before the FP64 phase (default 1e-8)")
+    ap.add_argument("--fp32-stall", type=int, default=None, help="stall checks of the FP32 phase (default 50)")
     ap.add_argument("--boiling-dT", default="0.3166,0.3381,0.3382")
     ap.add_argument("--boiling-steps", type=int, default=1000000)
     ap.add_argument("--boiling-prerun-cap", type=int, default=4000000)
     ap.add_argument("--mlp-iters", type=int, default=6000)
     ap.add_argument("--mlp-batch", type=int, default=8192)
     args = ap.parse_args(argv)
+    global FP32_TOL, FP32_STALL_CHECKS
+    if args.fp32_tol is not None:
+        FP32_TOL = args.fp32_tol
+    if args.fp32_stall is not None:
+        FP32_STALL_CHECKS = args.fp32_stall
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_env()

@@ -238,9 +238,10 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
  * lbm_batch_results. */
 int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, double* seconds);
 
-/* As lbm_batch_run; a column also stops once stall_checks (> 0) consecutive checks have not
- * lowered its smallest residual of this run by 1 % - its precision's rounding floor (FP32
- * columns floor near 1e-8). stall_checks = 0 is lbm_batch_run. The usual way to finish:
+/* As lbm_batch_run; a column also stops once stall_checks (> 0) consecutive checks with a
+ * residual below 1e-6 (FP32) / 1e-13 (FP64) have not lowered its smallest residual of this
+ * run by 1 % - its precision's rounding floor (FP32 columns floor near 1e-8; above those
+ * levels transients may plateau and do not count). stall_checks = 0 is lbm_batch_run. The usual way to finish:
  * FP32 with tol = the final target and stall_checks ~10, then lbm_batch_convert to FP64 and
  * lbm_batch_run to the target. */
 int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_every, int stall_checks,

@@ -110,6 +110,10 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// stalls count only below this residual: about 30 ulp of an FP32 / FP64 density of 0.3
+template <typename T>
+constexpr double kStallBelow = sizeof(T) == 4 ? 1e-6 : 1e-13;
+
 // sum of the stored (deviation) populations of a node in FP64, in a fixed order
 template <typename T>
 __device__ __forceinline__ double sum9_fp64(const T (&g)[9]) {
@@ -235,7 +239,8 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
         if (r < 0.99 * best) {
           best = r;
           stalled = 0;
-        } else if (run.stall_checks > 0 && ++stalled >= run.stall_checks) {  // at its rounding floor
+        } else if (run.stall_checks > 0 && r < kStallBelow<T> && ++stalled >= run.stall_checks) {
+          // no gain near the precision's rounding floor (transients above it may plateau)
           ++it;
           break;
         }
