@@ -261,6 +261,9 @@ def run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot):
 # FP32 phase of the FP32 -> FP64 runs: each column runs in FP32 to --fp32-tol, or until
 # --fp32-stall checks below the FP32 floor region bring no 1 % gain, then hands over to FP64
 FP32_TOL, FP32_STALL_CHECKS = 1e-8, 50
+# extrapolation (lbm_batch_set_acceleration) of the FP32 -> FP64 runs: every ACCEL_CHECKS
+# residual checks; the plain FP64 reference runs without it
+ACCEL_CHECKS = 5
 
 
 def column_set(n, seed, heights, lbm, inputs):
@@ -286,9 +289,11 @@ def run_to_steady(lbm, cols, rho0, cap, fp32_first):
     _, Tc, _ = lbm.lbm_critical_point(A, B, R)
     if fp32_first:
         b32 = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols, rho0)
+        lbm.lbm_batch_set_acceleration(b32, ACCEL_CHECKS)
         t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
         b = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
         lbm.lbm_batch_destroy(b32)
+        lbm.lbm_batch_set_acceleration(b, ACCEL_CHECKS)
     else:
         t32 = 0.0
         b = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp64", a=A, b=B, R=R), cols, rho0)
@@ -321,10 +326,12 @@ def run_columns(args):
     lbm.lbm_batch_destroy(b64)
     p32 = lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R)
     b32 = lbm.lbm_batch_init(p32, cols, rho)
+    lbm.lbm_batch_set_acceleration(b32, ACCEL_CHECKS)
     t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
     st32, _, _ = lbm.lbm_batch_results(b32, len(cols), check=False)
     bc = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
     lbm.lbm_batch_destroy(b32)
+    lbm.lbm_batch_set_acceleration(bc, ACCEL_CHECKS)
     tpol = lbm.lbm_batch_run(bc, 1e-10, cap, 100)
     stc, resc, sc = lbm.lbm_batch_results(bc, len(cols), check=False)
     lbm.lbm_batch_destroy(bc)
@@ -335,7 +342,8 @@ def run_columns(args):
         "metric": "time to steady state (residual 1e-10), batched columns", "unit": "s",
         "value": t32 + tpol, "higher_is_better": False, "impl": "gb300", "n_gpus": 1,
         "config": {"workload": f"{len(cols)} seeded 4xH liquid columns, H in {heights}", "nodes": nodes,
-                   "max_steps": cap, "check_every": 100},
+                   "max_steps": cap, "check_every": 100, "fp32_tol": FP32_TOL, "fp32_stall_checks": FP32_STALL_CHECKS,
+                   "accel_checks": ACCEL_CHECKS},
         "fp64_plain": {"seconds": t64, "converged": int(ok64.sum()), "nonphysical": int((s64 != 0).sum()),
                        "node_steps_per_s": float(np.sum(st64 * [4 * c["ny"] for c in cols]) / t64)},
         "fp32_then_fp64": {"seconds": t32 + tpol, "fp32_seconds": t32, "fp64_seconds": tpol,
@@ -690,13 +698,17 @@ def main(argv=None):
     ap.add_argument("--train-columns", type=int, default=16384)
     ap.add_argument("--fp32-tol", type=float, default=None, help="FP32 target before the FP64 phase (default 1e-8)")
     ap.add_argument("--fp32-stall", type=int, default=None, help="stall checks of the FP32 phase (default 50)")
+    ap.add_argument("--accel-checks", type=int, default=None, help="extrapolation cycle of the FP32 -> FP64 runs "
+                                                                    "in residual checks (default 5; 0: off)")
     ap.add_argument("--boiling-dT", default="0.3166,0.3381,0.3382")
     ap.add_argument("--boiling-steps", type=int, default=1000000)
     ap.add_argument("--boiling-prerun-cap", type=int, default=4000000)
     ap.add_argument("--mlp-iters", type=int, default=6000)
     ap.add_argument("--mlp-batch", type=int, default=8192)
     args = ap.parse_args(argv)
-    global FP32_TOL, FP32_STALL_CHECKS
+    global FP32_TOL, FP32_STALL_CHECKS, ACCEL_CHECKS
+    if args.accel_checks is not None:
+        ACCEL_CHECKS = args.accel_checks
     if args.fp32_tol is not None:
         FP32_TOL = args.fp32_tol
     if args.fp32_stall is not None:

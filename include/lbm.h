@@ -247,6 +247,17 @@ int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, 
 int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_every, int stall_checks,
                         double* seconds);
 
+/* Accelerate later runs of this batch by extrapolation (no counterpart in the paper: it
+ * changes the way to each column's steady state, not the state). Every `checks` (>= 2)
+ * residual checks a column's state is kept; after 6 such snapshots x_0..x_5 the fixed
+ * point is estimated by minimal polynomial extrapolation of order 4 - the coefficients c
+ * (c_4 = 1) minimising |sum_j c_j (x_{j+1} - x_j)| weight sum_j c_j x_j / sum_j c_j - which
+ * captures the damped oscillations in which the columns' slow modes decay. The estimate
+ * replaces the state when every density stays positive, and is undone when the next
+ * residual check is worse than the one before it. checks = 0 turns it off. The library
+ * allocates 6 x 9 x (total nodes) reals once. Not carried over by lbm_batch_convert. */
+int lbm_batch_set_acceleration(lbm_batch* b, int checks);
+
 /* Per column (host arrays of ncols, any may be NULL): total steps taken, last residual
  * (+inf before the first check), status (LBM_OK or LBM_ENONPHYS). Returns LBM_ENONPHYS if
  * any column is non-physical. Synchronises. */

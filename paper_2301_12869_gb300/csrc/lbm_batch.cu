@@ -40,11 +40,16 @@ struct BatchCol {
   double RT, gx, gy, rho_ref;
 };
 
+constexpr int kMpeK = 4;  // extrapolation order: kMpeK + 2 snapshots per cycle
+
 struct RunParams {
   double tol;
   long long max_steps;
   int check_every;
   int stall_checks;  // > 0: a column also stops after this many checks without a 1 % gain
+  int mpe_checks;    // > 0: a state snapshot every mpe_checks residual checks, extrapolation per cycle
+  void* snap;        // kMpeK + 2 slots of 9 * total_nodes reals (NULL: no extrapolation)
+  long long slot;    // elements per slot (9 * total_nodes)
 };
 
 struct BatchArgs {
@@ -123,7 +128,130 @@ __device__ __forceinline__ double sum9_fp64(const T (&g)[9]) {
   return s;
 }
 
-template <typename T, int MODE, bool UNIT>
+// Minimal polynomial extrapolation of a column's fixed-point iteration (no counterpart in the
+// paper; it changes the way to the steady state, not the state). The slow modes of a column
+// decay as damped oscillations, so a single-ratio (Aitken) step does not apply; from
+// kMpeK + 2 snapshots x_0..x_{kMpeK+1} taken every few hundred steps, with differences
+// u_j = x_{j+1} - x_j, the coefficients c (c_kMpeK = 1) minimising |sum_j c_j u_j| give the
+// estimate s = sum_j c_j x_j / sum_j c_j of the fixed point (j = 0..kMpeK). The Gram matrix
+// is reduced over the CTA in FP64 and solved by one thread (Gaussian elimination with
+// partial pivoting). The estimate replaces `cur` only if every node keeps a positive
+// density; returns whether it did. Uniform over the CTA.
+template <typename T>
+__device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* slot0, int tid, int lane, int warp,
+                                const lbm::PhysT<T>& k) {
+  constexpr int NU = kMpeK + 1, NG = NU * (NU + 1) / 2;
+  __shared__ double part[NG][kWarps];
+  __shared__ double gam[NU];
+  __shared__ int ok_s;
+  const size_t slot = size_t(run.slot);
+  double G[NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) G[i] = 0.0;
+  for (int e = tid; e < 9 * N; e += kThreads) {
+    double x[NU + 1], u[NU];
+#pragma unroll
+    for (int j = 0; j <= NU; ++j) x[j] = double(slot0[j * slot + e]);
+#pragma unroll
+    for (int j = 0; j < NU; ++j) u[j] = x[j + 1] - x[j];
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < NU; ++i)
+#pragma unroll
+      for (int j = i; j < NU; ++j) G[m++] += u[i] * u[j];
+  }
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+    const double v = lbm::warp_sum(G[i]);
+    if (lane == 0) part[i][warp] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double g[NG];
+    for (int i = 0; i < NG; ++i) {
+      g[i] = 0.0;
+      for (int w = 0; w < kWarps; ++w) g[i] += part[i][w];
+    }
+    auto at = [&](int i, int j) {
+      if (i > j) {
+        const int t = i;
+        i = j;
+        j = t;
+      }
+      return g[i * NU - i * (i - 1) / 2 + (j - i)];
+    };
+    // sum_{j<K} G_ij c_j = -G_iK for i < K (K = kMpeK), c_K = 1
+    double Am[kMpeK][kMpeK + 1];
+    for (int i = 0; i < kMpeK; ++i) {
+      for (int j = 0; j < kMpeK; ++j) Am[i][j] = at(i, j);
+      Am[i][kMpeK] = -at(i, kMpeK);
+    }
+    bool ok = at(kMpeK, kMpeK) > 0.0;
+    const double scale = at(0, 0) + at(kMpeK, kMpeK);
+    for (int ci = 0; ci < kMpeK && ok; ++ci) {
+      int piv = ci;
+      for (int i = ci + 1; i < kMpeK; ++i)
+        if (fabs(Am[i][ci]) > fabs(Am[piv][ci])) piv = i;
+      if (!(fabs(Am[piv][ci]) > 1e-14 * scale)) {
+        ok = false;
+        break;
+      }
+      if (piv != ci)
+        for (int j = 0; j <= kMpeK; ++j) {
+          const double t = Am[ci][j];
+          Am[ci][j] = Am[piv][j];
+          Am[piv][j] = t;
+        }
+      for (int i = ci + 1; i < kMpeK; ++i) {
+        const double f = Am[i][ci] / Am[ci][ci];
+        for (int j = ci; j <= kMpeK; ++j) Am[i][j] -= f * Am[ci][j];
+      }
+    }
+    double cvec[NU];
+    cvec[kMpeK] = 1.0;
+    for (int i = kMpeK - 1; i >= 0 && ok; --i) {
+      double sum = Am[i][kMpeK];
+      for (int j = i + 1; j < kMpeK; ++j) sum -= Am[i][j] * cvec[j];
+      cvec[i] = sum / Am[i][i];
+    }
+    double S = 0.0, Sabs = 0.0;
+    for (int j = 0; j < NU && ok; ++j) {
+      S += cvec[j];
+      Sabs += fabs(cvec[j]);
+    }
+    ok = ok && isfinite(S) && fabs(S) > 1e-8 * Sabs;
+    for (int j = 0; j < NU; ++j) gam[j] = ok ? cvec[j] / S : 0.0;
+    ok_s = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (!ok_s) return false;
+  // the estimate, node by node; a non-positive density rejects it
+  int bad = 0;
+  for (int n = tid; n < N; n += kThreads) {
+    double rho = k.rho_ref;
+    T v[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < NU; ++j) acc += gam[j] * double(slot0[j * slot + size_t(i) * N + n]);
+      v[i] = T(acc);
+      rho += acc;
+    }
+    if (!(rho > 0.0)) bad = 1;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) cur[i * N + n] = v[i];
+  }
+  if (__syncthreads_or(bad)) {  // back to the last snapshot (x_{kMpeK+1} is the state before)
+    const T* last = slot0 + size_t(kMpeK + 1) * slot;
+    for (int e = tid; e < 9 * N; e += kThreads) cur[e] = last[e];
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+template <typename T, int MODE, bool UNIT, bool ACC>
 __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double red[2][kWarps];  // mass partials of the state each iteration reads
@@ -165,6 +293,25 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
     double res = MODE == lbm::MODE_STEP ? a.resid[c] : 0.0;
     double best = INFINITY;  // smallest residual of this run, for the stall test
     int stalled = 0;
+    // extrapolation state (uniform over the CTA)
+    const bool mpe = ACC && MODE == lbm::MODE_STEP && run.mpe_checks > 0 && run.snap != nullptr;
+    int nsnap = 0, checks_since = 0;
+    bool verify = false, skip_cycle = false;
+    double res_before = 0.0;
+    auto slot_ptr = [&](int j) { return static_cast<T*>(run.snap) + size_t(j) * size_t(run.slot) + 9 * col.node_off; };
+    // FP64 partials of the stored mass of a state into red[q] (what the next step reads)
+    auto remass = [&](const T* st, int q) {
+      lbm::Acc<T> acc2;
+      for (int n = tid; n < N; n += kThreads) {
+        T g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = st[i * N + n];
+        acc2.add9(g);
+      }
+      const double v = lbm::warp_sum(acc2.value());
+      if (lane == 0) red[q][warp] = v;
+      __syncthreads();
+    };
     long long it = 0;
     const long long iters = MODE == lbm::MODE_STEP ? run.max_steps : 1;
     for (; it < iters; ++it) {
@@ -243,6 +390,39 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
           // no gain near the precision's rounding floor (transients above it may plateau)
           ++it;
           break;
+        }
+        if (ACC && mpe) {
+          const int q = (it + 1) & 1;  // partials the next iteration reads
+          if (verify) {
+            // the first check after an extrapolation: a larger change than before it means
+            // the estimate is worse - go back to the last snapshot
+            verify = false;
+            if (r > res_before) {
+              const T* last = slot_ptr(kMpeK + 1);
+              for (int e = tid; e < 9 * N; e += kThreads) cur[e] = last[e];
+              __syncthreads();
+              remass(cur, q);
+              skip_cycle = true;
+              nsnap = 0;
+              checks_since = 0;
+            }
+          }
+          if (++checks_since >= run.mpe_checks) {
+            checks_since = 0;
+            T* dst = slot_ptr(nsnap);
+            for (int e = tid; e < 9 * N; e += kThreads) dst[e] = cur[e];
+            __syncthreads();
+            if (++nsnap == kMpeK + 2) {
+              nsnap = 0;
+              if (skip_cycle) {
+                skip_cycle = false;
+              } else if (mpe_extrapolate<T>(run, N, cur, slot_ptr(0), tid, lane, warp, k)) {
+                remass(cur, q);
+                verify = true;
+                res_before = r;
+              }
+            }
+          }
         }
       }
     }
@@ -324,22 +504,29 @@ struct lbm_batch {
   int grid = 0;
   size_t smem = 0;
   cudaGraphExec_t graph = nullptr;
+  bool graph_acc = false;  // the captured launch is the extrapolating kernel
+  int grid_acc = 0;        // its resident grid
+  int mpe_checks = 0;      // extrapolation cycle (residual checks per snapshot); 0: off
+  void* snap = nullptr;    // kMpeK + 2 snapshot slots of 9 * total_nodes reals
 };
 
 namespace {
 
-template <typename T, int MODE, bool UNIT>
+template <typename T, int MODE, bool UNIT, bool ACC>
 void* batch_fn() {
-  return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT>);
+  return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT, ACC>);
 }
 
-void* pick_kernel(int precision, int mode, bool unit) {
-  if (precision == LBM_FP32) {
-    if (mode == lbm::MODE_MOMENTS) return batch_fn<float, lbm::MODE_MOMENTS, false>();
-    return unit ? batch_fn<float, lbm::MODE_STEP, true>() : batch_fn<float, lbm::MODE_STEP, false>();
-  }
-  if (mode == lbm::MODE_MOMENTS) return batch_fn<double, lbm::MODE_MOMENTS, false>();
-  return unit ? batch_fn<double, lbm::MODE_STEP, true>() : batch_fn<double, lbm::MODE_STEP, false>();
+template <typename T>
+void* pick_typed(int mode, bool unit, bool acc) {
+  if (mode == lbm::MODE_MOMENTS) return batch_fn<T, lbm::MODE_MOMENTS, false, false>();
+  if (acc) return unit ? batch_fn<T, lbm::MODE_STEP, true, true>() : batch_fn<T, lbm::MODE_STEP, false, true>();
+  return unit ? batch_fn<T, lbm::MODE_STEP, true, false>() : batch_fn<T, lbm::MODE_STEP, false, false>();
+}
+
+// the extrapolating kernel only when the batch is set to extrapolate (it holds more registers)
+void* pick_kernel(int precision, int mode, bool unit, bool acc = false) {
+  return precision == LBM_FP32 ? pick_typed<float>(mode, unit, acc) : pick_typed<double>(mode, unit, acc);
 }
 
 BatchArgs make_args(const lbm_batch* b) {
@@ -372,17 +559,20 @@ bool unit_tau(const lbm_params& p) {
   return p.tau_e == 1.0 && p.tau_varsigma == 1.0 && p.tau_j == 1.0 && p.tau_q == 1.0 && p.tau_nu == 1.0;
 }
 
+bool accelerated(const lbm_batch* b) { return b->snap != nullptr && b->mpe_checks > 0; }
+
 cudaError_t launch(const lbm_batch* b, int mode, BatchArgs args) {
-  void* fn = pick_kernel(b->p.precision, mode, unit_tau(b->p));
+  const bool acc = mode == lbm::MODE_STEP && accelerated(b);
+  void* fn = pick_kernel(b->p.precision, mode, unit_tau(b->p), acc);
   void* kargs[] = {&args};
-  return cudaLaunchKernel(fn, dim3(b->grid), dim3(kThreads), kargs, b->smem, b->stream);
+  return cudaLaunchKernel(fn, dim3(acc ? b->grid_acc : b->grid), dim3(kThreads), kargs, b->smem, b->stream);
 }
 
 void free_batch(lbm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (void* ptr : {(void*)b->cols_d, (void*)b->order_d, b->fA, b->fB, (void*)b->counter, (void*)b->run_d,
-                    (void*)b->steps_d, (void*)b->resid_d, (void*)b->status_d})
+                    (void*)b->steps_d, (void*)b->resid_d, (void*)b->status_d, b->snap})
     if (ptr) cudaFree(ptr);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -516,17 +706,35 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   b->smem = ((size_t(b->nx) * size_t(b->max_ny) * b->s + 15) & ~size_t(15)) + size_t(b->nx) * size_t(b->max_ny) * 8;
   for (int mode : {lbm::MODE_STEP, lbm::MODE_MOMENTS})
-    for (bool u : {false, true}) {
-      e = cudaFuncSetAttribute(pick_kernel(p->precision, mode, u), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(b->smem));
-      if (e != cudaSuccess) return fail(LBM_ECUDA, "batch kernel shared memory limit");
-    }
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(p->precision, lbm::MODE_STEP, unit_tau(*p)),
-                                                kThreads, b->smem);
+    for (bool u : {false, true})
+      for (bool acc : {false, true}) {
+        e = cudaFuncSetAttribute(pick_kernel(p->precision, mode, u, acc), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(b->smem));
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "batch kernel shared memory limit");
+      }
   const double avg_bytes = 2.0 * 9.0 * double(b->s) * double(off) / double(ncols);
   const int l2_cap = std::max(nsm, int(96.0e6 / avg_bytes));
-  b->grid = std::max(1, std::min({nsm * std::max(per_sm, 1), l2_cap, ncols}));
+  for (bool acc : {false, true}) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(p->precision, lbm::MODE_STEP, unit_tau(*p), acc),
+                                                  kThreads, b->smem);
+    (acc ? b->grid_acc : b->grid) = std::max(1, std::min({nsm * std::max(per_sm, 1), l2_cap, ncols}));
+  }
   *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_set_acceleration(lbm_batch* b, int checks) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  if (checks < 0 || checks == 1) return bfail(LBM_EINVAL, "checks must be 0 (off) or >= 2");
+  if (checks > 0 && !b->snap) {
+    const size_t bytes = size_t(kMpeK + 2) * 9 * size_t(b->total_nodes) * b->s;
+    cudaError_t e = cudaMalloc(&b->snap, bytes);
+    if (e != cudaSuccess) {
+      b->snap = nullptr;
+      return bfail(LBM_ENOMEM, "cudaMalloc of the extrapolation snapshots failed");
+    }
+  }
+  b->mpe_checks = checks;
   return LBM_OK;
 }
 
@@ -539,8 +747,13 @@ int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_e
   if (!b) return bfail(LBM_EINVAL, "batch is NULL");
   if (max_steps < 0 || check_every < 2 || !(tol >= 0) || stall_checks < 0)
     return bfail(LBM_EINVAL, "need max_steps >= 0, check_every >= 2, tol >= 0, stall_checks >= 0");
-  RunParams rp{tol, (long long)max_steps, check_every, stall_checks};
+  RunParams rp{tol, (long long)max_steps, check_every, stall_checks, b->snap ? b->mpe_checks : 0, b->snap,
+               9 * b->total_nodes};
   cudaError_t e = cudaMemcpyAsync(b->run_d, &rp, sizeof(rp), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && b->graph && b->graph_acc != accelerated(b)) {  // the kernel choice changed
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
   if (e == cudaSuccess && !b->graph) {  // capture [counter reset -> persistent kernel] once
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
@@ -551,6 +764,7 @@ int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_e
       if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e == cudaSuccess) b->graph_acc = accelerated(b);
     if (g) cudaGraphDestroy(g);
   }
   cudaEvent_t t0 = nullptr, t1 = nullptr;

@@ -40,7 +40,7 @@ EXPORTS = (
     "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
     "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
-    "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
+    "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
     "lbm_batch_convert", "lbm_batch_destroy",
     "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
     "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_destroy",
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
         "lbm_batch_init": (i32, [P(lbm_params), P(lbm_column), i32, vp, i32, vp, P(vp)]),
         "lbm_batch_run": (i32, [vp, d, i64, i32, P(d)]),
         "lbm_batch_run_stall": (i32, [vp, d, i64, i32, i32, P(d)]),
+        "lbm_batch_set_acceleration": (i32, [vp, i32]),
         "lbm_batch_results": (i32, [vp, vp, vp, vp]),
         "lbm_batch_moments": (i32, [vp, vp, vp, vp, i32]),
         "lbm_batch_get_state": (i32, [vp, vp, i32]),
@@ -318,6 +319,11 @@ def lbm_batch_run_stall(b, tol, max_steps, check_every=100, stall_checks=10):
     _check(load().lbm_batch_run_stall(b, float(tol), int(max_steps), int(check_every), int(stall_checks),
                                       ctypes.byref(sec)))
     return sec.value
+
+
+def lbm_batch_set_acceleration(b, checks):
+    """Extrapolation every `checks` residual checks (0: off) for later runs of this batch."""
+    _check(load().lbm_batch_set_acceleration(b, int(checks)))
 
 
 def lbm_batch_results(b, ncols, check=True):
