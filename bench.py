@@ -590,6 +590,38 @@ def run_warmstart(args):
     return 0
 
 
+# ---------------------------------------------------------------- tensor-core GEMM of the network
+def run_gemm(args):
+    """Throughput of the warm-start network's tcgen05 GEMM (lbm_mlp_gemm, C = A B^T, bfloat16 in,
+    FP32 out) on the network's own shape (a batch of rows through a 128 x 128 layer) and on a
+    large square product, timed with CUDA events around K calls (each call synchronises)."""
+    import torch
+
+    from paper_2301_12869_gb300 import lbm
+
+    peaks, peak_kind = measured_peaks()
+    rows = []
+    for M, N, K in ((int(args.gemm_m), 128, 128), (8192, 8192, 8192)):
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16).view(torch.int16)
+        Bm = torch.randn(N, K, device="cuda").to(torch.bfloat16).view(torch.int16)
+        C = torch.empty(M, N, device="cuda", dtype=torch.float32)
+        for _ in range(args.warmup):
+            lbm.lbm_mlp_gemm(A, Bm, C)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            lbm.lbm_mlp_gemm(A, Bm, C)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / args.steps
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        rows.append({"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / peaks["bf16_tflops"]})
+    print(json.dumps({"metric": "tcgen05 GEMM throughput", "unit": "TFLOP/s", "impl": "gb300", "n_gpus": 1,
+                      "peak": peaks["bf16_tflops"], "peak_kind": peak_kind, "shapes": rows}), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- boiling example
 def run_boiling(args):
     """The paper's phase-formation example (Sec. V): a 1-D column of 101 wet nodes (h = 100,
@@ -685,7 +717,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
-    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling"], default="domain",
+    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling", "gemm"],
+                    default="domain",
                     help="domain: the 1024 x 4096 single-domain throughput line (default); "
                          "columns: time to steady state of batched columns; "
                          "thermal: the 512 x 2048 thermal column")
@@ -701,6 +734,7 @@ def main(argv=None):
     ap.add_argument("--accel-checks", type=int, default=None, help="extrapolation cycle of the FP32 -> FP64 runs "
                                                                     "in residual checks (default 5; 0: off)")
     ap.add_argument("--boiling-dT", default="0.3166,0.3381,0.3382")
+    ap.add_argument("--gemm-m", type=int, default=65536, help="rows of the network-shaped GEMM")
     ap.add_argument("--boiling-steps", type=int, default=1000000)
     ap.add_argument("--boiling-prerun-cap", type=int, default=4000000)
     ap.add_argument("--mlp-iters", type=int, default=6000)
@@ -725,6 +759,8 @@ def main(argv=None):
         return run_warmstart(args) if rank == 0 else 0
     if args.workload == "boiling":
         return run_boiling(args) if rank == 0 else 0
+    if args.workload == "gemm":
+        return run_gemm(args) if rank == 0 else 0
 
     import numpy as np
     import torch
