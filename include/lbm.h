@@ -342,6 +342,14 @@ int lbm_mlp_warm_start(lbm_mlp* h, const lbm_column* cols, int ncols, int nx, do
  * <= 0: no split) summed by atomic adds. Synchronises `stream`. */
 int lbm_mlp_gemm(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N, int K,
                  int k_split, int accumulate, void* stream);
+/* lbm_mlp_gemm without synchronisation or allocation: the product is enqueued on `stream`
+ * (so it can be captured in a CUDA graph) and nothing waits for it. status: caller-owned
+ * DEVICE int that the kernel ORs a non-zero bit into when one of its bounded tensor-core
+ * waits timed out (C is then incomplete); the caller zeroes it and reads it after the
+ * stream completes. The arguments are checked as for lbm_mlp_gemm (LBM_EINVAL); a launch
+ * error returns LBM_ECUDA. Text in lbm_last_error(NULL). */
+int lbm_mlp_gemm_enqueue(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N,
+                         int K, int k_split, int accumulate, int* status, void* stream);
 /* Release a network. NULL is accepted. */
 int lbm_mlp_destroy(lbm_mlp* h);
 

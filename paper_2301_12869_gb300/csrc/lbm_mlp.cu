@@ -9,11 +9,16 @@
 // Every matrix product runs on the tcgen05 tensor cores through one GEMM kernel,
 // C[M x N] = A[M x K] B[N x K]^T with A and B bfloat16, K contiguous:
 //  * a CTA (4 warps) owns a 128 x 128 output tile whose FP32 accumulator lives in 128
-//    TMEM columns; K is consumed in chunks of 64 through two shared-memory stages;
-//  * all threads copy the next chunk into the canonical no-swizzle K-major layout (8-row x
-//    16-byte core matrices: 128 B apart along K, 1024 B apart along M/N) while the tensor
-//    cores work on the current one; one thread issues four 128 x 128 x 16 MMAs per chunk
-//    and commits them to the stage's mbarrier, which the copy into that stage waits for;
+//    TMEM columns; K is consumed in chunks of 64 through kStages shared-memory stages;
+//  * one thread (the producer) fills a stage with two TMA tile copies: a 2-D tensor map
+//    over each row-major operand with a 64-element (128 B) x 128-row box and the 128-byte
+//    swizzle lands the chunk as 128 rows of 128 B, the 16-byte pieces of row r permuted by
+//    r mod 8 - the K-major SWIZZLE_128B layout that the MMA's matrix descriptor names
+//    (8-row groups 1024 B apart; the K = 16 steps start 32 B apart); the copies complete
+//    on the stage's `full` mbarrier;
+//  * a second thread waits for a full stage, issues four 128 x 128 x 16 MMAs on it and
+//    commits them to the stage's `empty` mbarrier, which the producer waits for before
+//    refilling the stage, and after the last chunk to the `done` mbarrier;
 //  * the epilogue reads the accumulator with tcgen05.ld (warp w: rows 32w..32w+31) and
 //    applies a fused operation: store, split-K atomic add, bias + SiLU (forward), or the
 //    SiLU derivative (backward) with the bias gradient as a column sum.
@@ -23,6 +28,7 @@
 #include "lbm_internal.h"
 #include "lbm_ptx.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -58,8 +64,9 @@ __constant__ float kScale[LBM_MLP_INPUTS] = {0.125f, 1.0f, 0.5f, 1.1f, 0.5f};
 
 // ------------------------------------------------------------------ GEMM
 constexpr int BM = 128, BN = 128, BK = 64, GT = 128;
-constexpr int TILE_BYTES = BM * BK * 2;                 // one operand, one stage: 16 KB
-constexpr int GEMM_SMEM = 4 * TILE_BYTES + 1024 + 64;  // A/B x 2 stages, alignment, barriers
+constexpr int kStages = 3;
+constexpr int TILE_BYTES = BM * BK * 2;   // one operand, one stage: 16 KB
+constexpr int GEMM_SMEM = 2 * kStages * TILE_BYTES + 1024 + 128;  // stages, alignment, barriers
 // instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B bfloat16 (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
@@ -85,11 +92,28 @@ struct GemmArgs {
   int* status;
 };
 
-// shared-memory matrix descriptor: no swizzle, K-major; LBO = 128 B (next core matrix
-// along K), SBO = 1024 B (next 8 rows), descriptor version 1 (bits 46-47)
+// shared-memory matrix descriptor, K-major with the 128-byte swizzle (layout type 2 in bits
+// 61-63): SBO = 1024 B between 8-row groups, LBO unused inside one swizzle atom (16 B by
+// convention), descriptor version 1 (bits 46-47); p lies in a 1024-byte aligned tile,
+// offset by 32 B per K = 16 step
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   const uint32_t a = lbm::smem_u32(p);
-  return uint64_t((a >> 4) & 0x3FFF) | (uint64_t(128 >> 4) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46);
+  return uint64_t((a >> 4) & 0x3FFF) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) |
+         (uint64_t(2) << 61);
+}
+
+// TMA: one box of a 2-D tensor map (x = element along K, y = row) into shared memory,
+// completing on an mbarrier
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          lbm::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(lbm::smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(lbm::smem_u32(bar)), "r"(bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
@@ -103,29 +127,18 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// rows r0.. r0+127 of X (row-major, ld elements, columns [k, kend)) into the core-matrix
-// layout of one stage: 16-byte chunk q (row r = 8 (q >> 6) + (q & 7), column block
-// (q >> 3) & 7) goes to byte 16 q; rows >= rows and columns >= kend read as zero
-__device__ __forceinline__ void load_tile(uint8_t* dst, const bf16* X, int ld, int rows, int r0, int k, int kend) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int q = threadIdx.x + GT * i;
-    const int r = 8 * (q >> 6) + (q & 7), kb = (q >> 3) & 7;
-    const int row = r0 + r, col = k + 8 * kb;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (row < rows && col + 8 <= kend) v = *reinterpret_cast<const uint4*>(X + size_t(row) * ld + col);
-    *reinterpret_cast<uint4*>(dst + 16 * q) = v;
-  }
-}
-
 template <int EPI>
-__global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
+__global__ void __launch_bounds__(GT, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA[2] = {smem, smem + TILE_BYTES};
-  uint8_t* sB[2] = {smem + 2 * TILE_BYTES, smem + 3 * TILE_BYTES};
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * TILE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint8_t* sA = smem;                          // stage s at sA + s * TILE_BYTES
+  uint8_t* sB = smem + kStages * TILE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * kStages * TILE_BYTES);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  int* err_s = reinterpret_cast<int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * g.k_split;
@@ -134,8 +147,12 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
   if (nchunks == 0) return;  // uniform over the CTA, before any allocation
 
   if (tid == 0) {
-    lbm::mbar_init(&bar[0], 1);
-    lbm::mbar_init(&bar[1], 1);
+    for (int i = 0; i < kStages; ++i) {
+      lbm::mbar_init(&full[i], 1);
+      lbm::mbar_init(&empty[i], 1);
+    }
+    lbm::mbar_init(done, 1);
+    *err_s = 0;
     lbm::fence_mbar_init();
   }
   if (warp == 0) {
@@ -146,46 +163,54 @@ __global__ void __launch_bounds__(GT, 1) gemm_kernel(const GemmArgs g) {
   __syncthreads();
   lbm::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // K = 16 steps of chunk c (the last chunk may be short: K is a multiple of 16; the box
+  // reads zeros beyond K, and a split boundary is a multiple of BK)
+  auto ksteps = [&](int c) { return min(BK, kend - (kbeg + c * BK)) / 16; };
 
-  load_tile(sA[0], g.A, g.lda, g.M, m0, kbeg, kend);
-  load_tile(sB[0], g.B, g.ldb, g.N, n0, kbeg, kend);
-  lbm::fence_proxy_async_smem();
-  __syncthreads();
-
-  bool ok = true;
-  int c = 0;
-  for (; c < nchunks; ++c) {
-    const int s = c & 1;
-    if (tid == 0) {
-      lbm::tc_fence_after();
-      const int steps = (min(BK, kend - (kbeg + c * BK)) + 15) / 16;
-      for (int j = 0; j < steps; ++j)
-        lbm::tc_mma_f16(tmem, smem_desc(sA[s] + 256 * j), smem_desc(sB[s] + 256 * j), kIdesc, (c > 0 || j > 0) ? 1u : 0u);
-      lbm::tc_commit(&bar[s]);
-    }
-    if (c + 1 < nchunks) {
-      // stage s^1 was read by the MMAs of chunk c - 1: wait for their commit
-      if (c >= 1) ok = lbm::mbar_wait_bounded(&bar[(c - 1) & 1], uint32_t(((c - 1) >> 1) & 1)) && ok;
-      if (ok) {
-        const int k = kbeg + (c + 1) * BK;
-        load_tile(sA[s ^ 1], g.A, g.lda, g.M, m0, k, kend);
-        load_tile(sB[s ^ 1], g.B, g.ldb, g.N, n0, k, kend);
-        lbm::fence_proxy_async_smem();
+  int c = 0;  // producer: chunks whose copies were issued
+  if (tid == 0) {
+    // producer: TMA copies of A and B for every chunk, each into a free stage
+    for (; c < nchunks; ++c) {
+      const int st = c % kStages;
+      if (c >= kStages && !lbm::mbar_wait_bounded(&empty[st], uint32_t(((c / kStages) - 1) & 1))) {
+        atomicOr(err_s, 1);
+        break;
       }
+      mbar_expect_tx(&full[st], uint32_t(2 * TILE_BYTES));  // whole boxes, zero fill included
+      const int k = kbeg + c * BK;
+      tma_load_2d(sA + st * TILE_BYTES, &mapA, k, m0, &full[st]);
+      tma_load_2d(sB + st * TILE_BYTES, &mapB, k, n0, &full[st]);
     }
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      ++c;
-      break;
+  } else if (tid == 32) {
+    // MMA issuer: four K = 16 steps per chunk, the stage freed by the commit
+    for (int c = 0; c < nchunks; ++c) {
+      const int st = c % kStages;
+      if (!lbm::mbar_wait_bounded(&full[st], uint32_t((c / kStages) & 1))) {
+        atomicOr(err_s, 1);
+        break;
+      }
+      lbm::tc_fence_after();
+      const int steps = ksteps(c);
+      for (int j = 0; j < steps; ++j)
+        lbm::tc_mma_f16(tmem, smem_desc(sA + st * TILE_BYTES + 32 * j), smem_desc(sB + st * TILE_BYTES + 32 * j),
+                        kIdesc, (c > 0 || j > 0) ? 1u : 0u);
+      lbm::tc_commit(&empty[st]);
     }
+    lbm::tc_commit(done);  // every MMA issued so far, also after an error
   }
-  // the last chunk issued (c - 1) completes after every earlier one
-  const int last = c - 1;
-  const bool done = lbm::mbar_wait_bounded(&bar[last & 1], uint32_t((last >> 1) & 1), ok ? kWaitCycles : kWaitCycles / 4);
-  ok = __syncthreads_and(ok && done);
+  // the accumulator is final once `done` completes
+  const bool fin = lbm::mbar_wait_bounded(done, 0u);
+  bool ok = __syncthreads_and(fin && *err_s == 0);
   lbm::tc_fence_after();
   if (!ok) {
-    if (tid == 0) atomicOr(g.status, lbm::STATUS_TIMEOUT);
+    if (tid == 0) {
+      atomicOr(g.status, lbm::STATUS_TIMEOUT);
+      // copies in flight must land before the CTA's shared memory goes away: only the last
+      // kStages issued chunks can be outstanding (a stage is refilled after its previous
+      // chunk was consumed); bounded waits
+      for (int q = max(0, c - kStages); q < c; ++q)
+        (void)lbm::mbar_wait_bounded(&full[q % kStages], uint32_t((q / kStages) & 1), kWaitCycles / 8);
+    }
   } else {
     const int m = m0 + 32 * warp + lane;
     const bool row_ok = m < g.M;
@@ -448,10 +473,43 @@ cudaError_t gemm_prepare() {
   return e;
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link)
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encoder() {
+  static EncodeTiled fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// 2-D map of a row-major bfloat16 matrix (rows x cols, ld elements per row) with a
+// BK-element x 128-row box written with the 128-byte swizzle; reads outside the matrix
+// fill zeros
+bool make_map(CUtensorMap* m, const bf16* base, int rows, int cols, int ld) {
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(ld) * 2};
+  const cuuint32_t box[2] = {BK, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int EPI>
 cudaError_t gemm(const GemmArgs& a, int splits, cudaStream_t s) {
   const dim3 grid((a.M + BM - 1) / BM, (a.N + BN - 1) / BN, splits);
-  gemm_kernel<EPI><<<grid, GT, GEMM_SMEM, s>>>(a);
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, a.A, a.M, a.K, a.lda) || !make_map(&mB, a.B, a.N, a.K, a.ldb)) return cudaErrorInvalidValue;
+  gemm_kernel<EPI><<<grid, GT, GEMM_SMEM, s>>>(mA, mB, a);
   return cudaGetLastError();
 }
 
@@ -796,8 +854,10 @@ int lbm_mlp_warm_start(lbm_mlp* h, const lbm_column* cols, int ncols, int nx, do
   return rc;
 }
 
-int lbm_mlp_gemm(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N, int K,
-                 int k_split, int accumulate, void* stream) {
+namespace {
+// checks of lbm_mlp_gemm / lbm_mlp_gemm_enqueue, then the launch on stream s
+int gemm_launch(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N, int K,
+                int k_split, int accumulate, int* status, cudaStream_t s) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 16 || K % 16) return fail(LBM_EINVAL, "need M, N >= 1 and K a multiple of 16");
   if (lda % 8 || ldb % 8 || lda < K || ldb < K || ldc < N) return fail(LBM_EINVAL, "lda, ldb multiples of 8 and >= K; ldc >= N");
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) return fail(LBM_EINVAL, "A and B 16-byte aligned");
@@ -806,23 +866,40 @@ int lbm_mlp_gemm(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* 
   if (!accumulate && k_split < K) return fail(LBM_EINVAL, "split K needs accumulate");
   cudaError_t e = gemm_prepare();
   if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel attributes: %s", cudaGetErrorString(e));
-  int* status = nullptr;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  MLP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int), s));
-  MLP_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
   GemmArgs a = gargs(reinterpret_cast<const bf16*>(A), lda, reinterpret_cast<const bf16*>(B), ldb, M, N, K, status);
   a.k_split = std::min(K, (k_split + BK - 1) / BK * BK);
   a.C = C;
   a.ldc = ldc;
   const int splits = (K + a.k_split - 1) / a.k_split;
   e = accumulate ? gemm<EPI_ATOMIC>(a, splits, s) : gemm<EPI_STORE>(a, 1, s);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "gemm: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+}  // namespace
+
+int lbm_mlp_gemm(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N, int K,
+                 int k_split, int accumulate, void* stream) {
+  int* status = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MLP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int), s));
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  int rc = e == cudaSuccess ? gemm_launch(A, lda, B, ldb, C, ldc, M, N, K, k_split, accumulate, status, s)
+                            : fail(LBM_ECUDA, "gemm: %s", cudaGetErrorString(e));
   int st = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (rc == LBM_OK) e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaFreeAsync(status, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (rc != LBM_OK) return rc;
+  if (e == cudaSuccess) e = es;
   if (e != cudaSuccess) return fail(LBM_ECUDA, "gemm: %s", cudaGetErrorString(e));
   if (st & lbm::STATUS_TIMEOUT) return fail(LBM_ETIMEOUT, "a tensor-core wait timed out");
   return LBM_OK;
+}
+
+int lbm_mlp_gemm_enqueue(const uint16_t* A, int lda, const uint16_t* B, int ldb, float* C, int ldc, int M, int N,
+                         int K, int k_split, int accumulate, int* status, void* stream) {
+  if (!status || reinterpret_cast<uintptr_t>(status) % alignof(int)) return fail(LBM_EINVAL, "status: an aligned device int");
+  return gemm_launch(A, lda, B, ldb, C, ldc, M, N, K, k_split, accumulate, status, static_cast<cudaStream_t>(stream));
 }
 
 int lbm_mlp_destroy(lbm_mlp* h) {

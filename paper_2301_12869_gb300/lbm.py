@@ -43,7 +43,8 @@ EXPORTS = (
     "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
     "lbm_batch_convert", "lbm_batch_destroy",
     "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
-    "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_destroy",
+    "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_gemm_enqueue",
+    "lbm_mlp_destroy",
 )
 
 MLP_WIDTH, MLP_INPUTS, MLP_IN_PAD = 128, 5, 16
@@ -132,6 +133,7 @@ def load(path: str = LIB_PATH):
         "lbm_mlp_features": (i32, [vp, i32, i32, d, d, d, vp, vp, vp, vp, vp]),
         "lbm_mlp_warm_start": (i32, [vp, vp, i32, i32, d, d, d, vp, vp]),
         "lbm_mlp_gemm": (i32, [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp]),
+        "lbm_mlp_gemm_enqueue": (i32, [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp]),
         "lbm_mlp_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -548,6 +550,15 @@ def lbm_mlp_gemm(A, B, C, k_split=0, accumulate=False, stream=None):
     N = B.shape[0]
     _check(load().lbm_mlp_gemm(_dev(A), A.stride(0), _dev(B), B.stride(0), _dev(C), C.stride(0), M, N, K,
                                int(k_split), 1 if accumulate else 0, stream))
+
+
+def lbm_mlp_gemm_enqueue(A, B, C, status, k_split=0, accumulate=False, stream=None):
+    """lbm_mlp_gemm enqueued on `stream` without waiting; status: a CUDA int32 tensor of one
+    element that the kernel ORs a non-zero bit into on a tensor-core wait timeout."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(load().lbm_mlp_gemm_enqueue(_dev(A), A.stride(0), _dev(B), B.stride(0), _dev(C), C.stride(0), M, N, K,
+                                       int(k_split), 1 if accumulate else 0, _dev(status), stream))
 
 
 def lbm_mlp_destroy(h):

@@ -46,6 +46,9 @@ def bf16_bits(a):
     (300, 200, 192, 0, False),    # ragged M and N (two N tiles), three K chunks through both stages
     (128, 16, 1024, 256, True),   # split K with atomic accumulation, N = 16
     (256, 128, 640, 0, False),    # ten K chunks
+    (40, 24, 80, 0, False),       # one partial tile in M and N; the second chunk has one K step
+    (512, 384, 4096, 1024, True), # four K splits of sixteen chunks: every stage refilled five times
+    (128, 128, 1040, 0, False),   # seventeen chunks, the last one K step
 ])
 def test_tensor_core_gemm_matches_exact_product(M, N, K, k_split, acc):
     import torch
@@ -59,6 +62,35 @@ def test_tensor_core_gemm_matches_exact_product(M, N, K, k_split, acc):
     want = Ar @ Br.T + (C0 if acc else 0.0)
     bound = 2 * K * 2.0**-24 * (np.abs(Ar) @ np.abs(Br).T) + 1e-6 * np.abs(C0)
     assert np.all(np.abs(C.cpu().numpy() - want) <= bound + 1e-30)
+
+
+def test_enqueued_gemm_replays_in_a_cuda_graph():
+    """lbm_mlp_gemm_enqueue allocates and waits for nothing: captured once in a CUDA graph
+    with the accumulating epilogue, each replay adds A B^T to C again; the status word stays 0."""
+    import torch
+
+    M, N, K = 384, 256, 320
+    rng = np.random.default_rng(17)
+    A, Ar = bf16_bits(rng.normal(size=(M, K)))
+    B, Br = bf16_bits(rng.normal(size=(N, K)))
+    C = torch.zeros(M, N, device="cuda", dtype=torch.float32)
+    status = torch.zeros(1, device="cuda", dtype=torch.int32)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        lbm.lbm_mlp_gemm_enqueue(A, B, C, status, accumulate=True, stream=s.cuda_stream)  # eager, before capture
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        lbm.lbm_mlp_gemm_enqueue(A, B, C, status, accumulate=True, stream=s.cuda_stream)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    want = 4.0 * (Ar @ Br.T)
+    bound = 4 * 2 * K * 2.0**-24 * (np.abs(Ar) @ np.abs(Br).T) + 4 * 2.0**-22 * np.abs(want)
+    assert np.all(np.abs(C.cpu().numpy() - want) <= bound + 1e-30)
+    assert int(status.item()) == 0
+    with pytest.raises(lbm.LbmError, match="multiple of 16"):
+        lbm.lbm_mlp_gemm_enqueue(A[:, :24].contiguous(), B[:, :24].contiguous(), C, status)
 
 
 def params_for_test(seed=1):
