@@ -19,9 +19,12 @@
 //  * a second thread waits for a full stage, issues four 128 x 128 x 16 MMAs on it and
 //    commits them to the stage's `empty` mbarrier, which the producer waits for before
 //    refilling the stage, and after the last chunk to the `done` mbarrier;
-//  * the epilogue reads the accumulator with tcgen05.ld (warp w: rows 32w..32w+31) and
-//    applies a fused operation: store, split-K atomic add, bias + SiLU (forward), or the
-//    SiLU derivative (backward) with the bias gradient as a column sum.
+//  * the epilogue reads the accumulator with tcgen05.ld (warp w: rows 32w..32w+31, one row
+//    per lane), turns each 32 x 32 piece around in shared memory so that the lanes run
+//    along a row of C, and applies a fused operation with coalesced accesses: store,
+//    split-K atomic add, bias + SiLU (forward), or the SiLU derivative (backward) with the
+//    bias gradient as a column sum; transposed bfloat16 copies go out with the lanes
+//    along the rows again.
 // Waits are bounded (clock64); a timeout sets the status word and the CTA still waits
 // (bounded) for its MMAs and frees its TMEM before returning.
 #include "lbm.h"
@@ -212,42 +215,59 @@ __global__ void __launch_bounds__(GT, 1)
         (void)lbm::mbar_wait_bounded(&full[q % kStages], uint32_t((q / kStages) & 1), kWaitCycles / 8);
     }
   } else {
-    const int m = m0 + 32 * warp + lane;
-    const bool row_ok = m < g.M;
+    // each warp stages its 32 x 32 pieces of the accumulator through a padded shared tile
+    // (the drained stage buffers) so that global rows are written by 32 lanes at once:
+    // t[r][c] holds row 32 warp + r, column nb + c
+    float* t = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+    const int mw = m0 + 32 * warp;
+    float csum = 0.0f;  // EPI_BWD: this lane's column sum over the warp's rows
 #pragma unroll 1
     for (int cc = 0; cc < BN / 32; ++cc) {
       float v[32];
       lbm::tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(32 * cc), v);
       const int nb = n0 + 32 * cc;
+      const int n = nb + lane;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int n = nb + i;
-        const bool in = row_ok && n < g.N;
+      for (int i = 0; i < 32; ++i) t[lane * 33 + i] = v[i];
+      __syncwarp();
+      if constexpr (EPI == EPI_BWD) csum = 0.0f;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int m = mw + r;
+        const bool in = m < g.M && n < g.N;
+        const float x = t[r * 33 + lane];
         if constexpr (EPI == EPI_STORE) {
-          if (in) g.C[size_t(m) * g.ldc + n] = v[i];
+          if (in) g.C[size_t(m) * g.ldc + n] = x;
         } else if constexpr (EPI == EPI_ATOMIC) {
-          if (in) atomicAdd(g.C + size_t(m) * g.ldc + n, v[i]);
+          if (in) atomicAdd(g.C + size_t(m) * g.ldc + n, x);
         } else if constexpr (EPI == EPI_FWD) {
           if (in) {
-            const float z = v[i] + g.bias[n];
+            const float z = x + g.bias[n];
             g.Z[size_t(m) * g.ldz + n] = z;
             const bf16 h = __float2bfloat16_rn(silu_f(z));
             if (g.H) g.H[size_t(m) * g.ldh + n] = h;
-            if (g.HT) g.HT[size_t(n) * g.ldht + m] = h;
+            t[r * 33 + lane] = __bfloat162float(h);
           }
         } else {  // EPI_BWD
-          const float dz = in ? v[i] * dsilu_f(g.Z[size_t(m) * g.ldz + n]) : 0.0f;
-          if (in) {
-            const bf16 d = __float2bfloat16_rn(dz);
-            if (g.H) g.H[size_t(m) * g.ldh + n] = d;
-            if (g.HT) g.HT[size_t(n) * g.ldht + m] = d;
-          }
-          if (g.colsum) {
-            const float sum = warp_sum_f(dz);
-            if (lane == 0 && n < g.N) atomicAdd(g.colsum + n, sum);
-          }
+          const float dz = in ? x * dsilu_f(g.Z[size_t(m) * g.ldz + n]) : 0.0f;
+          const bf16 d = __float2bfloat16_rn(dz);
+          if (in && g.H) g.H[size_t(m) * g.ldh + n] = d;
+          t[r * 33 + lane] = __bfloat162float(d);
+          csum += dz;
         }
       }
+      if constexpr (EPI == EPI_FWD || EPI == EPI_BWD) {
+        if (g.colsum && n < g.N) atomicAdd(g.colsum + n, csum);
+        // the transposed copy, lanes along rows again: HT[n][m] for consecutive m
+        if (g.HT) {
+          __syncwarp();
+          const int m = mw + lane;
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i)
+            if (m < g.M && nb + i < g.N) g.HT[size_t(nb + i) * g.ldht + m] = __float2bfloat16_rn(t[lane * 33 + i]);
+        }
+      }
+      __syncwarp();
     }
   }
   lbm::tc_fence_before();
