@@ -857,7 +857,7 @@ def main(argv=None):
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profile(args.precision),
-            "peak_kind": peak_kind, "kernel": ("step_kernel_ws<8 consumer warps, 4 stages>" if args.precision == "fp32"
+            "peak_kind": peak_kind, "kernel": (f"step_kernel_ws<8 consumer warps, {info['stages']} stages>" if args.precision == "fp32"
                                                 else "step_kernel<double, 128-node bands>"),
             "algorithmic_bytes_per_launch": alg_bytes,
         },

@@ -772,7 +772,7 @@ int lbm_launch_info(const lbm_handle* h, int* grid, int* block, int* smem_bytes,
   if (smem_bytes) *smem_bytes = h->tiling.smem_bytes;
   if (band_width) *band_width = h->tiling.band_w;
   if (strip_rows) *strip_rows = h->tiling.strip_h;
-  if (stages) *stages = lbm::stages();
+  if (stages) *stages = lbm::stages(h->p.precision, h->tiling.variant);
   return LBM_OK;
 }
 

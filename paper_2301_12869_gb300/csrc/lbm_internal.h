@@ -51,7 +51,7 @@ struct StepIO {
 };
 
 // ---- launch wrappers (lbm_kernels.cu). All are asynchronous on `stream`.
-int stages();  // pipeline depth of the fused kernel
+int stages(int precision, int variant);  // pipeline depth (rows in shared memory) of a tile variant
 int step_num_variants(int precision);
 // has the thermal and Zou-He wall kernels (io.Tfield set, StepPhys::wall = LBM_WALL_ZOU_HE)
 bool step_variant_extended(int precision, int variant);

@@ -93,6 +93,18 @@ __device__ __forceinline__ void pull(const float* st, int loc, bool lo_wall, boo
   const float* p = st + loc;
   auto pair = [&](int off) { return make_f2(p[off], p[off + 1]); };
   auto aligned = [&](int off) { return *reinterpret_cast<const f2*>(p + off); };
+  if (!(lo_wall || hi_wall)) {  // interior row (uniform over a warp): no selects
+    g[0] = aligned(0 * SW);
+    g[1] = pair(1 * SW - 1);
+    g[2] = aligned(2 * SW);
+    g[3] = pair(3 * SW + 1);
+    g[4] = aligned(4 * SW);
+    g[5] = pair(5 * SW - 1);
+    g[6] = pair(6 * SW + 1);
+    g[7] = pair(7 * SW + 1);
+    g[8] = pair(8 * SW - 1);
+    return;
+  }
   g[0] = aligned(0 * SW);
   g[1] = pair(1 * SW - 1);
   g[2] = aligned(2 * SW);
@@ -575,6 +587,10 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     V gp[9];  // pulled populations of walk row kk - 1
 #pragma unroll
     for (int i = 0; i < 9; ++i) gp[i] = cst<V>(0.0);
+    // two rows per iteration: the row state rotates by renaming instead of copies (the
+    // Zou-He kernels, with their wall-row code, would spill)
+    constexpr int kRowUnroll = ZH ? 1 : 2;
+#pragma unroll kRowUnroll
     for (int kk = 0; kk < nrows; ++kk) {
       const int q = row_of(kk), s = kk % S;
       if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], uint32_t((kk / S) & 1)))) {
@@ -780,7 +796,7 @@ constexpr int kExt = 3;
 __host__ __device__ constexpr int ext_index(bool th, bool zh) { return th && zh ? 2 : (zh ? 1 : 0); }
 
 struct VariantF {  // FP32 storage; `paired` variants evaluate two nodes per value
-  int bw, threads;
+  int bw, threads, stages;
   bool paired;
   StepFnF step, step_unit, moments;      // scalar variants
   StepFnP pstep, pstep_unit, pmoments;   // paired variants
@@ -788,7 +804,7 @@ struct VariantF {  // FP32 storage; `paired` variants evaluate two nodes per val
   ExtFns<StepFnP> ext[kExt] = {};        // paired extensions (variant 0 only)
 };
 struct VariantD {
-  int bw, threads;
+  int bw, threads, stages;
   StepFnD step, step_unit, moments;
   size_t smem;
   ExtFns<StepFnD> ext[kExt] = {};
@@ -796,7 +812,7 @@ struct VariantD {
 
 template <int BW, int NPT, int MINB>
 constexpr VariantF make_f() {
-  return VariantF{BW, BW / NPT, false,
+  return VariantF{BW, BW / NPT, kStages, false,
                   step_kernel<float, float, MODE_STEP, false, BW, NPT, MINB>,
                   step_kernel<float, float, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<float, float, MODE_MOMENTS, false, BW, NPT, MINB>,
@@ -804,14 +820,14 @@ constexpr VariantF make_f() {
 }
 template <int BW, int NPT, int MINB>
 constexpr VariantF make_p() {
-  return VariantF{BW, BW / NPT, true, nullptr, nullptr, nullptr,
+  return VariantF{BW, BW / NPT, kStages, true, nullptr, nullptr, nullptr,
                   step_kernel<float, f2, MODE_STEP, false, BW, NPT, MINB>,
                   step_kernel<float, f2, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<float, f2, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<float, BW>()};
 }
 template <int BW, int NPT, int MINB>
 constexpr VariantD make_d() {
-  return VariantD{BW, BW / NPT, step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB>,
+  return VariantD{BW, BW / NPT, kStages, step_kernel<double, double, MODE_STEP, false, BW, NPT, MINB>,
                   step_kernel<double, double, MODE_STEP, true, BW, NPT, MINB>,
                   step_kernel<double, double, MODE_MOMENTS, false, BW, NPT, MINB>, step_smem<double, BW>()};
 }
@@ -833,7 +849,7 @@ constexpr VariantD make_d_ext() {
 
 template <int NWC, int S, int MINB>
 constexpr VariantF make_ws() {
-  return VariantF{64 * NWC, (NWC + 1) * 32, true, nullptr, nullptr, nullptr,
+  return VariantF{64 * NWC, (NWC + 1) * 32, S, true, nullptr, nullptr, nullptr,
                   step_kernel_ws<MODE_STEP, false, NWC, S, MINB>, step_kernel_ws<MODE_STEP, true, NWC, S, MINB>,
                   step_kernel_ws<MODE_MOMENTS, false, NWC, S, MINB>, ws_smem<NWC, S>()};
 }
@@ -852,7 +868,7 @@ constexpr VariantF make_ws_ext() {
 }
 
 const VariantF kVariantsF[] = {
-    make_ws_ext<8, 4, 2>(),  // barrier-free: 8 consumer warps + producer, 4 stages, 75 KB (+ thermal, Zou-He)
+    make_ws_ext<8, 3, 2>(),  // barrier-free: 8 consumer warps + producer, 3 stages, 56 KB (+ thermal, Zou-He)
     make_ws<4, 4, 4>(),      // barrier-free: 4 consumer warps + producer, 4 stages, 38 KB
     make_p<256, 2, 5>(),     // pairs, 4 warps, 42 KB shared, one CTA barrier per row
     make_f<256, 2, 5>(),     // scalar, 4 warps, 42 KB shared, one CTA barrier per row
@@ -907,7 +923,9 @@ int grid_for(size_t n, int block) {
 }  // namespace
 
 // ---------------------------------------------------------------- launch wrappers
-int stages() { return kStages; }
+int stages(int precision, int variant) {
+  return precision == 1 ? kVariantsF[variant].stages : kVariantsD[variant].stages;
+}
 
 int step_num_variants(int precision) { return precision == 1 ? kNumF : kNumD; }
 

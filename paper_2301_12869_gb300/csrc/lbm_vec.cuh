@@ -22,11 +22,13 @@ __device__ __forceinline__ f2 make_f2(float a, float b) {
 __device__ __forceinline__ float lo(f2 x) {
   float a, b;
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+  (void)b;
   return a;
 }
 __device__ __forceinline__ float hi(f2 x) {
   float a, b;
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+  (void)a;
   return b;
 }
 __device__ __forceinline__ f2 operator+(f2 a, f2 b) {
@@ -81,13 +83,23 @@ __device__ __forceinline__ V cst(double c) {
 }
 
 // Division and square root: IEEE in FP64 (the FP64 path is checked to 1e-14); in FP32
-// the fast intrinsics __fdividef (<= 2 ulp) and rsqrtf (<= 2 ulp) add at most a few
-// ulp, far inside the FP32 path's 1e-6 bound against the FP64 oracle.
+// the fast intrinsics __fdividef (<= 2 ulp) and rsqrtf (<= 2 ulp), and for node pairs the
+// approximate reciprocal and square root instructions (rcp.approx / sqrt.approx, a few
+// ulp), add at most a few ulp, far inside the FP32 path's 1e-6 bound against the FP64
+// oracle.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ f2 fast_div(f2 a, f2 b) {
-  return make_f2(__fdividef(lo(a), lo(b)), __fdividef(hi(a), hi(b)));
-}
+__device__ __forceinline__ f2 fast_div(f2 a, f2 b) { return a * make_f2(rcp_approx(lo(b)), rcp_approx(hi(b))); }
 
 // sqrt of max(x, 0); sets `bad` when x < 0 or NaN (psi undefined)
 __device__ __forceinline__ double sqrt_checked(double x, bool& bad) {
@@ -105,7 +117,9 @@ __device__ __forceinline__ float sqrt_checked(float x, bool& bad) {
   return x > 0.f ? x * rsqrtf(x) : 0.f;
 }
 __device__ __forceinline__ f2 sqrt_checked(f2 x, bool& bad) {
-  return make_f2(sqrt_checked(lo(x), bad), sqrt_checked(hi(x), bad));
+  const float s = lo(x), t = hi(x);
+  if (!(s >= 0.f) || !(t >= 0.f)) bad = true;
+  return make_f2(sqrt_approx(fmaxf(s, 0.f)), sqrt_approx(fmaxf(t, 0.f)));
 }
 
 // true if any component is <= 0 or NaN
