@@ -37,6 +37,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -134,6 +136,8 @@ __device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (
 // neighbouring strips reach their common halo rows at the same time (L2 reuse).
 template <typename T, typename V, int MODE, bool UNIT, int BW, int NPT, int MINB, bool TH = false, bool ZH = false>
 __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling tl, const PhysT<V> k, const StepIO io) {
+  griddep_wait();  // launched as a dependent of the previous step: its state is complete
+  griddep_launch_dependents();
   constexpr int NT = BW / NPT;
   constexpr int VW = VecTraits<V>::width;  // nodes per value
   constexpr int NU = NPT / VW;             // values per thread
@@ -430,6 +434,8 @@ struct PsiRow {  // psi at the left neighbour, the lane's own pair, the right ne
 template <int MODE, bool UNIT, int NWC, int S, int MINB, bool TH = false, bool ZH = false>
 __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     step_kernel_ws(const StepTiling tl, const PhysT<f2> k, const StepIO io) {
+  griddep_wait();  // launched as a dependent of the previous step: its state is complete
+  griddep_launch_dependents();
   using T = float;
   using V = f2;
   constexpr int BW = 64 * NWC;
@@ -972,6 +978,25 @@ cudaError_t step_prepare(int precision) {
   return cudaSuccess;
 }
 
+// A step kernel launched as a programmatic dependent of the previous kernel in the stream:
+// the launch and the block set-up overlap that kernel's last blocks; the kernel's first
+// instruction waits for it to complete (griddep_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
+
 cudaError_t launch_step(int precision, int mode, const StepTiling& t, const StepPhys& ph, const StepIO& io,
                         cudaStream_t stream) {
   const dim3 grid(t.nbands * t.nstrips), block(t.threads);
@@ -983,13 +1008,13 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
       const ExtFns<StepFnP>& x = v.ext[ext_index(th, zh)];
       const StepFnP fn = mode == MODE_MOMENTS ? x.moments : (unit ? x.step_unit : x.step);
       if (!fn) return cudaErrorInvalidValue;  // no extension kernels for this tile variant
-      fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<f2>(ph), io);
+      return launch_dependent(fn, grid, block, t.smem_bytes, stream, t, to_phys<f2>(ph), io);
     } else if (v.paired) {
       const StepFnP fn = mode == MODE_MOMENTS ? v.pmoments : (unit ? v.pstep_unit : v.pstep);
-      fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<f2>(ph), io);
+      return launch_dependent(fn, grid, block, t.smem_bytes, stream, t, to_phys<f2>(ph), io);
     } else {
       const StepFnF fn = mode == MODE_MOMENTS ? v.moments : (unit ? v.step_unit : v.step);
-      fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<float>(ph), io);
+      return launch_dependent(fn, grid, block, t.smem_bytes, stream, t, to_phys<float>(ph), io);
     }
   } else {
     const VariantD& v = kVariantsD[t.variant];
@@ -999,9 +1024,8 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
       fn = mode == MODE_MOMENTS ? x.moments : (unit ? x.step_unit : x.step);
     }
     if (!fn) return cudaErrorInvalidValue;  // no extension kernels for this tile variant
-    fn<<<grid, block, t.smem_bytes, stream>>>(t, to_phys<double>(ph), io);
+    return launch_dependent(fn, grid, block, t.smem_bytes, stream, t, to_phys<double>(ph), io);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_init(int precision, const double* rho0, void* f, int nx, int ny, double rho_ref,

@@ -32,6 +32,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Waits for the phase with the given parity; gives up after `limit` clock cycles.
+// Programmatic dependent launch. A kernel launched with the programmatic stream
+// serialization attribute may start while the previous kernel in its stream is still
+// running; griddep_wait() returns once that kernel has completed and its writes are
+// visible, so nothing before it may touch global memory that kernel reads or writes.
+// griddep_launch_dependents() lets the next kernel of the stream be scheduled (its blocks
+// take the resources of this kernel's blocks as they exit, and wait in turn).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
