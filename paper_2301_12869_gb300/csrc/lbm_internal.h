@@ -47,6 +47,9 @@ struct StepIO {
   double* rho_out;         // MODE_MOMENTS outputs, [y][x] doubles (may be NULL)
   double* ux_out;
   double* uy_out;
+  float* rho32;            // MODE_MOMENTS with FP32 storage, barrier-free tile: rho, u as floats
+  float* ux32;             // (may be NULL), [y][x]
+  float* uy32;
   const void* Tfield;      // thermal variant: real[ny][nx] temperature (NULL: uniform T)
 };
 
@@ -82,11 +85,12 @@ cudaError_t launch_profile_scan(const double* rowmean, int ny, double level, dou
 
 // ---- thermal variant (lbm_thermal.cu): Eq. Energy_Equation on a real[ny][nx] field
 // One Heun step in one launch: Tout = Tin + (k1 + k2)/2 with k1 = L(Tin), k2 = L(Tin + k1),
-// rho, ux, uy ([y][x] doubles) held fixed. Tin and Tout are distinct real[ny][nx] fields.
-// wall_nodes: rows 0 and ny - 1 keep their temperature (Zou-He walls); else wall ghosts.
+// rho, ux, uy ([y][x] real: float for precision 1, double for 2) held fixed. Tin and Tout
+// are distinct real[ny][nx] fields. wall_nodes: rows 0 and ny - 1 keep their temperature
+// (Zou-He walls); else wall ghosts.
 cudaError_t launch_energy_step(int precision, int nx, int ny, int wall_nodes, double R, double b, double c_v,
-                               double kappa, double T_bot, double T_top, const double* rho, const double* ux,
-                               const double* uy, const void* Tin, void* Tout, cudaStream_t stream);
+                               double kappa, double T_bot, double T_top, const void* rho, const void* ux,
+                               const void* uy, const void* Tin, void* Tout, cudaStream_t stream);
 // Tf = T_bot + (T_top - T_bot)(y + 1/2)/ny, or T_bot + (T_top - T_bot) y/(ny - 1) with wall nodes
 cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, int wall_nodes, void* Tf,
                             cudaStream_t stream);

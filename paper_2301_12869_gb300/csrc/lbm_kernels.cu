@@ -37,8 +37,6 @@
 
 #include <cuda_runtime.h>
 
-#include <utility>
-
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -586,6 +584,10 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
         if (io.rho_out) { io.rho_out[node] = lo(rho); io.rho_out[node + 1] = hi(rho); }
         if (io.ux_out) { io.ux_out[node] = lo(ux); io.ux_out[node + 1] = hi(ux); }
         if (io.uy_out) { io.uy_out[node] = lo(uy); io.uy_out[node + 1] = hi(uy); }
+        // FP32 outputs: one aligned pair per lane, no FP64 conversion (slow on GB300)
+        if (io.rho32) *reinterpret_cast<V*>(io.rho32 + node) = rho;
+        if (io.ux32) *reinterpret_cast<V*>(io.ux32 + node) = ux;
+        if (io.uy32) *reinterpret_cast<V*>(io.uy32 + node) = uy;
       }
     };
 
@@ -596,9 +598,20 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     // two rows per iteration: the row state rotates by renaming instead of copies (the
     // Zou-He kernels, with their wall-row code, would spill)
     constexpr int kRowUnroll = ZH ? 1 : 2;
+    // thermal variant: T of the next walk row is loaded one row ahead, so its latency hides
+    // behind the current row's work
+    const T* Tcol = TH ? Tf + xa + j - 1 : nullptr;
+    V Tq = cst<V>(0.0);
+    if constexpr (TH) {
+      if (active) Tq = load_value(Tcol + size_t(row_of(0)) * nx, V{});
+    }
 #pragma unroll kRowUnroll
     for (int kk = 0; kk < nrows; ++kk) {
       const int q = row_of(kk), s = kk % S;
+      V Tn = cst<V>(0.0);
+      if constexpr (TH) {
+        if (active && kk + 1 < nrows) Tn = load_value(Tcol + size_t(row_of(kk + 1)) * nx, V{});
+      }
       if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], uint32_t((kk / S) & 1)))) {
         flag |= STATUS_TIMEOUT;
         failed = true;
@@ -623,7 +636,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       if (lane == 0) mbar_arrive(&empty[s]);  // this warp has read everything it needs of row kk
       PsiRow nw;
       if (active) {
-        const V RT = TH ? k.R * load_value(Tf + size_t(q) * nx + xa + j - 1, V{}) : k.RT;
+        const V RT = TH ? k.R * Tq : k.RT;
         nw.c = psi_of<V>(k.rho_ref + sum9(g), RT, k, flag);
       } else {
         nw.c = cst<V>(0.0);
@@ -647,6 +660,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       }
 #pragma unroll
       for (int i = 0; i < 9; ++i) gp[i] = g[i];
+      if constexpr (TH) Tq = Tn;
     }
     if (!failed) {  // last walk row: own only at a wall, where the stencil is not needed
       const int y = row_of(nrows - 1);
@@ -976,25 +990,6 @@ cudaError_t step_prepare(int precision) {
     }
   }
   return cudaSuccess;
-}
-
-// A step kernel launched as a programmatic dependent of the previous kernel in the stream:
-// the launch and the block set-up overlap that kernel's last blocks; the kernel's first
-// instruction waits for it to complete (griddep_wait).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_dependent(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
-                             Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
 }
 
 cudaError_t launch_step(int precision, int mode, const StepTiling& t, const StepPhys& ph, const StepIO& io,

@@ -1,9 +1,13 @@
 // Inline-PTX helpers shared by the kernels of liblbm (sm_103a): shared-memory addresses,
-// mbarriers with bounded waits, and the tcgen05 tensor-core instructions (TMEM
-// allocation, MMA issue and commit, TMEM loads, and their ordering fences).
+// mbarriers with bounded waits, programmatic dependent launch (device side and the host
+// launch wrapper), and the tcgen05 tensor-core instructions (TMEM allocation, MMA issue
+// and commit, TMEM loads, and their ordering fences).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
+#include <utility>
 
 namespace lbm {
 
@@ -41,6 +45,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host side: launches fn as a programmatic dependent of the previous kernel in `stream`
+// (its launch and block set-up overlap that kernel's last blocks); fn must call
+// griddep_wait() before it touches global memory.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
 }
 
 __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {

@@ -20,15 +20,15 @@ __device__ __forceinline__ f2 make_f2(float a, float b) {
   return r;
 }
 __device__ __forceinline__ float lo(f2 x) {
-  float a, b;
+  float a;
+  [[maybe_unused]] float b;
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
-  (void)b;
   return a;
 }
 __device__ __forceinline__ float hi(f2 x) {
-  float a, b;
+  [[maybe_unused]] float a;
+  float b;
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
-  (void)a;
   return b;
 }
 __device__ __forceinline__ f2 operator+(f2 a, f2 b) {
