@@ -359,9 +359,9 @@ def run_columns(args):
 TH_NX, TH_NY, TH_LIQUID = 512, 2048, 1024
 TH_TBOT, TH_TTOP, TH_GY = 0.95, 0.80, -5e-5
 # per node and step, as launched: fused step 72 B populations + 4 B T; moments pass 36 B
-# populations + 4 B T read, 24 B rho/u written; Heun kernel 4 B T + 24 B rho/u read, 4 B T
-# written (FP32 storage, FP64 rho and u; FP64 storage doubles the population and T terms)
-TH_BYTES_PER_NODE = {"fp32": 76 + 64 + 32, "fp64": 152 + 104 + 40}
+# populations + 4 B T read, 12 B rho/u written; Heun kernel 4 B T + 12 B rho/u read, 4 B T
+# written (FP32 storage, rho and u handed over as floats; FP64 storage doubles every term)
+TH_BYTES_PER_NODE = {"fp32": 76 + 52 + 20, "fp64": 152 + 104 + 40}
 # The heated column goes non-physical: its 1024 vapour rows weigh more than the vapour's
 # saturation pressure can carry at g_y = -5e-5 (scale height of the vapour ~100 rows), so
 # the vapour falls freely and the top empties (max |u| = |g| t) within ~5000 steps. Timed
