@@ -282,24 +282,39 @@ def column_set(n, seed, heights, lbm, inputs):
     return cols, np.concatenate([r.ravel() for r in rhos])
 
 
-def run_to_steady(lbm, cols, rho0, cap, fp32_first):
+TUNE_STEPS = 200  # steps per candidate block size of the batched kernel's autotuner
+
+
+def run_to_steady(lbm, cols, rho0, cap, fp32_first, tuned=None):
     """FP64 alone, or FP32 until each column reaches FP32_TOL or its FP32 rounding floor (no
     1 % gain in FP32_STALL_CHECKS checks) then FP64 from that state, to residual 1e-10
-    (checked every 100 steps). Returns (device seconds, steps, residual, status, batch)."""
+    (checked every 100 steps). Each batch's block size comes from lbm_batch_autotune (its
+    timing runs on a copy of the batch, outside the timed runs); the choices and timings go
+    into `tuned`. Returns (device seconds, steps, residual, status, batch)."""
     _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    tuned = {} if tuned is None else tuned
     if fp32_first:
         b32 = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols, rho0)
+        tuned["fp32"] = lbm.lbm_batch_autotune(b32, TUNE_STEPS)
         lbm.lbm_batch_set_acceleration(b32, ACCEL_CHECKS)
         t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
         b = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
         lbm.lbm_batch_destroy(b32)
+        tuned["fp64_after_fp32"] = lbm.lbm_batch_autotune(b, TUNE_STEPS)
         lbm.lbm_batch_set_acceleration(b, ACCEL_CHECKS)
     else:
         t32 = 0.0
         b = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp64", a=A, b=B, R=R), cols, rho0)
+        tuned["fp64"] = lbm.lbm_batch_autotune(b, TUNE_STEPS)
     t64 = lbm.lbm_batch_run(b, 1e-10, cap, 100)
     st, res, status = lbm.lbm_batch_results(b, len(cols), check=False)
     return t32 + t64, st, res, status, b
+
+
+def tuned_summary(tuned):
+    """{batch: {"threads": kept, "us_per_step": {candidate: us}}} of the autotuner's results."""
+    return {k: {"threads": v[0], "us_per_step": {str(t): round(u, 2) for t, u in v[1].items()}}
+            for k, v in tuned.items()}
 
 
 def run_columns(args):
@@ -319,18 +334,22 @@ def run_columns(args):
     nodes = rho.size
     cap = args.column_max_steps
     out = {}
+    tuned = {}
     p64 = lbm.make_params(4, 8, 0.8 * Tc, "fp64", a=A, b=B, R=R)
     b64 = lbm.lbm_batch_init(p64, cols, rho)
+    tuned["fp64_plain"] = lbm.lbm_batch_autotune(b64, TUNE_STEPS)
     t64 = lbm.lbm_batch_run(b64, 1e-10, cap, 100)
     st64, res64, s64 = lbm.lbm_batch_results(b64, len(cols), check=False)
     lbm.lbm_batch_destroy(b64)
     p32 = lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R)
     b32 = lbm.lbm_batch_init(p32, cols, rho)
+    tuned["fp32"] = lbm.lbm_batch_autotune(b32, TUNE_STEPS)
     lbm.lbm_batch_set_acceleration(b32, ACCEL_CHECKS)
     t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
     st32, _, _ = lbm.lbm_batch_results(b32, len(cols), check=False)
     bc = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
     lbm.lbm_batch_destroy(b32)
+    tuned["fp64_after_fp32"] = lbm.lbm_batch_autotune(bc, TUNE_STEPS)
     lbm.lbm_batch_set_acceleration(bc, ACCEL_CHECKS)
     tpol = lbm.lbm_batch_run(bc, 1e-10, cap, 100)
     stc, resc, sc = lbm.lbm_batch_results(bc, len(cols), check=False)
@@ -350,6 +369,7 @@ def run_columns(args):
                            "converged": int(okc.sum()), "nonphysical": int((sc != 0).sum())},
         "speedup_vs_fp64": t64 / (t32 + tpol),
         "steps_ratio_converged": float(np.sum(stc[both]) / max(1, np.sum(st64[both]))),
+        "block_threads": tuned_summary(tuned),
     }
     print(json.dumps(out), flush=True)
     return 0
@@ -549,12 +569,13 @@ def run_warmstart(args):
     final = {}
     for name, init, fp32_first in (("fp64_tanh", rho0, False), ("fp32_fp64_tanh", rho0, True),
                                    ("fp64_warm", rho_ml, False), ("fp32_fp64_warm", rho_ml, True)):
-        sec, st, res, status, bb = run_to_steady(lbm, cols, init, cap, fp32_first)
+        tuned = {}
+        sec, st, res, status, bb = run_to_steady(lbm, cols, init, cap, fp32_first, tuned)
         final[name] = torch.empty(rho0.size, dtype=torch.float64, device="cuda")
         lbm.lbm_batch_moments(bb, rho=final[name])
         lbm.lbm_batch_destroy(bb)
         runs[name] = dict(seconds=sec + (t_inf if "warm" in name else 0.0), steps=st, ok=(res <= 1e-10) & (status == 0),
-                          nonphysical=int((status != 0).sum()))
+                          nonphysical=int((status != 0).sum()), block_threads=tuned_summary(tuned))
     ok = np.logical_and.reduce([r["ok"] for r in runs.values()])
     def per_column_max(v):
         return np.array([blk.max() for blk in np.split(np.abs(v), np.cumsum(sizes)[:-1])])
@@ -574,7 +595,8 @@ def run_warmstart(args):
     out["config"] = {"workload": f"{len(cols)} held-out seeded 4xH liquid columns, H in {heights}; network trained on "
                                  f"{len(cols_tr)} steady columns of another seed", "max_steps": cap, "check_every": 100}
     out["runs"] = {k: {"seconds": v["seconds"], "converged": int(v["ok"].sum()), "nonphysical": v["nonphysical"],
-                       "steps_all_converged": int(v["steps"][ok].sum())} for k, v in runs.items()}
+                       "steps_all_converged": int(v["steps"][ok].sum()), "block_threads": v["block_threads"]}
+                   for k, v in runs.items()}
     out["columns_converged_in_all_runs"] = int(ok.sum())
     out["warm_start_inference_s"] = t_inf
     out["final_profile_difference_vs_plain_fp64"] = diff

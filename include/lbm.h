@@ -258,6 +258,19 @@ int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_e
  * allocates 6 x 9 x (total nodes) reals once. Not carried over by lbm_batch_convert. */
 int lbm_batch_set_acceleration(lbm_batch* b, int checks);
 
+/* Block size of the batched kernel (a runtime choice, no counterpart in the paper): threads
+ * = 128, 256 (the default) or 512 per CTA; a CTA iterates one column at a time. Carried
+ * over by lbm_batch_convert. LBM_EINVAL for another value. */
+int lbm_batch_set_threads(lbm_batch* b, int threads);
+/* Autotuner of the batched kernel's block size: on a copy of the batch's current state,
+ * every column runs `steps` (>= 1) steps with no residual stop (after a 2-step warm-up) for
+ * each candidate block size, timed with CUDA events on the batch's stream; the fastest is
+ * kept (lbm_batch_set_threads). threads[3] and us[3] (host, may be NULL) receive the
+ * candidates and their microseconds per step of the whole batch. The batch's own state,
+ * step counts and residuals are not touched; the copy needs as much device memory as the
+ * batch. Synchronises. */
+int lbm_batch_autotune(lbm_batch* b, int steps, int* threads, double* us);
+
 /* Per column (host arrays of ncols, any may be NULL): total steps taken, last residual
  * (+inf before the first check), status (LBM_OK or LBM_ENONPHYS). Returns LBM_ENONPHYS if
  * any column is non-physical. Synchronises. */

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <iterator>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -31,8 +32,9 @@
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// threads per column CTA: the candidates of lbm_batch_autotune (256 by default)
+constexpr int kThreadChoices[3] = {128, 256, 512};
+constexpr int kDefaultThreads = 256;
 
 struct BatchCol {
   int ny, form;
@@ -137,18 +139,18 @@ __device__ __forceinline__ double sum9_fp64(const T (&g)[9]) {
 // is reduced over the CTA in FP64 and solved by one thread (Gaussian elimination with
 // partial pivoting). The estimate replaces `cur` only if every node keeps a positive
 // density; returns whether it did. Uniform over the CTA.
-template <typename T>
+template <typename T, int NT>
 __device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* slot0, int tid, int lane, int warp,
                                 const lbm::PhysT<T>& k) {
-  constexpr int NU = kMpeK + 1, NG = NU * (NU + 1) / 2;
-  __shared__ double part[NG][kWarps];
+  constexpr int NU = kMpeK + 1, NG = NU * (NU + 1) / 2, NW = NT / 32;
+  __shared__ double part[NG][NW];
   __shared__ double gam[NU];
   __shared__ int ok_s;
   const size_t slot = size_t(run.slot);
   double G[NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i) G[i] = 0.0;
-  for (int e = tid; e < 9 * N; e += kThreads) {
+  for (int e = tid; e < 9 * N; e += NT) {
     double x[NU + 1], u[NU];
 #pragma unroll
     for (int j = 0; j <= NU; ++j) x[j] = double(slot0[j * slot + e]);
@@ -170,7 +172,7 @@ __device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* sl
     double g[NG];
     for (int i = 0; i < NG; ++i) {
       g[i] = 0.0;
-      for (int w = 0; w < kWarps; ++w) g[i] += part[i][w];
+      for (int w = 0; w < NW; ++w) g[i] += part[i][w];
     }
     auto at = [&](int i, int j) {
       if (i > j) {
@@ -227,7 +229,7 @@ __device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* sl
   if (!ok_s) return false;
   // the estimate, node by node; a non-positive density rejects it
   int bad = 0;
-  for (int n = tid; n < N; n += kThreads) {
+  for (int n = tid; n < N; n += NT) {
     double rho = k.rho_ref;
     T v[9];
 #pragma unroll
@@ -244,18 +246,19 @@ __device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* sl
   }
   if (__syncthreads_or(bad)) {  // back to the last snapshot (x_{kMpeK+1} is the state before)
     const T* last = slot0 + size_t(kMpeK + 1) * slot;
-    for (int e = tid; e < 9 * N; e += kThreads) cur[e] = last[e];
+    for (int e = tid; e < 9 * N; e += NT) cur[e] = last[e];
     __syncthreads();
     return false;
   }
   return true;
 }
 
-template <typename T, int MODE, bool UNIT, bool ACC>
-__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
+template <typename T, int MODE, bool UNIT, bool ACC, int NT>
+__global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double red[2][kWarps];  // mass partials of the state each iteration reads
-  __shared__ double rmax[kWarps];
+  __shared__ double red[2][NW];  // mass partials of the state each iteration reads
+  __shared__ double rmax[NW];
   __shared__ int s_col;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const RunParams run = *a.run;
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
 
     {  // mass of the stored state, for <rho> of the first step
       lbm::Acc<T> acc;
-      for (int n = tid; n < N; n += kThreads) {
+      for (int n = tid; n < N; n += NT) {
         T g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = cur[i * N + n];
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
     // FP64 partials of the stored mass of a state into red[q] (what the next step reads)
     auto remass = [&](const T* st, int q) {
       lbm::Acc<T> acc2;
-      for (int n = tid; n < N; n += kThreads) {
+      for (int n = tid; n < N; n += NT) {
         T g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = st[i * N + n];
@@ -317,12 +320,12 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
     for (; it < iters; ++it) {
       const int p = int(it & 1);
       double msum = 0.0;
-      for (int w2 = 0; w2 < kWarps; ++w2) msum += red[p][w2];  // same order in every thread
+      for (int w2 = 0; w2 < NW; ++w2) msum += red[p][w2];  // same order in every thread
       const T dmean = T(msum / double(N));
       const bool save = MODE == lbm::MODE_STEP && K >= 2 && ((it + 2) % K == 0);
       const bool chk = MODE == lbm::MODE_STEP && K >= 2 && ((it + 1) % K == 0);
       // (A) rho and psi of every node (Eqs. Density, EOS, InteractionPotential)
-      for (int n = tid; n < N; n += kThreads) {
+      for (int n = tid; n < N; n += NT) {
         const int x = n % nx, y = n / nx;
         T g[9];
         pull_col(cur, nx, ny, N, x, y, g);
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
       // OperatorMRT, LiFS)
       lbm::Acc<T> acc;
       double rm = 0.0;
-      for (int n = tid; n < N; n += kThreads) {
+      for (int n = tid; n < N; n += NT) {
         const int x = n % nx, y = n / nx;
         const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
         T g[9];
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
       nxt = t;
       if (chk) {
         double r = 0.0;
-        for (int w2 = 0; w2 < kWarps; ++w2) r = fmax(r, rmax[w2]);
+        for (int w2 = 0; w2 < NW; ++w2) r = fmax(r, rmax[w2]);
         res = r;
         if (!(r > run.tol)) {  // converged (uniform decision)
           ++it;
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
             verify = false;
             if (r > res_before) {
               const T* last = slot_ptr(kMpeK + 1);
-              for (int e = tid; e < 9 * N; e += kThreads) cur[e] = last[e];
+              for (int e = tid; e < 9 * N; e += NT) cur[e] = last[e];
               __syncthreads();
               remass(cur, q);
               skip_cycle = true;
@@ -410,13 +413,13 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
           if (++checks_since >= run.mpe_checks) {
             checks_since = 0;
             T* dst = slot_ptr(nsnap);
-            for (int e = tid; e < 9 * N; e += kThreads) dst[e] = cur[e];
+            for (int e = tid; e < 9 * N; e += NT) dst[e] = cur[e];
             __syncthreads();
             if (++nsnap == kMpeK + 2) {
               nsnap = 0;
               if (skip_cycle) {
                 skip_cycle = false;
-              } else if (mpe_extrapolate<T>(run, N, cur, slot_ptr(0), tid, lane, warp, k)) {
+              } else if (mpe_extrapolate<T, NT>(run, N, cur, slot_ptr(0), tid, lane, warp, k)) {
                 remass(cur, q);
                 verify = true;
                 res_before = r;
@@ -429,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(const BatchArgs a) {
     if (MODE == lbm::MODE_STEP) {
       T* A = static_cast<T*>(a.fA) + 9 * col.node_off;
       if (cur != A)  // the state ends in the second buffer: copy it back
-        for (int e = tid; e < 9 * N; e += kThreads) A[e] = cur[e];
+        for (int e = tid; e < 9 * N; e += NT) A[e] = cur[e];
     }
     const int any = __syncthreads_or(flag);
     if (tid == 0 && MODE == lbm::MODE_STEP) {
@@ -505,7 +508,10 @@ struct lbm_batch {
   size_t smem = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_acc = false;  // the captured launch is the extrapolating kernel
+  int graph_threads = 0;   // and its block size
   int grid_acc = 0;        // its resident grid
+  int threads = kDefaultThreads;  // block size (one CTA per column at a time)
+  int nsm = 0;
   int mpe_checks = 0;      // extrapolation cycle (residual checks per snapshot); 0: off
   void* snap = nullptr;    // kMpeK + 2 snapshot slots of 9 * total_nodes reals
 };
@@ -513,20 +519,26 @@ struct lbm_batch {
 namespace {
 
 template <typename T, int MODE, bool UNIT, bool ACC>
-void* batch_fn() {
-  return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT, ACC>);
+void* batch_fn(int threads) {
+  switch (threads) {
+    case 128: return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT, ACC, 128>);
+    case 512: return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT, ACC, 512>);
+    default: return reinterpret_cast<void*>(&batch_kernel<T, MODE, UNIT, ACC, 256>);
+  }
 }
 
 template <typename T>
-void* pick_typed(int mode, bool unit, bool acc) {
-  if (mode == lbm::MODE_MOMENTS) return batch_fn<T, lbm::MODE_MOMENTS, false, false>();
-  if (acc) return unit ? batch_fn<T, lbm::MODE_STEP, true, true>() : batch_fn<T, lbm::MODE_STEP, false, true>();
-  return unit ? batch_fn<T, lbm::MODE_STEP, true, false>() : batch_fn<T, lbm::MODE_STEP, false, false>();
+void* pick_typed(int mode, bool unit, bool acc, int threads) {
+  if (mode == lbm::MODE_MOMENTS) return batch_fn<T, lbm::MODE_MOMENTS, false, false>(threads);
+  if (acc)
+    return unit ? batch_fn<T, lbm::MODE_STEP, true, true>(threads) : batch_fn<T, lbm::MODE_STEP, false, true>(threads);
+  return unit ? batch_fn<T, lbm::MODE_STEP, true, false>(threads) : batch_fn<T, lbm::MODE_STEP, false, false>(threads);
 }
 
 // the extrapolating kernel only when the batch is set to extrapolate (it holds more registers)
-void* pick_kernel(int precision, int mode, bool unit, bool acc = false) {
-  return precision == LBM_FP32 ? pick_typed<float>(mode, unit, acc) : pick_typed<double>(mode, unit, acc);
+void* pick_kernel(int precision, int mode, bool unit, bool acc, int threads) {
+  return precision == LBM_FP32 ? pick_typed<float>(mode, unit, acc, threads)
+                               : pick_typed<double>(mode, unit, acc, threads);
 }
 
 BatchArgs make_args(const lbm_batch* b) {
@@ -563,9 +575,23 @@ bool accelerated(const lbm_batch* b) { return b->snap != nullptr && b->mpe_check
 
 cudaError_t launch(const lbm_batch* b, int mode, BatchArgs args) {
   const bool acc = mode == lbm::MODE_STEP && accelerated(b);
-  void* fn = pick_kernel(b->p.precision, mode, unit_tau(b->p), acc);
+  void* fn = pick_kernel(b->p.precision, mode, unit_tau(b->p), acc, b->threads);
   void* kargs[] = {&args};
-  return cudaLaunchKernel(fn, dim3(acc ? b->grid_acc : b->grid), dim3(kThreads), kargs, b->smem, b->stream);
+  return cudaLaunchKernel(fn, dim3(acc ? b->grid_acc : b->grid), dim3(b->threads), kargs, b->smem, b->stream);
+}
+
+// persistent grids of the plain and the extrapolating kernel at the batch's block size:
+// resident CTAs on every SM, capped so that the columns in flight keep their two buffers
+// in L2 (about 96 MB)
+void size_grids(lbm_batch* b) {
+  const double avg_bytes = 2.0 * 9.0 * double(b->s) * double(b->total_nodes) / double(b->ncols);
+  const int l2_cap = std::max(b->nsm, int(96.0e6 / avg_bytes));
+  for (bool acc : {false, true}) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, pick_kernel(b->p.precision, lbm::MODE_STEP, unit_tau(b->p), acc, b->threads), b->threads, b->smem);
+    (acc ? b->grid_acc : b->grid) = std::max(1, std::min({b->nsm * std::max(per_sm, 1), l2_cap, b->ncols}));
+  }
 }
 
 void free_batch(lbm_batch* b) {
@@ -699,26 +725,19 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
-  // persistent grid: resident CTAs on every SM, capped so that the columns in flight keep
-  // their two buffers in L2 (about 96 MB)
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
   b->smem = ((size_t(b->nx) * size_t(b->max_ny) * b->s + 15) & ~size_t(15)) + size_t(b->nx) * size_t(b->max_ny) * 8;
-  for (int mode : {lbm::MODE_STEP, lbm::MODE_MOMENTS})
-    for (bool u : {false, true})
-      for (bool acc : {false, true}) {
-        e = cudaFuncSetAttribute(pick_kernel(p->precision, mode, u, acc), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(b->smem));
-        if (e != cudaSuccess) return fail(LBM_ECUDA, "batch kernel shared memory limit");
-      }
-  const double avg_bytes = 2.0 * 9.0 * double(b->s) * double(off) / double(ncols);
-  const int l2_cap = std::max(nsm, int(96.0e6 / avg_bytes));
-  for (bool acc : {false, true}) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(p->precision, lbm::MODE_STEP, unit_tau(*p), acc),
-                                                  kThreads, b->smem);
-    (acc ? b->grid_acc : b->grid) = std::max(1, std::min({nsm * std::max(per_sm, 1), l2_cap, ncols}));
-  }
+  for (int nt : kThreadChoices)
+    for (int mode : {lbm::MODE_STEP, lbm::MODE_MOMENTS})
+      for (bool u : {false, true})
+        for (bool acc : {false, true}) {
+          e = cudaFuncSetAttribute(pick_kernel(p->precision, mode, u, acc, nt),
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem));
+          if (e != cudaSuccess) return fail(LBM_ECUDA, "batch kernel shared memory limit");
+        }
+  size_grids(b);
   *out = b;
   return LBM_OK;
 }
@@ -738,6 +757,60 @@ int lbm_batch_set_acceleration(lbm_batch* b, int checks) {
   return LBM_OK;
 }
 
+int lbm_batch_set_threads(lbm_batch* b, int threads) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  if (std::find(std::begin(kThreadChoices), std::end(kThreadChoices), threads) == std::end(kThreadChoices))
+    return bfail(LBM_EINVAL, "threads must be 128, 256 or 512");
+  b->threads = threads;
+  size_grids(b);
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int steps, int* threads, double* us) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  if (steps < 1) return bfail(LBM_EINVAL, "steps must be >= 1");
+  // a copy of the current state, so that b's state and results stay as they are
+  lbm_batch* t = nullptr;
+  int rc = lbm_batch_convert(b, b->p.precision, &t);
+  if (rc) return rc;
+  t->mpe_checks = b->mpe_checks;
+  t->snap = nullptr;  // timed without extrapolation snapshots: the plain kernel's block size
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double best_us = 0.0;
+  int best = b->threads;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    t->threads = kThreadChoices[i];
+    size_grids(t);
+    float ms = 0.f;
+    // every column `steps` steps (tol < 0: no column stops early), after a 2-step warm-up
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+      const RunParams rp{-1.0, pass == 0 ? 2LL : (long long)steps, 100, 0, 0, nullptr, 9 * t->total_nodes};
+      e = cudaMemcpyAsync(t->run_d, &rp, sizeof(rp), cudaMemcpyHostToDevice, t->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(t->counter, 0, sizeof(int), t->stream);
+      if (e == cudaSuccess && pass == 1) e = cudaEventRecord(e0, t->stream);
+      if (e == cudaSuccess) e = launch(t, lbm::MODE_STEP, make_args(t));
+      if (e == cudaSuccess && pass == 1) e = cudaEventRecord(e1, t->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    const double v = 1e3 * double(ms) / steps;
+    if (threads) threads[i] = kThreadChoices[i];
+    if (us) us[i] = v;
+    if (i == 0 || v < best_us) {
+      best_us = v;
+      best = kThreadChoices[i];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  lbm_batch_destroy(t);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  return lbm_batch_set_threads(b, best);
+}
+
 int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, double* seconds) {
   return lbm_batch_run_stall(b, tol, max_steps, check_every, 0, seconds);
 }
@@ -750,7 +823,8 @@ int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_e
   RunParams rp{tol, (long long)max_steps, check_every, stall_checks, b->snap ? b->mpe_checks : 0, b->snap,
                9 * b->total_nodes};
   cudaError_t e = cudaMemcpyAsync(b->run_d, &rp, sizeof(rp), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess && b->graph && b->graph_acc != accelerated(b)) {  // the kernel choice changed
+  if (e == cudaSuccess && b->graph && (b->graph_acc != accelerated(b) || b->graph_threads != b->threads)) {
+    // the kernel choice changed
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
   }
@@ -764,7 +838,10 @@ int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_e
       if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
-    if (e == cudaSuccess) b->graph_acc = accelerated(b);
+    if (e == cudaSuccess) {
+      b->graph_acc = accelerated(b);
+      b->graph_threads = b->threads;
+    }
     if (g) cudaGraphDestroy(g);
   }
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -879,6 +956,8 @@ int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out) {
   if (rc == LBM_OK) rc = lbm_batch_init(&p, cols.data(), src->ncols, rho0.data(), LBM_HOST, src->own_stream ? nullptr : src->stream, out);
   if (rc == LBM_OK) {
     lbm_batch* b = *out;
+    b->threads = src->threads;
+    size_grids(b);
     for (int c = 0; c < b->ncols; ++c) b->cols[c].rho_ref = precision == LBM_FP64 && std::isnan(src->p.rho_ref) ? 0.0 : src->cols[c].rho_ref;
     cudaError_t e = cudaMemcpyAsync(b->cols_d, b->cols.data(), sizeof(BatchCol) * b->ncols, cudaMemcpyHostToDevice, b->stream);
     const int g = std::min(b->ncols, 4096);

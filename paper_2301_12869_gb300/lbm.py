@@ -42,6 +42,7 @@ EXPORTS = (
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
     "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
     "lbm_batch_convert", "lbm_batch_destroy",
+    "lbm_batch_set_threads", "lbm_batch_autotune",
     "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
     "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_gemm_enqueue",
     "lbm_mlp_destroy",
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH):
         "lbm_batch_run": (i32, [vp, d, i64, i32, P(d)]),
         "lbm_batch_run_stall": (i32, [vp, d, i64, i32, i32, P(d)]),
         "lbm_batch_set_acceleration": (i32, [vp, i32]),
+        "lbm_batch_set_threads": (i32, [vp, i32]),
+        "lbm_batch_autotune": (i32, [vp, i32, vp, vp]),
         "lbm_batch_results": (i32, [vp, vp, vp, vp]),
         "lbm_batch_moments": (i32, [vp, vp, vp, vp, i32]),
         "lbm_batch_get_state": (i32, [vp, vp, i32]),
@@ -326,6 +329,43 @@ def lbm_batch_run_stall(b, tol, max_steps, check_every=100, stall_checks=10):
 def lbm_batch_set_acceleration(b, checks):
     """Extrapolation every `checks` residual checks (0: off) for later runs of this batch."""
     _check(load().lbm_batch_set_acceleration(b, int(checks)))
+
+
+def lbm_batch_set_threads(b, threads):
+    """Block size of the batched kernel: 128, 256 (default) or 512 threads per column CTA."""
+    _check(load().lbm_batch_set_threads(b, int(threads)))
+
+
+def lbm_batch_autotune(b, steps=200):
+    """Times each block size on a copy of the batch's state and keeps the fastest; returns
+    (threads kept, {threads: microseconds per step of the whole batch})."""
+    th = (ctypes.c_int * 3)()
+    us = (ctypes.c_double * 3)()
+    _check(load().lbm_batch_autotune(b, int(steps), th, us))
+    times = {int(th[i]): float(us[i]) for i in range(3)}
+    return min(times, key=times.get), times
+
+
+def batch_tuned_threads(b, cache_path, key, steps=200):
+    """lbm_batch_autotune with its result cached in a JSON file: the block size stored under
+    `key` (a string naming the GPU and the batch's shape) is applied without timing; else the
+    batch is tuned and the choice and its timings are stored. Returns the block size."""
+    import json
+
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        lbm_batch_set_threads(b, cache[key]["threads"])
+        return int(cache[key]["threads"])
+    best, times = lbm_batch_autotune(b, steps)
+    cache[key] = {"threads": best, "us_per_step": {str(k): v for k, v in times.items()}, "steps": int(steps)}
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return best
 
 
 def lbm_batch_results(b, ncols, check=True):

@@ -220,3 +220,53 @@ def test_extrapolation_reaches_the_same_steady_states_in_fewer_steps():
     off = np.cumsum([0] + [NX * c["ny"] for c in cols])
     for c in np.nonzero(ok)[0]:
         assert np.max(np.abs(r1[off[c]:off[c + 1]] - r0[off[c]:off[c + 1]])) <= 1e-5, c
+
+
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-14), ("fp32", 1e-6 * math.sqrt(40) + 1e-6)])
+def test_every_block_size_matches_oracle(precision, tol):
+    """128, 256 and 512 threads per column CTA: the oracle's states after 40 steps (the
+    block size changes only the order of the FP64 mass partials)."""
+    cols, rhos = make_columns(10, seed=21, heights=(8, 24, 64, 150))
+    p = batch_params(precision)
+    total = sum(9 * NX * c["ny"] for c in cols)
+    for threads in (128, 256, 512):
+        b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+        try:
+            lbm.lbm_batch_set_threads(b, threads)
+            f0 = np.empty(total)
+            lbm.lbm_batch_get_state(b, f0)
+            lbm.lbm_batch_run(b, 0.0, 40, check_every=1000)
+            f1 = np.empty(total)
+            lbm.lbm_batch_get_state(b, f1)
+            for col, g0, g1 in zip(cols, split_state(f0, cols), split_state(f1, cols)):
+                want = olbm.run(g0, oracle_column(col, p), 40)
+                assert np.max(np.abs(g1 - want)) <= tol * (40 if precision == "fp64" else 1), (threads, col)
+        finally:
+            lbm.lbm_batch_destroy(b)
+
+
+def test_autotune_keeps_the_fastest_block_size_and_leaves_the_state():
+    cols, rhos = make_columns(64, seed=22, heights=(32, 64, 96))
+    b = lbm.lbm_batch_init(batch_params("fp32"), cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_run(b, 0.0, 30, check_every=10)
+        total = sum(9 * NX * c["ny"] for c in cols)
+        f0 = np.empty(total)
+        lbm.lbm_batch_get_state(b, f0)
+        st0, res0, _ = lbm.lbm_batch_results(b, len(cols))
+        best, times = lbm.lbm_batch_autotune(b, steps=50)
+        assert sorted(times) == [128, 256, 512] and all(t > 0 for t in times.values())
+        assert best == min(times, key=times.get)
+        f1 = np.empty(total)
+        lbm.lbm_batch_get_state(b, f1)
+        st1, res1, _ = lbm.lbm_batch_results(b, len(cols))
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(st1, st0)
+        np.testing.assert_array_equal(res1, res0)
+        # the tuned batch still runs (the graph is recaptured for the kept block size)
+        lbm.lbm_batch_run(b, 0.0, 10, check_every=5)
+        assert np.all(lbm.lbm_batch_results(b, len(cols))[0] == 40)
+        with pytest.raises(lbm.LbmError, match="128, 256 or 512"):
+            lbm.lbm_batch_set_threads(b, 64)
+    finally:
+        lbm.lbm_batch_destroy(b)
