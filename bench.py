@@ -323,7 +323,8 @@ def run_columns(args):
     in [1e-6, 1e-4], either gravity form, liquid fraction ~ U[0.3, 0.7]) restricted to the
     heights in --column-heights, each run to max |rho_t - rho_(t-1)| <= 1e-10 (checked every
     100 steps): plain FP64 against FP32 down to its rounding floor (~1e-8; the residual is
-    evaluated in FP64) followed by FP64 from that state."""
+    evaluated in FP64) followed, from that state, by FP64 or by double-float (FP32-pair)
+    arithmetic. `value` is the FP32 + double-float time."""
     import numpy as np
 
     from paper_2301_12869_gb300 import inputs, lbm
@@ -348,26 +349,48 @@ def run_columns(args):
     t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
     st32, _, _ = lbm.lbm_batch_results(b32, len(cols), check=False)
     bc = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
+    bd = lbm.lbm_batch_convert(b32, lbm.LBM_DOUBLE_FLOAT)
     lbm.lbm_batch_destroy(b32)
     tuned["fp64_after_fp32"] = lbm.lbm_batch_autotune(bc, TUNE_STEPS)
     lbm.lbm_batch_set_acceleration(bc, ACCEL_CHECKS)
     tpol = lbm.lbm_batch_run(bc, 1e-10, cap, 100)
     stc, resc, sc = lbm.lbm_batch_results(bc, len(cols), check=False)
+    rc_ = np.empty(nodes)
+    lbm.lbm_batch_moments(bc, rho=rc_)
     lbm.lbm_batch_destroy(bc)
+    # the same FP32 state finished in double-float (FP32-pair) arithmetic instead of FP64
+    tuned["dd_after_fp32"] = lbm.lbm_batch_autotune(bd, TUNE_STEPS)
+    lbm.lbm_batch_set_acceleration(bd, ACCEL_CHECKS)
+    tdd = lbm.lbm_batch_run(bd, 1e-10, cap, 100)
+    std_, resd, sd = lbm.lbm_batch_results(bd, len(cols), check=False)
+    rd_ = np.empty(nodes)
+    lbm.lbm_batch_moments(bd, rho=rd_)
+    lbm.lbm_batch_destroy(bd)
     ok64 = (res64 <= 1e-10) & (s64 == 0)
     okc = (resc <= 1e-10) & (sc == 0)
+    okd = (resd <= 1e-10) & (sd == 0)
     both = ok64 & okc
+    offs = np.cumsum([0] + [4 * c["ny"] for c in cols])
+    dd_vs_fp64 = np.array([np.max(np.abs(rd_[offs[i]:offs[i + 1]] - rc_[offs[i]:offs[i + 1]]))
+                           for i in np.nonzero(okc & okd)[0]])
     out = {
         "metric": "time to steady state (residual 1e-10), batched columns", "unit": "s",
-        "value": t32 + tpol, "higher_is_better": False, "impl": "gb300", "n_gpus": 1,
+        "value": t32 + tdd, "higher_is_better": False, "impl": "gb300", "n_gpus": 1,
         "config": {"workload": f"{len(cols)} seeded 4xH liquid columns, H in {heights}", "nodes": nodes,
                    "max_steps": cap, "check_every": 100, "fp32_tol": FP32_TOL, "fp32_stall_checks": FP32_STALL_CHECKS,
                    "accel_checks": ACCEL_CHECKS},
         "fp64_plain": {"seconds": t64, "converged": int(ok64.sum()), "nonphysical": int((s64 != 0).sum()),
                        "node_steps_per_s": float(np.sum(st64 * [4 * c["ny"] for c in cols]) / t64)},
         "fp32_then_fp64": {"seconds": t32 + tpol, "fp32_seconds": t32, "fp64_seconds": tpol,
-                           "converged": int(okc.sum()), "nonphysical": int((sc != 0).sum())},
-        "speedup_vs_fp64": t64 / (t32 + tpol),
+                           "converged": int(okc.sum()), "nonphysical": int((sc != 0).sum()),
+                           "speedup_vs_fp64": t64 / (t32 + tpol)},
+        "fp32_then_double_float": {"seconds": t32 + tdd, "fp32_seconds": t32, "double_float_seconds": tdd,
+                                   "converged": int(okd.sum()), "nonphysical": int((sd != 0).sum()),
+                                   "speedup_vs_fp64": t64 / (t32 + tdd),
+                                   "max_rho_difference_vs_fp32_then_fp64": {
+                                       "median": float(np.median(dd_vs_fp64)) if dd_vs_fp64.size else None,
+                                       "max": float(np.max(dd_vs_fp64)) if dd_vs_fp64.size else None}},
+        "speedup_vs_fp64": t64 / (t32 + tdd),
         "steps_ratio_converged": float(np.sum(stc[both]) / max(1, np.sum(st64[both]))),
         "block_threads": tuned_summary(tuned),
     }

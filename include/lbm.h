@@ -53,7 +53,11 @@ enum {
 };
 
 /* ---- enumerations */
-enum { LBM_FP64 = 0, LBM_FP32 = 1 };                              /* storage and arithmetic */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_DOUBLE_FLOAT = 2 };        /* storage and arithmetic */
+/* LBM_DOUBLE_FLOAT (batches only: lbm_batch_init, lbm_batch_convert): every real is the
+ * unevaluated sum hi + lo of two FP32 numbers (8 bytes, about 48 significant bits) and all
+ * arithmetic runs on FP32 instructions - FP64-class accuracy (~2^-46 relative per
+ * operation) at GB300's FP32 rate; the residual is evaluated in FP64 as for FP64 batches. */
 enum { LBM_GRAVITY_RHO_G = 1, LBM_GRAVITY_RHO_MINUS_MEAN_G = 2 }; /* Eq. Gravity_1 / _2 */
 enum { LBM_HOST = 0, LBM_DEVICE = 1 };                            /* where a buffer lives */
 /* walls below row 0 and above row ny-1 */

@@ -17,6 +17,7 @@
 // run parameters live in device memory so the graph is reused by every run.
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_dd.cuh"
 #include "lbm_physics.cuh"
 
 #include <cuda_runtime.h>
@@ -74,21 +75,21 @@ struct BatchArgs {
 template <typename T>
 __device__ lbm::PhysT<T> column_phys(const BatchArgs& a, const BatchCol& c) {
   lbm::PhysT<T> k;
-  k.rho_ref = T(c.rho_ref);
-  k.RT = T(c.RT);
-  k.R = T(0.0);  // unused: batched columns are isothermal
-  k.a = T(a.a);
-  k.b4 = T(a.b / 4.0);
-  k.twoOverG = T(2.0 / a.G);
-  k.negG = T(-a.G);
-  k.G2 = T(a.G * a.G);
-  k.s_e = T(a.s_e); k.s_vs = T(a.s_vs); k.s_j = T(a.s_j); k.s_q = T(a.s_q); k.s_nu = T(a.s_nu);
-  k.h_e = T(1.0 - 0.5 * a.s_e); k.h_vs = T(1.0 - 0.5 * a.s_vs); k.h_j = T(1.0 - 0.5 * a.s_j);
-  k.h_q = T(1.0 - 0.5 * a.s_q); k.h_nu = T(1.0 - 0.5 * a.s_nu);
-  k.sig_e = T(a.sig_e);
-  k.nsig_vs = T(-a.sig_vs);
-  k.gx = T(c.gx);
-  k.gy = T(c.gy);
+  k.rho_ref = lbm::from_double<T>(c.rho_ref);
+  k.RT = lbm::from_double<T>(c.RT);
+  k.R = lbm::from_double<T>(0.0);  // unused: batched columns are isothermal
+  k.a = lbm::from_double<T>(a.a);
+  k.b4 = lbm::from_double<T>(a.b / 4.0);
+  k.twoOverG = lbm::from_double<T>(2.0 / a.G);
+  k.negG = lbm::from_double<T>(-a.G);
+  k.G2 = lbm::from_double<T>(a.G * a.G);
+  k.s_e = lbm::from_double<T>(a.s_e); k.s_vs = lbm::from_double<T>(a.s_vs); k.s_j = lbm::from_double<T>(a.s_j); k.s_q = lbm::from_double<T>(a.s_q); k.s_nu = lbm::from_double<T>(a.s_nu);
+  k.h_e = lbm::from_double<T>(1.0 - 0.5 * a.s_e); k.h_vs = lbm::from_double<T>(1.0 - 0.5 * a.s_vs); k.h_j = lbm::from_double<T>(1.0 - 0.5 * a.s_j);
+  k.h_q = lbm::from_double<T>(1.0 - 0.5 * a.s_q); k.h_nu = lbm::from_double<T>(1.0 - 0.5 * a.s_nu);
+  k.sig_e = lbm::from_double<T>(a.sig_e);
+  k.nsig_vs = lbm::from_double<T>(-a.sig_vs);
+  k.gx = lbm::from_double<T>(c.gx);
+  k.gy = lbm::from_double<T>(c.gy);
   k.form = c.form;
   return k;
 }
@@ -126,7 +127,7 @@ template <typename T>
 __device__ __forceinline__ double sum9_fp64(const T (&g)[9]) {
   double s = 0.0;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) s += double(g[i]);
+  for (int i = 0; i < 9; ++i) s += lbm::hsum(g[i]);
   return s;
 }
 
@@ -153,7 +154,7 @@ __device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* sl
   for (int e = tid; e < 9 * N; e += NT) {
     double x[NU + 1], u[NU];
 #pragma unroll
-    for (int j = 0; j <= NU; ++j) x[j] = double(slot0[j * slot + e]);
+    for (int j = 0; j <= NU; ++j) x[j] = lbm::hsum(slot0[j * slot + e]);
 #pragma unroll
     for (int j = 0; j < NU; ++j) u[j] = x[j + 1] - x[j];
     int m = 0;
@@ -230,14 +231,14 @@ __device__ bool mpe_extrapolate(const RunParams& run, int N, T* cur, const T* sl
   // the estimate, node by node; a non-positive density rejects it
   int bad = 0;
   for (int n = tid; n < N; n += NT) {
-    double rho = k.rho_ref;
+    double rho = lbm::hsum(k.rho_ref);
     T v[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < NU; ++j) acc += gam[j] * double(slot0[j * slot + size_t(i) * N + n]);
-      v[i] = T(acc);
+      for (int j = 0; j < NU; ++j) acc += gam[j] * lbm::hsum(slot0[j * slot + size_t(i) * N + n]);
+      v[i] = lbm::from_double<T>(acc);
       rho += acc;
     }
     if (!(rho > 0.0)) bad = 1;
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
       const int p = int(it & 1);
       double msum = 0.0;
       for (int w2 = 0; w2 < NW; ++w2) msum += red[p][w2];  // same order in every thread
-      const T dmean = T(msum / double(N));
+      const T dmean = lbm::from_double<T>(msum / double(N));
       const bool save = MODE == lbm::MODE_STEP && K >= 2 && ((it + 2) % K == 0);
       const bool chk = MODE == lbm::MODE_STEP && K >= 2 && ((it + 1) % K == 0);
       // (A) rho and psi of every node (Eqs. Density, EOS, InteractionPotential)
@@ -343,15 +344,15 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
         const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
         T g[9];
         pull_col(cur, nx, ny, N, x, y, g);
-        T Sx = T(0), Sy = T(0);
+        T Sx = lbm::cst<T>(0.0), Sy = lbm::cst<T>(0.0);
         if (y > 0 && y < ny - 1) {  // stencil w(1) = 1/3, w(2) = 1/12; zero on the wall rows
           const T* pc = psi_s + y * nx;
           const T* pn = pc + nx;
           const T* ps = pc - nx;
           const T E = pc[xr], Wt = pc[xl], Nn = pn[x], Ss = ps[x];
           const T NE = pn[xr], NW = pn[xl], SE = ps[xr], SWt = ps[xl];
-          Sx = lbm::fmadd(T(1.0 / 3.0), E - Wt, T(1.0 / 12.0) * ((NE - NW) + (SE - SWt)));
-          Sy = lbm::fmadd(T(1.0 / 3.0), Nn - Ss, T(1.0 / 12.0) * ((NE + NW) - (SE + SWt)));
+          Sx = lbm::fmadd(lbm::cst<T>(1.0 / 3.0), E - Wt, lbm::cst<T>(1.0 / 12.0) * ((NE - NW) + (SE - SWt)));
+          Sy = lbm::fmadd(lbm::cst<T>(1.0 / 3.0), Nn - Ss, lbm::cst<T>(1.0 / 12.0) * ((NE + NW) - (SE + SWt)));
         }
         T o[9], rho, ux, uy;
         lbm::collide_node<T, UNIT>(g, psi_s[n], Sx, Sy, dmean, k, o, rho, ux, uy, flag);
@@ -362,9 +363,9 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
           if (chk) rm = fmax(rm, fabs(sum9_fp64(g) - rho_prev[n]));
         } else {
           const long long idx = col.node_off + n;
-          if (a.rho_out) a.rho_out[idx] = double(rho);
-          if (a.ux_out) a.ux_out[idx] = double(ux);
-          if (a.uy_out) a.uy_out[idx] = double(uy);
+          if (a.rho_out) a.rho_out[idx] = lbm::hsum(rho);
+          if (a.ux_out) a.ux_out[idx] = lbm::hsum(ux);
+          if (a.uy_out) a.uy_out[idx] = lbm::hsum(uy);
         }
       }
       if (MODE != lbm::MODE_STEP) break;
@@ -454,7 +455,7 @@ __global__ void batch_init_kernel(const BatchCol* cols, int ncols, int nx, const
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
       const double d = r[n] - col.rho_ref;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) fc[i * N + n] = T(lbm::w_of(i) * d);
+      for (int i = 0; i < 9; ++i) fc[i * N + n] = lbm::from_double<T>(lbm::w_of(i) * d);
     }
   }
 }
@@ -470,9 +471,9 @@ __global__ void batch_state_kernel(const BatchCol* cols, int ncols, int nx, T* f
     for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
       const double w = lbm::w_of(e / N) * col.rho_ref;
       if (to_double)
-        oc[e] = double(fc[e]) + w;
+        oc[e] = lbm::hsum(fc[e]) + w;
       else
-        fc[e] = T(oc[e] - w);
+        fc[e] = lbm::from_double<T>(oc[e] - w);
     }
   }
 }
@@ -537,9 +538,33 @@ void* pick_typed(int mode, bool unit, bool acc, int threads) {
 
 // the extrapolating kernel only when the batch is set to extrapolate (it holds more registers)
 void* pick_kernel(int precision, int mode, bool unit, bool acc, int threads) {
-  return precision == LBM_FP32 ? pick_typed<float>(mode, unit, acc, threads)
-                               : pick_typed<double>(mode, unit, acc, threads);
+  if (precision == LBM_FP32) return pick_typed<float>(mode, unit, acc, threads);
+  if (precision == LBM_DOUBLE_FLOAT) return pick_typed<lbm::dd>(mode, unit, acc, threads);
+  return pick_typed<double>(mode, unit, acc, threads);
 }
+
+// one kernel launch over the batch's state in its storage type
+template <template <typename> class K, typename... Args>
+void launch_typed(int precision, int grid, cudaStream_t s, void* f, Args... args) {
+  if (precision == LBM_FP32)
+    K<float>::launch(grid, s, static_cast<float*>(f), args...);
+  else if (precision == LBM_DOUBLE_FLOAT)
+    K<lbm::dd>::launch(grid, s, static_cast<lbm::dd*>(f), args...);
+  else
+    K<double>::launch(grid, s, static_cast<double*>(f), args...);
+}
+template <typename T>
+struct InitLaunch {
+  static void launch(int grid, cudaStream_t s, T* f, const BatchCol* cols, int ncols, int nx, const double* rho0) {
+    batch_init_kernel<T><<<grid, 256, 0, s>>>(cols, ncols, nx, rho0, f);
+  }
+};
+template <typename T>
+struct StateLaunch {
+  static void launch(int grid, cudaStream_t s, T* f, const BatchCol* cols, int ncols, int nx, double* out, bool to_double) {
+    batch_state_kernel<T><<<grid, 256, 0, s>>>(cols, ncols, nx, f, out, to_double);
+  }
+};
 
 BatchArgs make_args(const lbm_batch* b) {
   BatchArgs a{};
@@ -617,6 +642,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   q.ny = cols[0].ny;
   q.T = cols[0].T;
   q.gravity_form = cols[0].gravity_form;
+  if (q.precision == LBM_DOUBLE_FLOAT) q.precision = LBM_FP64;  // batches only; validated like FP64
   char err[512];
   int rc = lbm::validate_params(&q, err);
   if (rc) return bfail(rc, err);
@@ -661,7 +687,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   // deviation reference per column: the mean of its rho0 in FP32, 0 in FP64 (or p->rho_ref)
   std::vector<double> rho_h;
   const double* rho_src = rho0;
-  if (rho0_where == LBM_DEVICE && p->precision == LBM_FP32 && std::isnan(p->rho_ref)) {
+  if (rho0_where == LBM_DEVICE && p->precision != LBM_FP64 && std::isnan(p->rho_ref)) {
     rho_h.resize(size_t(off));
     if (cudaMemcpy(rho_h.data(), rho0, size_t(off) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(LBM_ECUDA, "copy of rho0");
@@ -671,7 +697,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
     BatchCol& bc = b->cols[c];
     if (!std::isnan(p->rho_ref)) {
       bc.rho_ref = p->rho_ref;
-    } else if (p->precision == LBM_FP32) {
+    } else if (p->precision != LBM_FP64) {
       const long long n = (long long)p->nx * bc.ny;
       double s = 0.0;
       for (long long i = 0; i < n; ++i) s += rho_src[bc.node_off + i];
@@ -717,10 +743,8 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
     rho_d = static_cast<double*>(b->fB);
   }
   if (e == cudaSuccess && rho_d) {
-    if (p->precision == LBM_FP32)
-      batch_init_kernel<float><<<std::min(ncols, 4096), 256, 0, b->stream>>>(b->cols_d, ncols, b->nx, rho_d, (float*)b->fA);
-    else
-      batch_init_kernel<double><<<std::min(ncols, 4096), 256, 0, b->stream>>>(b->cols_d, ncols, b->nx, rho_d, (double*)b->fA);
+    launch_typed<InitLaunch>(p->precision, std::min(ncols, 4096), b->stream, b->fA, (const BatchCol*)b->cols_d, ncols,
+                             b->nx, (const double*)rho_d);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -916,10 +940,8 @@ int lbm_batch_get_state(lbm_batch* b, double* f, int where) {
   if (where == LBM_HOST) e = cudaMalloc(&dst, bytes);
   const int g = std::min(b->ncols, 4096);
   if (e == cudaSuccess) {
-    if (b->p.precision == LBM_FP32)
-      batch_state_kernel<float><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (float*)b->fA, dst, true);
-    else
-      batch_state_kernel<double><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (double*)b->fA, dst, true);
+    launch_typed<StateLaunch>(b->p.precision, g, b->stream, b->fA, (const BatchCol*)b->cols_d, b->ncols, b->nx, dst,
+                              true);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && where == LBM_HOST) e = cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, b->stream);
@@ -930,7 +952,8 @@ int lbm_batch_get_state(lbm_batch* b, double* f, int where) {
 }
 
 int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out) {
-  if (!src || !out || (precision != LBM_FP32 && precision != LBM_FP64)) return bfail(LBM_EINVAL, "bad arguments");
+  if (!src || !out || (precision != LBM_FP32 && precision != LBM_FP64 && precision != LBM_DOUBLE_FLOAT))
+    return bfail(LBM_EINVAL, "bad arguments");
   *out = nullptr;
   // the new batch starts from src's state: absolute populations through a device buffer
   const size_t n9 = size_t(src->total_nodes) * 9;
@@ -962,10 +985,8 @@ int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out) {
     cudaError_t e = cudaMemcpyAsync(b->cols_d, b->cols.data(), sizeof(BatchCol) * b->ncols, cudaMemcpyHostToDevice, b->stream);
     const int g = std::min(b->ncols, 4096);
     if (e == cudaSuccess) {
-      if (precision == LBM_FP32)
-        batch_state_kernel<float><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (float*)b->fA, abs_d, false);
-      else
-        batch_state_kernel<double><<<g, 256, 0, b->stream>>>(b->cols_d, b->ncols, b->nx, (double*)b->fA, abs_d, false);
+      launch_typed<StateLaunch>(precision, g, b->stream, b->fA, (const BatchCol*)b->cols_d, b->ncols, b->nx, abs_d,
+                                false);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->steps_d, src->steps_d, sizeof(long long) * b->ncols, cudaMemcpyDeviceToDevice, b->stream);

@@ -127,6 +127,18 @@ __device__ __forceinline__ bool nonpositive(double x) { return !(x > 0.0); }
 __device__ __forceinline__ bool nonpositive(float x) { return !(x > 0.f); }
 __device__ __forceinline__ bool nonpositive(f2 x) { return !(lo(x) > 0.f) || !(hi(x) > 0.f); }
 
+// a value of type V from a double (one component)
+template <typename V>
+__host__ __device__ V from_double(double x);
+template <>
+__host__ __device__ inline float from_double<float>(double x) {
+  return float(x);
+}
+template <>
+__host__ __device__ inline double from_double<double>(double x) {
+  return x;
+}
+
 // sum of the components in FP64
 __device__ __forceinline__ double hsum(double x) { return x; }
 __device__ __forceinline__ double hsum(float x) { return double(x); }

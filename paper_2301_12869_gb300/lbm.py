@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 
 # ---- constants of include/lbm.h
 LBM_OK, LBM_EINVAL, LBM_ECUDA, LBM_ENONPHYS, LBM_ETIMEOUT, LBM_ENOMEM = 0, -1, -2, -3, -4, -5
-LBM_FP64, LBM_FP32 = 0, 1
+LBM_FP64, LBM_FP32, LBM_DOUBLE_FLOAT = 0, 1, 2
 LBM_GRAVITY_RHO_G, LBM_GRAVITY_RHO_MINUS_MEAN_G = 1, 2
 LBM_HOST, LBM_DEVICE = 0, 1
 LBM_WALL_BOUNCE_BACK, LBM_WALL_ZOU_HE = 0, 1
@@ -405,7 +405,9 @@ def make_params(nx, ny, T, precision="fp64", **kw):
     ``form`` is accepted for ``gravity_form`` and ``g`` for (gx, gy))."""
     p = lbm_params_default()
     p.nx, p.ny, p.T = int(nx), int(ny), float(T)
-    p.precision = LBM_FP32 if str(precision).lower() in ("fp32", "float32", "1") else LBM_FP64
+    prec = str(precision).lower()
+    p.precision = (LBM_FP32 if prec in ("fp32", "float32", "1")
+                   else LBM_DOUBLE_FLOAT if prec in ("dd", "double_float", "2") else LBM_FP64)
     if "form" in kw:
         p.gravity_form = int(kw.pop("form"))
     if "g" in kw:
