@@ -287,8 +287,8 @@ TUNE_STEPS = 200  # steps per candidate block size of the batched kernel's autot
 
 def run_to_steady(lbm, cols, rho0, cap, fp32_first, tuned=None):
     """FP64 alone, or FP32 until each column reaches FP32_TOL or its FP32 rounding floor (no
-    1 % gain in FP32_STALL_CHECKS checks) then FP64 from that state, to residual 1e-10
-    (checked every 100 steps). Each batch's block size comes from lbm_batch_autotune (its
+    1 % gain in FP32_STALL_CHECKS checks) then double-float (FP32-pair) arithmetic from that
+    state, to residual 1e-10 (checked every 100 steps). Each batch's block size comes from lbm_batch_autotune (its
     timing runs on a copy of the batch, outside the timed runs); the choices and timings go
     into `tuned`. Returns (device seconds, steps, residual, status, batch)."""
     _, Tc, _ = lbm.lbm_critical_point(A, B, R)
@@ -298,9 +298,9 @@ def run_to_steady(lbm, cols, rho0, cap, fp32_first, tuned=None):
         tuned["fp32"] = lbm.lbm_batch_autotune(b32, TUNE_STEPS)
         lbm.lbm_batch_set_acceleration(b32, ACCEL_CHECKS)
         t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
-        b = lbm.lbm_batch_convert(b32, lbm.LBM_FP64)
+        b = lbm.lbm_batch_convert(b32, lbm.LBM_DOUBLE_FLOAT)
         lbm.lbm_batch_destroy(b32)
-        tuned["fp64_after_fp32"] = lbm.lbm_batch_autotune(b, TUNE_STEPS)
+        tuned["dd_after_fp32"] = lbm.lbm_batch_autotune(b, TUNE_STEPS)
         lbm.lbm_batch_set_acceleration(b, ACCEL_CHECKS)
     else:
         t32 = 0.0
@@ -548,7 +548,7 @@ def run_warmstart(args):
     heights = tuple(int(h) for h in args.column_heights.split(","))
     rho_c, Tc, _ = lbm.lbm_critical_point(A, B, R)
     cap = args.column_max_steps
-    out = {"metric": "time to steady state (residual 1e-10), batched columns, FP32 + warm start vs plain FP64",
+    out = {"metric": "time to steady state (residual 1e-10), batched columns, FP32 (+ double-float finish) + warm start vs plain FP64",
            "unit": "s", "higher_is_better": False, "impl": "gb300", "n_gpus": 1}
     # ---- training data: steady profiles of the method (FP32 to its rounding floor)
     cols_tr, rho_tr = column_set(args.train_columns, SEED + 1, heights, lbm, inputs)
@@ -590,8 +590,8 @@ def run_warmstart(args):
     lbm.lbm_mlp_destroy(h)
     runs = {}
     final = {}
-    for name, init, fp32_first in (("fp64_tanh", rho0, False), ("fp32_fp64_tanh", rho0, True),
-                                   ("fp64_warm", rho_ml, False), ("fp32_fp64_warm", rho_ml, True)):
+    for name, init, fp32_first in (("fp64_tanh", rho0, False), ("fp32_dd_tanh", rho0, True),
+                                   ("fp64_warm", rho_ml, False), ("fp32_dd_warm", rho_ml, True)):
         tuned = {}
         sec, st, res, status, bb = run_to_steady(lbm, cols, init, cap, fp32_first, tuned)
         final[name] = torch.empty(rho0.size, dtype=torch.float64, device="cuda")
@@ -627,8 +627,8 @@ def run_warmstart(args):
                                   "tanh_max_abs_median": float(np.median(per_col_tanh[ok])),
                                   "network_max_abs_p90": float(np.percentile(per_col[ok], 90)),
                                   "tanh_max_abs_p90": float(np.percentile(per_col_tanh[ok], 90))}
-    out["value"] = runs["fp32_fp64_warm"]["seconds"]
-    out["speedup_vs_plain_fp64"] = runs["fp64_tanh"]["seconds"] / runs["fp32_fp64_warm"]["seconds"]
+    out["value"] = runs["fp32_dd_warm"]["seconds"]
+    out["speedup_vs_plain_fp64"] = runs["fp64_tanh"]["seconds"] / runs["fp32_dd_warm"]["seconds"]
     out["steps_ratio_warm_vs_tanh_fp64"] = out["runs"]["fp64_warm"]["steps_all_converged"] / max(
         1, out["runs"]["fp64_tanh"]["steps_all_converged"])
     print(json.dumps(out), flush=True)
