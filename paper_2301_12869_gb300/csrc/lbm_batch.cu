@@ -112,6 +112,13 @@ __device__ __forceinline__ void pull_col(const T* f, int nx, int ny, int N, int 
   g[8] = hi ? f[6 * N + node] : f[8 * N + (y + 1) * nx + xl];
 }
 
+// lane 0's value in every lane of the warp
+__device__ __forceinline__ float bcast_lane0(float v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ double bcast_lane0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ lbm::dd bcast_lane0(lbm::dd v) {
+  return lbm::dd{__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0)};
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int m = 16; m; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
@@ -320,9 +327,18 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
     const long long iters = MODE == lbm::MODE_STEP ? run.max_steps : 1;
     for (; it < iters; ++it) {
       const int p = int(it & 1);
-      double msum = 0.0;
-      for (int w2 = 0; w2 < NW; ++w2) msum += red[p][w2];  // same order in every thread
-      const T dmean = lbm::from_double<T>(msum / double(N));
+      // <rho> - rho_ref from the FP64 mass partials: lane 0 of each warp forms it (GB300's
+      // FP64 pipe is slow; the division alone is ~20 FP64 instructions) and broadcasts it
+      T dmean;
+      {
+        T dm = lbm::cst<T>(0.0);
+        if (lane == 0) {
+          double msum = 0.0;
+          for (int w2 = 0; w2 < NW; ++w2) msum += red[p][w2];  // same order in every warp
+          dm = lbm::from_double<T>(msum / double(N));
+        }
+        dmean = bcast_lane0(dm);
+      }
       const bool save = MODE == lbm::MODE_STEP && K >= 2 && ((it + 2) % K == 0);
       const bool chk = MODE == lbm::MODE_STEP && K >= 2 && ((it + 1) % K == 0);
       // (A) rho and psi of every node (Eqs. Density, EOS, InteractionPotential)
