@@ -681,6 +681,45 @@ def run_gemm(args):
     return 0
 
 
+# ---------------------------------------------------------------- small FP64 column
+def run_small(args):
+    """The plain method in FP64 on a 4 x 200 column (bounce-back walls, T = 0.85 T_c, rho g
+    with g_y = -2e-5, liquid below y = 100 joined by a tanh of width 5, tau = 1): 20 000
+    steps, device-timed with CUDA events. 800 nodes give 2 CTAs, so the step is bound by
+    launch and pipeline latency, not by HBM: the line reports microseconds per step."""
+    import torch
+
+    from paper_2301_12869_gb300 import inputs, lbm
+
+    nx, ny, steps = 4, 200, 20000
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    rv, rl, _ = lbm.lbm_coexistence(A, B, R, 0.85 * Tc)
+    rho0 = inputs.column_rho0(nx, ny, rl, rv, 100, width=5.0)
+    p = lbm.make_params(nx, ny, 0.85 * Tc, "fp64", a=A, b=B, R=R, form=1, g=(0.0, -2e-5))
+    lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
+    lat.step(max(args.warmup, 3))
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    lat.step(steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mass = lat.reduce(lbm.LBM_REDUCE_MASS)[0]
+    info = lbm.lbm_launch_info(lat.h)
+    status = lat.status()
+    lat.close()
+    print(json.dumps({"metric": "us per step (4 x 200 FP64 column)", "value": 1e3 * ms / steps, "unit": "us",
+                      "higher_is_better": False, "impl": "gb300", "n_gpus": 1, "steps": steps,
+                      "mlups": nx * ny * steps / (ms * 1e-3) / 1e6, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "4x200 D2Q9 column, FP64, bounce-back walls", "T_over_Tc": 0.85,
+                                 "gravity": "rho g", "g_y": -2e-5, "liquid_rows": 100, "tanh_width": 5.0,
+                                 "launch": info},
+                      "status": status, "mass": mass}), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- boiling example
 def run_boiling(args):
     """The paper's phase-formation example (Sec. V): a 1-D column of 101 wet nodes (h = 100,
@@ -776,11 +815,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
-    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling", "gemm"],
+    ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling", "gemm", "small"],
                     default="domain",
                     help="domain: the 1024 x 4096 single-domain throughput line (default); "
                          "columns: time to steady state of batched columns; "
-                         "thermal: the 512 x 2048 thermal column")
+                         "thermal: the 512 x 2048 thermal column; "
+                         "small: the 4 x 200 FP64 column, 20000 steps (latency-bound)")
     ap.add_argument("--thermal-track", action="store_true")
     ap.add_argument("--thermal-steps", type=int, default=8000)
     ap.add_argument("--thermal-every", type=int, default=500)
@@ -820,6 +860,8 @@ def main(argv=None):
         return run_boiling(args) if rank == 0 else 0
     if args.workload == "gemm":
         return run_gemm(args) if rank == 0 else 0
+    if args.workload == "small":
+        return run_small(args) if rank == 0 else 0
 
     import numpy as np
     import torch
