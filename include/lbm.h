@@ -300,7 +300,7 @@ int lbm_batch_destroy(lbm_batch* b);
  * A 5 -> 128 -> 128 -> 128 -> 1 network with SiLU activations predicts the steady density
  * profile rho(z)/rho_c of a column from its descriptors (T/T_c, log10|g|, gravity form,
  * <rho>/rho_c, z/H) with z = y + 1/2 and H = ny. Its only use is to initialise columns;
- * the lattice Boltzmann run to the residual target stays the judge of the result.
+ * the lattice Boltzmann run to the residual target alone decides the result.
  * Arithmetic: bfloat16 inputs, weights and activations as tensor-core operands (tcgen05,
  * FP32 accumulation in tensor memory), FP32 biases, output layer, loss and Adam; inputs
  * normalised as x_n = (x - c)/s with c = (0.825, -5, 1.5, 1.4, 0.5), s = (0.125, 1, 0.5,

@@ -2,7 +2,7 @@
 
 The network is not part of the paper: it predicts the steady density profile of a
 liquid column (the set-up of Sec. IV) from five column descriptors, and its output
-only initialises the lattice Boltzmann run, which stays the judge of the result.
+only initialises the lattice Boltzmann run, which alone decides the result.
 
 Definition (plain FP64, in this order):
     x  = (T/T_c, log10|g|, form, <rho>/rho_c, z/H) mapped by the fixed affine

@@ -1,7 +1,7 @@
 // Learned warm start for the liquid-column runs: a 5 -> 128 -> 128 -> 128 -> 1 SiLU
 // network that predicts the steady density profile rho(z)/rho_c of a column from
 // (T/T_c, log10|g|, gravity form, <rho>/rho_c, z/H). It has no counterpart in the paper;
-// it only initialises lattice Boltzmann runs (Sec. IV set-up), which remain the judge.
+// it only initialises lattice Boltzmann runs (Sec. IV set-up), which decide the result.
 //
 // Arithmetic: bfloat16 inputs, weights and activations as matrix operands, FP32
 // accumulation, FP32 biases, output layer, loss and Adam (FP32 master weights).

@@ -242,7 +242,7 @@ def test_warm_start_gain_on_held_out_columns():
     trained on the steady profiles of 512 seeded 4 x 64 columns (FP32 runs of the method),
     its mass-corrected start is closer to the converged profile than the tanh start, and the
     lattice Boltzmann run from it reaches the tanh start's steady state on most columns (the
-    network only initialises; the FP64 run to 1e-10 is the judge)."""
+    network only initialises; the FP64 run to 1e-10 decides)."""
     import torch
 
     a, b, R = 0.25, 4.0, 1.0

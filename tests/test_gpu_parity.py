@@ -4,7 +4,7 @@ Inputs come from paper_2301_12869_gb300.inputs (seeded); expected values come
 only from oracle/. Tolerances:
 * FP64 path: the two sides evaluate the same formulas in different association
   orders, so each step adds a few ulp (~1e-17 on populations of order 0.1);
-  step-by-step checks use |df| <= 1e-14, and the 10^4-step run the north-star
+  step-by-step checks use |df| <= 1e-14, and the 10^4-step run the stated
   bound |drho|/rho <= 1e-12.
 * FP32 path: one step rounds each of the ~20 terms that build a population to
   FP32 (relative 6e-8 of terms up to ~0.3), so one step is within 1e-6 absolute
