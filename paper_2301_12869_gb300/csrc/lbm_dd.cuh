@@ -65,7 +65,7 @@ __device__ __forceinline__ dd fast_div(dd a, dd b) {
 
 // sqrt of max(x, 0) with `bad` set when x < 0 or NaN, as for the other value types
 __device__ __forceinline__ dd sqrt_checked(dd x, bool& bad) {
-  if (!(x.hi >= 0.f)) {
+  if (!(x.hi >= 0.f) || (x.hi == 0.f && x.lo < 0.f)) {
     bad = true;
     return dd{0.f, 0.f};
   }
