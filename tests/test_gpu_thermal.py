@@ -248,3 +248,37 @@ def test_thermal_handle_keeps_a_thermal_tile(precision):
         assert lbm.lbm_status(h) == 0
     finally:
         lbm.lbm_destroy(h)
+
+
+def test_full_size_thermal_column_sampled():
+    """The 512 x 2048 FP32 heated column of the thermal workload (bench.py's set-up, default
+    tile: the launch configuration it times): one thermal step - fused LBM step, moments
+    pass, Heun step - after 20, checked on sampled columns against the oracle run on a
+    24-column strip around each column (full height, so the walls are exact; one thermal step
+    reaches 6 columns, the strip's periodic seams are 12 away)."""
+    import dataclasses
+
+    import bench
+
+    p, rho0, _ = bench.thermal_setup("fp32", lbm, inputs)
+    op, th = oracle_of(p)
+    h = lbm.lbm_init(p, rho0)
+    try:
+        lbm.lbm_step(h, 20)
+        f_t, T_t = read(h, p)
+        lbm.lbm_step(h, 1)
+        f_n, T_n = read(h, p)
+        assert lbm.lbm_status(h) == 0
+    finally:
+        lbm.lbm_destroy(h)
+    nx = p.nx
+    q = dataclasses.replace(op, nx=24)
+    worst_f = worst_T = 0.0
+    for x in (0, 1, 255, 256, 300, nx - 1):
+        cols = [(x + d) % nx for d in range(-12, 12)]
+        fo, To = oth.thermal_step(np.ascontiguousarray(f_t[:, :, cols]), np.ascontiguousarray(T_t[:, cols]), q, th)
+        worst_f = max(worst_f, float(np.max(np.abs(f_n[:, :, x] - fo[:, :, 12]))))
+        worst_T = max(worst_T, float(np.max(np.abs(T_n[:, x] - To[:, 12]))))
+    assert worst_f <= 2e-6, worst_f
+    assert worst_T <= 2e-6, worst_T
+    assert np.max(np.abs(T_n - T_t)) > 0  # the field moved: the check is not vacuous
