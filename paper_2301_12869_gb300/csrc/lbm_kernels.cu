@@ -419,6 +419,10 @@ __host__ __device__ constexpr size_t ws_smem() {
   return off + 2 * S * sizeof(uint64_t) + (NWC + 2) * sizeof(double);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 struct PsiRow {  // psi at the left neighbour, the lane's own pair, the right neighbour
   float l;
   f2 c;

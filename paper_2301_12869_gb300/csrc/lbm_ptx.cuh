@@ -35,10 +35,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// one arrival on the barrier (release semantics at CTA scope)
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
+// Waits for the phase with the given parity; gives up after `limit` clock cycles.
 // Programmatic dependent launch. A kernel launched with the programmatic stream
 // serialization attribute may start while the previous kernel in its stream is still
 // running; griddep_wait() returns once that kernel has completed and its writes are
@@ -69,7 +66,6 @@ cudaError_t launch_dependent(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t
   return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
 }
 
-// Waits for the phase with the given parity; gives up after `limit` clock cycles.
 __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kWaitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
