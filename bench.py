@@ -157,8 +157,9 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle timing
-def oracle_sample_main(ny_slice, steps):
-    """Runs in a child process: oracle steps on a 1024 x ny_slice slice around the interface."""
+def oracle_sample_main(ny_slice, steps, warmup=1):
+    """Runs in a child process: `warmup` untimed, then `steps` timed oracle steps on a
+    1024 x ny_slice slice around the interface."""
     import numpy as np
 
     from oracle import eos
@@ -172,7 +173,8 @@ def oracle_sample_main(ny_slice, steps):
     rho0 = np.ascontiguousarray(rho_full_rows[y0:y0 + ny_slice])
     p = olbm.Params(nx=NX, ny=ny_slice, a=A, b=B, R=R, T=TR * Tc, g=(0.0, GY), form=2)
     f = olbm.init_state(rho0)
-    f = olbm.step(f, p)  # warm-up (allocations)
+    for _ in range(max(1, warmup)):  # warm-up (allocations)
+        f = olbm.step(f, p)
     t0 = time.perf_counter()
     for _ in range(steps):
         f = olbm.step(f, p)
@@ -180,9 +182,9 @@ def oracle_sample_main(ny_slice, steps):
     print(json.dumps({"seconds": dt, "nodes": NX * ny_slice, "steps": steps}))
 
 
-def time_oracle(ny_slice, steps):
+def time_oracle(ny_slice, steps, warmup=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = f"import bench; bench.oracle_sample_main({ny_slice}, {steps})"
+    code = f"import bench; bench.oracle_sample_main({ny_slice}, {steps}, {warmup})"
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -790,13 +792,14 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     ny_slice = args.ref_rows
-    # the child process runs one untimed warm-up step, then times K oracle steps
-    mlups, res = time_oracle(ny_slice, max(1, args.steps))
+    # the child process runs W untimed warm-up steps, then times K oracle steps
+    mlups, res = time_oracle(ny_slice, max(1, args.steps), max(1, args.warmup))
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["seconds"] * 1e3 / res["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": workload_config("fp64") | {"sample_rows": ny_slice},
+        # the workload of the GPU arm's line; the oracle computes it in FP64 (dtype)
+        "config": workload_config(args.precision) | {"sample_rows": ny_slice},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": f"{res['steps']} FP64 oracle steps on a {NX}x{ny_slice} slice around the interface"},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
