@@ -397,6 +397,14 @@ int lbm_mlp_destroy(lbm_mlp* h);
  *   this step (LBM_ENONPHYS, LBM_ETIMEOUT); text in lbm_last_error(NULL). */
 int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_out, void* stream);
 
+/* Self-check of the failure path every device-side wait of the library takes (no
+ * counterpart in the paper): one thread waits on an mbarrier that nothing arrives on,
+ * bounded by `cycles` clock cycles (1 .. 2e9, about 1 ns each), then records the timeout in
+ * a device status word that is read back - no trap, the context stays usable. Returns
+ * LBM_ETIMEOUT, the expected outcome, or LBM_EINVAL / LBM_ECUDA; LBM_OK would mean the
+ * wait did not give up. Allocates 4 device bytes on the current device; synchronises. */
+int lbm_wait_bound_selftest(long long cycles);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 // LBM_REDUCE_INTERFACE_Y. All arithmetic of the time step runs in the kernels.
 #include "lbm.h"
 #include "lbm_internal.h"
+#include "lbm_ptx.cuh"
 
 #include <cuda_runtime.h>
 
@@ -777,6 +778,41 @@ int lbm_set_tiling(lbm_handle* h, int variant) {
   if (rc) return rc;
   h->tiling = t;
   h->P = t.nbands * t.nstrips;
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// the wait-bound self-check: the bounded wait the library's kernels use, on a barrier that
+// expects one arrival and never gets it
+__global__ void wait_bound_kernel(long long cycles, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    lbm::mbar_init(&bar, 1);
+    lbm::fence_mbar_init();
+    if (!lbm::mbar_wait_bounded(&bar, 0u, cycles)) atomicOr(status, lbm::STATUS_TIMEOUT);
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_wait_bound_selftest(long long cycles) {
+  if (cycles < 1 || cycles > 2000000000LL) { set_err(g_err, "cycles must be in [1, 2e9]"); return LBM_EINVAL; }
+  int* status = nullptr;
+  cudaError_t e = cudaMalloc(&status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    wait_bound_kernel<<<1, 32>>>(cycles, status);
+    e = cudaGetLastError();
+  }
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (status) cudaFree(status);
+  if (e != cudaSuccess) { set_err(g_err, "wait-bound self-check: %s", cudaGetErrorString(e)); return LBM_ECUDA; }
+  if (st & lbm::STATUS_TIMEOUT) { set_err(g_err, "the bounded wait gave up as intended"); return LBM_ETIMEOUT; }
+  set_err(g_err, "the bounded wait did not give up");
   return LBM_OK;
 }
 

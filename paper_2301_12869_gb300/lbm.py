@@ -42,7 +42,7 @@ EXPORTS = (
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
     "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
     "lbm_batch_convert", "lbm_batch_destroy",
-    "lbm_batch_set_threads", "lbm_batch_autotune",
+    "lbm_batch_set_threads", "lbm_batch_autotune", "lbm_wait_bound_selftest",
     "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
     "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_gemm_enqueue",
     "lbm_mlp_destroy",
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
         "lbm_batch_run_stall": (i32, [vp, d, i64, i32, i32, P(d)]),
         "lbm_batch_set_acceleration": (i32, [vp, i32]),
         "lbm_batch_set_threads": (i32, [vp, i32]),
+        "lbm_wait_bound_selftest": (i32, [ctypes.c_longlong]),
         "lbm_batch_autotune": (i32, [vp, i32, vp, vp]),
         "lbm_batch_results": (i32, [vp, vp, vp, vp]),
         "lbm_batch_moments": (i32, [vp, vp, vp, vp, i32]),
@@ -329,6 +330,15 @@ def lbm_batch_run_stall(b, tol, max_steps, check_every=100, stall_checks=10):
 def lbm_batch_set_acceleration(b, checks):
     """Extrapolation every `checks` residual checks (0: off) for later runs of this batch."""
     _check(load().lbm_batch_set_acceleration(b, int(checks)))
+
+
+def lbm_wait_bound_selftest(cycles=2_000_000):
+    """The device-side bounded wait's failure path on purpose: returns LBM_ETIMEOUT's code
+    when the wait gave up and its status came back (the expected outcome), else raises."""
+    rc = load().lbm_wait_bound_selftest(int(cycles))
+    if rc != LBM_ETIMEOUT:
+        _check(rc if rc != LBM_OK else LBM_EINVAL)
+    return rc
 
 
 def lbm_batch_set_threads(b, threads):
