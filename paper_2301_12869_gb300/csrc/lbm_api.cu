@@ -394,6 +394,7 @@ int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes) {
 }
 
 int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stream, lbm_handle** out) {
+  lbm::TraceRange trace("lbm_init");
   int rc = validate(p, g_err);
   if (rc) return rc;
   if (!out || !rho0) { set_err(g_err, "out and rho0 must not be NULL"); return LBM_EINVAL; }
@@ -496,6 +497,7 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
 }
 
 int lbm_step(lbm_handle* h, int64_t nsteps) {
+  lbm::TraceRange trace("lbm_step");
   if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
   if (nsteps < 0) { set_err(h->err, "nsteps must be >= 0"); return LBM_EINVAL; }
   lbm::StepIO io{};
@@ -527,6 +529,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
 }
 
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, int where) {
+  lbm::TraceRange trace("lbm_moments");
   if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
   if (where != LBM_HOST && where != LBM_DEVICE) { set_err(h->err, "where must be LBM_HOST or LBM_DEVICE"); return LBM_EINVAL; }
   int rc;
@@ -540,6 +543,7 @@ int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy, int where) {
 }
 
 int lbm_reduce(lbm_handle* h, int kind, double* out) {
+  lbm::TraceRange trace("lbm_reduce");
   if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
   if (!out) { set_err(h->err, "out is NULL"); return LBM_EINVAL; }
   int rc;
@@ -599,6 +603,7 @@ int lbm_reduce(lbm_handle* h, int kind, double* out) {
 }
 
 int lbm_get_state(lbm_handle* h, double* f, int where, int64_t* steps_done) {
+  lbm::TraceRange trace("lbm_get_state");
   if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
   if (!f || (where != LBM_HOST && where != LBM_DEVICE)) { set_err(h->err, "bad f or where"); return LBM_EINVAL; }
   if (steps_done) *steps_done = h->steps;
@@ -615,6 +620,7 @@ int lbm_get_state(lbm_handle* h, double* f, int where, int64_t* steps_done) {
 }
 
 int lbm_set_state(lbm_handle* h, const double* f, int where, int64_t steps_done) {
+  lbm::TraceRange trace("lbm_set_state");
   if (!h) { set_err(g_err, "handle is NULL"); return LBM_EINVAL; }
   if (!f || (where != LBM_HOST && where != LBM_DEVICE)) { set_err(h->err, "bad f or where"); return LBM_EINVAL; }
   for (int i = 0; i < 9; ++i) {

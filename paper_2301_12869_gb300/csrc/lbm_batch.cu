@@ -807,6 +807,7 @@ int lbm_batch_set_threads(lbm_batch* b, int threads) {
 }
 
 int lbm_batch_autotune(lbm_batch* b, int steps, int* threads, double* us) {
+  lbm::TraceRange trace("lbm_batch_autotune");
   if (!b) return bfail(LBM_EINVAL, "batch is NULL");
   if (steps < 1) return bfail(LBM_EINVAL, "steps must be >= 1");
   // a copy of the current state, so that b's state and results stay as they are
@@ -857,6 +858,7 @@ int lbm_batch_run(lbm_batch* b, double tol, int64_t max_steps, int check_every, 
 
 int lbm_batch_run_stall(lbm_batch* b, double tol, int64_t max_steps, int check_every, int stall_checks,
                         double* seconds) {
+  lbm::TraceRange trace("lbm_batch_run");
   if (!b) return bfail(LBM_EINVAL, "batch is NULL");
   if (max_steps < 0 || check_every < 2 || !(tol >= 0) || stall_checks < 0)
     return bfail(LBM_EINVAL, "need max_steps >= 0, check_every >= 2, tol >= 0, stall_checks >= 0");
@@ -968,6 +970,7 @@ int lbm_batch_get_state(lbm_batch* b, double* f, int where) {
 }
 
 int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out) {
+  lbm::TraceRange trace("lbm_batch_convert");
   if (!src || !out || (precision != LBM_FP32 && precision != LBM_FP64 && precision != LBM_DOUBLE_FLOAT))
     return bfail(LBM_EINVAL, "bad arguments");
   *out = nullptr;

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbm.h"
 
@@ -94,6 +95,15 @@ cudaError_t launch_energy_step(int precision, int nx, int ny, int wall_nodes, do
 // Tf = T_bot + (T_top - T_bot)(y + 1/2)/ny, or T_bot + (T_top - T_bot) y/(ny - 1) with wall nodes
 cudaError_t launch_linear_T(int precision, int nx, int ny, double T_bot, double T_top, int wall_nodes, void* Tf,
                             cudaStream_t stream);
+
+// ---- NVTX range over the rest of a host scope (init, step, moments, reductions, state I/O,
+// batch runs): named intervals on a profiler's timeline, no cost without a tool attached
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // ---- host helpers of lbm_api.cu shared with other entry points (same behaviour as lbm_init's)
 int validate_params(const lbm_params* p, char* err);  // err: 512 bytes
