@@ -378,21 +378,27 @@ int lbm_mlp_destroy(lbm_mlp* h);
  * allocations of its own. lbm_step_noalloc runs one time step f_out = step(f_in) - the
  * same fused kernel as lbm_step - on caller-owned device arrays and allocates nothing.
  *
- * f_in, f_out: distinct DEVICE arrays of 9*nx*ny reals (float for LBM_FP32, double for
- *   LBM_FP64), layout [i][y][x] in the order of Eq. VelocitySet, holding the deviations
- *   f_i - w_i rho_ref with rho_ref = p->rho_ref (NaN means 0). Caller-owned; read / written.
+ * f_in, f_out: distinct DEVICE arrays (of the current device, or managed memory) of
+ *   9*nx*ny reals (float for LBM_FP32, double for LBM_FP64), layout [i][y][x] in the order
+ *   of Eq. VelocitySet, holding the deviations f_i - w_i rho_ref with rho_ref = p->rho_ref
+ *   (NaN means 0). Caller-owned; read / written. A pointer that is not device memory is
+ *   rejected (LBM_EINVAL); the element type and count cannot be checked here and are the
+ *   caller's to get right (the Python binding checks them).
  * p: as for lbm_init, isothermal (thermal = 0), any wall; p->workspace is ignored. stream: a cudaStream_t (NULL = default).
  * Scratch: the FP64 partial mass sums that give <rho> (Eq. Gravity_2) and a status word
  *   live in a file-scope __device__ array of 65 792 bytes inside liblbm, held by every
  *   device that loads the library until the process exits. Its 4096 partial slots bound
  *   the step's grid: lattices wider than 4096 x-bands (nx > 4 194 304 in FP32, 2 097 152 in
  *   FP64) are rejected with LBM_EINVAL.
+ * Cost: with Eq. Gravity_2 each call first reads f_in once more to form its mass partials
+ *   (a handle keeps them from the previous step instead); with Eq. Gravity_1 it does not.
  * Every call shares that array and leaves its own values there; the status word is
  *   cleared at the start of each call. Calls that overlap on the GPU (several streams, or
  *   host threads without ordering) race on it: serialise them.
  * The first call on a device (per process) looks up the array's device address with
  *   cudaGetSymbolAddress and sets the kernels' shared-memory limit; make that first call
- *   before any stream capture.
+ *   before any stream capture. If that set-up fails, the call returns LBM_ECUDA and the
+ *   next call on the device tries it again.
  * Synchronises `stream`. Returns LBM_OK, LBM_EINVAL, LBM_ECUDA, or the device status of
  *   this step (LBM_ENONPHYS, LBM_ETIMEOUT); text in lbm_last_error(NULL). */
 int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_out, void* stream);

@@ -2,26 +2,27 @@
 // and its helpers. Method: arXiv 2301.12869, Sec. III (equations named inline).
 //
 // Fused step, one launch per time step. CTA b owns a band of nodes along x
-// (width band_w, x periodic) and a strip of rows; it walks its rows bottom-up:
+// (x periodic) and a strip of rows, which it walks row by row (even strips upward,
+// odd strips downward, so neighbouring strips read their shared halo rows together).
+// For each pulled row r (the strip's rows plus one halo row below and above) the
+// bulk-copy engine (cp.async.bulk, completion on an mbarrier) brings the 9 source
+// rows that pull streaming (Eq. LBE) needs into a shared-memory stage: plane i from
+// row r - c_iy, or - where the link crosses a wall - plane opp(i) of row r (halfway
+// bounce-back), each with 16 bytes of periodic x halo on both sides. From the stage,
+// rho (Eq. Density) and psi (Eqs. EOS, InteractionPotential) of row r are formed;
+// once psi of rows r-2, r-1 and r is known, row r-1 is collided: the Shan-Chen force
+// from the 3x3 psi stencil (Eq. ShanChenForce), gravity (Eqs. Gravity_1/2), the
+// velocity (Eq. Momentum) and MRT with Li's forcing (Eqs. OperatorMRT, LiFS) in
+// moment space, and its 9 post-collision values are stored.
 //
-//   for each pulled row r (strip rows plus one halo row below and above):
-//     1. the bulk-copy engine (cp.async.bulk, completion on an mbarrier) brings
-//        the 9 source rows that pull streaming (Eq. LBE) needs for row r into a
-//        shared-memory stage: plane i from row r - c_iy, or - where the link
-//        crosses a wall - plane opp(i) of row r (halfway bounce-back); each
-//        copy carries 16 bytes of x halo on both sides (periodic wrap);
-//     2. every thread computes rho (Eq. Density) and psi (Eqs. EOS,
-//        InteractionPotential) of row r for the band plus one x halo node on
-//        each side into a 4-row psi ring;
-//     3. one CTA barrier; the stage of row r-2 is refilled with row r-2+S;
-//     4. row r-1 is collided: Shan-Chen force from the 3x3 psi stencil
-//        (Eq. ShanChenForce), gravity (Eqs. Gravity_1/2), velocity
-//        (Eq. Momentum), MRT with Li's forcing (Eqs. OperatorMRT, LiFS) in
-//        moment space, and the 9 post-collision values are stored.
-//
-// In FP32 each thread can own two neighbouring nodes and evaluate both with packed
-// FP32x2 instructions (value type f2 of lbm_vec.cuh); FP64 and the scalar FP32 tile
-// variant evaluate one node per value.
+// Default FP32 kernel (step_kernel_ws): one producer warp issues the copies into a
+// ring of S stages; 8 consumer warps each own 64 nodes (a pair of neighbouring nodes
+// per lane, evaluated with packed FP32x2 instructions, value type f2 of lbm_vec.cuh)
+// and walk the rows without any CTA barrier: psi of the three rows around the
+// collided row stays in registers, x neighbours come by warp shuffles, and a stage is
+// refilled once every consumer warp has arrived on its `empty` mbarrier.
+// Other tile variants (step_kernel, FP64 and the tuner's alternatives) keep psi in a
+// 4-row shared ring and take one CTA barrier per row.
 //
 // The populations are stored as deviations g_i = f_i - w_i rho_ref, which
 // turns every moment of the reference rest state into a constant that the

@@ -28,12 +28,44 @@ constexpr int kMaxDevices = 64;
 // held by every device that loads the library until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[2 * kMaxCtas + 32];
 
+// Per-device set-up state. A failed set-up is not remembered: the next call on that
+// device tries again (under the mutex, so concurrent first calls do it once).
 struct DeviceScratch {
-  std::once_flag once;
-  double* ptr = nullptr;       // device address of g_noalloc_scratch on this device
-  cudaError_t err = cudaSuccess;
+  double* ptr = nullptr;  // device address of g_noalloc_scratch on this device; NULL until set up
 };
 DeviceScratch g_dev[kMaxDevices];
+std::mutex g_setup_mutex;
+
+// The scratch array's device address and the step kernels' shared-memory limit, once per
+// device with that device current; returns the address or NULL with err set.
+double* scratch_on_device(int dev, cudaError_t* err) {
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  DeviceScratch& ds = g_dev[dev];
+  *err = cudaSuccess;
+  if (ds.ptr) return ds.ptr;
+  double* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_scratch);
+  if (e == cudaSuccess) e = lbm::step_prepare(LBM_FP32);
+  if (e == cudaSuccess) e = lbm::step_prepare(LBM_FP64);
+  if (e != cudaSuccess || !ptr) {
+    (void)cudaGetLastError();  // not sticky: a later call retries
+    *err = e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+    return nullptr;
+  }
+  ds.ptr = ptr;
+  return ptr;
+}
+
+// true when p is device memory of device dev or managed memory (not host, pinned or
+// unregistered memory, nor another device's)
+bool is_device_pointer(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
+}
 
 int fail(int code, const char* msg) {
   lbm::set_last_error(msg);
@@ -53,16 +85,15 @@ extern "C" int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_o
     return fail(LBM_ECUDA, "no CUDA device");
   if (dev >= kMaxDevices) return fail(LBM_EINVAL, "device index beyond the 64 this entry point supports");
 
+  if (!is_device_pointer(f_in, dev) || !is_device_pointer(f_out, dev))
+    return fail(LBM_EINVAL, "f_in and f_out must be device memory of the current device");
+
   // once per device, with that device current: the scratch array's device address and the
   // kernels' shared-memory limit (both precisions)
-  DeviceScratch& ds = g_dev[dev];
-  std::call_once(ds.once, [&ds]() {
-    ds.err = cudaGetSymbolAddress(reinterpret_cast<void**>(&ds.ptr), g_noalloc_scratch);
-    if (ds.err == cudaSuccess) ds.err = lbm::step_prepare(LBM_FP32);
-    if (ds.err == cudaSuccess) ds.err = lbm::step_prepare(LBM_FP64);
-  });
-  if (ds.err != cudaSuccess || !ds.ptr) {
-    snprintf(err, sizeof(err), "scratch set-up failed: %s", cudaGetErrorString(ds.err));
+  cudaError_t se = cudaSuccess;
+  double* scratch = scratch_on_device(dev, &se);
+  if (!scratch) {
+    snprintf(err, sizeof(err), "scratch set-up failed: %s", cudaGetErrorString(se));
     return fail(LBM_ECUDA, err);
   }
 
@@ -73,7 +104,10 @@ extern "C" int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_o
              kMaxCtas, kMaxCtas * t.band_w);
     return fail(LBM_EINVAL, err);
   }
-  if (t.nbands * t.nstrips > kMaxCtas) {  // fewer, taller strips so the partials fit
+  // The plan fills one wave: nbands x nstrips <= max(nbands, SMs x resident CTAs per SM),
+  // 304 on GB300 (152 SMs x 2), so this only acts on a GPU with more than 4096 resident
+  // step CTAs: fewer, taller strips (ceil(ny / ceil(ny / m)) <= m strips for m = 4096 / nbands)
+  if (t.nbands * t.nstrips > kMaxCtas) {
     const int nstrips = kMaxCtas / t.nbands;
     t.strip_h = (p->ny + nstrips - 1) / nstrips;
     t.nstrips = (p->ny + t.strip_h - 1) / t.strip_h;
@@ -83,17 +117,20 @@ extern "C" int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_o
   if (!std::isfinite(rho_ref)) return fail(LBM_EINVAL, "rho_ref must be finite or NaN");
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  double* part_in = ds.ptr;
-  double* part_out = ds.ptr + kMaxCtas;
-  int* status = reinterpret_cast<int*>(ds.ptr + 2 * kMaxCtas);
+  double* part_in = scratch;
+  double* part_out = scratch + kMaxCtas;
+  int* status = reinterpret_cast<int*>(scratch + 2 * kMaxCtas);
+  // <rho> enters only Eq. Gravity_2: the mass partials of f_in (one extra read of it) are
+  // formed only for that form
+  const bool need_mean = p->gravity_form == LBM_GRAVITY_RHO_MINUS_MEAN_G;
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);  // the array keeps the last call's status
-  if (e == cudaSuccess) e = lbm::launch_partials(p->precision, f_in, p->nx, p->ny, part_in, P, s);
+  if (e == cudaSuccess && need_mean) e = lbm::launch_partials(p->precision, f_in, p->nx, p->ny, part_in, P, s);
   if (e == cudaSuccess) {
     lbm::StepIO io{};
     io.fin = f_in;
     io.fout = f_out;
     io.part_in = part_in;
-    io.npart_in = P;
+    io.npart_in = need_mean ? P : 0;
     io.part_out = part_out;
     io.status = status;
     e = lbm::launch_step(p->precision, lbm::MODE_STEP, t, lbm::phys_from_params(*p, rho_ref), io, s);

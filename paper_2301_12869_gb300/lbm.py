@@ -290,10 +290,32 @@ def lbm_set_tiling(h, variant):
     _check(load().lbm_set_tiling(h, int(variant)), h)
 
 
+def _noalloc_buffer(t, name, p):
+    """Address of a populations array for lbm_step_noalloc: a contiguous torch CUDA tensor
+    on the current device, of the precision's real type, with 9 nx ny elements. The C side
+    receives only a pointer, so a host array or a short / wrongly typed one is refused here
+    before it can reach the kernel as a device address."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch CUDA tensor (got {type(t).__name__})")
+    if not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must live on the current CUDA device (got {t.device})")
+    want = torch.float32 if p.precision == LBM_FP32 else torch.float64
+    if t.dtype != want:
+        raise ValueError(f"{name} must be {want} for this precision (got {t.dtype})")
+    if t.numel() != 9 * p.nx * p.ny:
+        raise ValueError(f"{name} must hold 9 nx ny = {9 * p.nx * p.ny} values (got {t.numel()})")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
 def lbm_step_noalloc(p, f_in, f_out, stream=None):
     """One step f_out = step(f_in) on caller-owned device arrays of deviations
     f_i - w_i rho_ref (real type of p.precision), with no device allocation."""
-    _check(load().lbm_step_noalloc(ctypes.byref(p), _ptr(f_in)[0], _ptr(f_out)[0], stream))
+    a_in, a_out = _noalloc_buffer(f_in, "f_in", p), _noalloc_buffer(f_out, "f_out", p)
+    _check(load().lbm_step_noalloc(ctypes.byref(p), a_in, a_out, stream))
 
 
 def lbm_batch_init(p, columns, rho0, stream=None):

@@ -97,6 +97,36 @@ def test_every_column_matches_oracle(precision, steps, tol, taus):
         lbm.lbm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("precision, tol", [
+    ("fp64", 1e-13),
+    ("fp32", 1e-6 * math.sqrt(32) + 1e-6),
+    ("dd", 1e-11),
+])
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_tall_columns_match_oracle(precision, tol, threads):
+    """The heights of the batched workload up to 1024 rows in one batch: the dynamic shared
+    memory is sized by the tallest column and a 128-thread CTA carries 32 nodes per thread.
+    Every column, after 32 steps, against the oracle run on that column alone."""
+    heights = (1024, 512, 256, 64, 1024, 128, 256, 512, 1024, 256)
+    cols, rhos = make_columns(len(heights), seed=31, heights=heights)
+    p = batch_params(precision)
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_set_threads(b, threads)
+        total = sum(9 * NX * c["ny"] for c in cols)
+        f0, f1 = np.empty(total), np.empty(total)
+        lbm.lbm_batch_get_state(b, f0)
+        lbm.lbm_batch_run(b, 0.0, 32, check_every=1000)
+        lbm.lbm_batch_get_state(b, f1)
+        st, _, status = lbm.lbm_batch_results(b, len(cols))
+        assert np.all(st == 32) and np.all(status == 0)
+        for col, g0, g1 in zip(cols, split_state(f0, cols), split_state(f1, cols)):
+            want = olbm.run(g0, oracle_column(col, p), 32)
+            assert np.max(np.abs(g1 - want)) <= tol, col
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
 def test_batch_column_equals_single_lattice_handle():
     """The batch runner and lbm_step give the same state for the same column (FP64)."""
     cols, rhos = make_columns(3, seed=9, heights=(40,))
