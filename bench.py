@@ -156,6 +156,85 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlClocks:
+    """SM clock and clock-event reasons of one GPU read through NVML (libnvidia-ml, ctypes)
+    by a thread every ~0.2 ms between start() and stop(), so that a timed region of a
+    millisecond still gets samples. Reads only; falls back to nothing if NVML is absent.
+    Reason bits as NVML defines them: 0x4 sw_power_cap, 0x8 hw_slowdown,
+    0x20 sw_thermal_slowdown, 0x40 hw_thermal_slowdown, 0x80 hw_power_brake_slowdown."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, torch_device):
+        import ctypes
+        import threading
+
+        self.samples, self.max_mhz, self.err = [], None, None
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            self.lib, self.h = lib, ctypes.c_void_p()
+            rc = -1
+            uuid = getattr(self._props(torch_device), "uuid", None)
+            if uuid is not None:
+                rc = lib.nvmlDeviceGetHandleByUUID(("GPU-" + str(uuid)).encode(), ctypes.byref(self.h))
+            if rc != 0:
+                rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(torch_device), ctypes.byref(self.h))
+            if rc != 0:
+                raise RuntimeError("no NVML handle")
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:  # 1: NVML_CLOCK_SM
+                self.max_mhz = mx.value
+            self._reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        except Exception as exc:  # noqa: BLE001 - reported in the summary
+            self.lib, self.err = None, str(exc)
+
+    @staticmethod
+    def _props(dev):
+        import torch
+
+        return torch.cuda.get_device_properties(dev)
+
+    def _run(self):
+        import ctypes
+
+        clk, rsn = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                r = rsn.value if self._reasons(self.h, ctypes.byref(rsn)) == 0 else 0
+                self.samples.append((time.perf_counter(), clk.value, r))
+            time.sleep(0.0002)
+
+    def start(self):
+        import threading
+
+        if self.lib is not None:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+        return self
+
+    def stop(self):
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(timeout=5)
+
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and the reasons seen, over the samples taken within [t0, t1]
+        (host perf_counter seconds) if given, else over all of them."""
+        sel = [s for s in self.samples if (t0 is None or s[0] >= t0) and (t1 is None or s[0] <= t1)]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0,
+                    "source": "nvml" if self.lib is not None else f"none ({self.err})"}
+        reasons = sorted({name for _, _, r in sel for bit, name in self.REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(c for _, c, _ in sel), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sel), "source": "nvml, ~0.2 ms period"}
+
+
 # ---------------------------------------------------------------- CPU oracle timing
 def oracle_sample_main(ny_slice, steps, warmup=1):
     """Runs in a child process: `warmup` untimed, then `steps` timed oracle steps on a
@@ -231,32 +310,86 @@ def aggregate(local_ms, local_units, torch):
 # ---------------------------------------------------------------- end to end
 def run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot):
     """The same metric through the public C ABI with host buffers: lbm_init from pinned
-    host rho0 (host-to-device copy inside), K lbm_step calls' worth of steps, lbm_moments
-    of rho, u_x, u_y to pinned host memory and lbm_reduce(MASS); the library allocates
-    its own device memory. Timed on the host clock around the synchronous calls."""
+    host rho0 (host-to-device copy and the initial state inside), K steps (the same
+    restores as the device-timed run), lbm_moments of rho to pinned host memory and
+    lbm_reduce(MASS). The handle's device workspace is allocated once before the timed
+    region (lbm_workspace_bytes, a torch buffer passed as p->workspace), as a user who
+    runs many jobs allocates it once. Timed on the host clock around the synchronous
+    calls."""
     pinned = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True)
     pinned.copy_(torch.from_numpy(rho0))
     rho_h = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True)
-    ux_h = torch.empty_like(rho_h)
-    uy_h = torch.empty_like(rho_h)
     pe = lbm.make_params(NX, NY, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY))
+    nbytes = lbm.lbm_workspace_bytes(pe)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    pe.workspace = (ws.data_ptr() + 255) // 256 * 256
+    pe.workspace_bytes = nbytes
+    stream = torch.cuda.current_stream().cuda_stream
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = lbm.lbm_init(pe, pinned.numpy())
+    h = lbm.lbm_init(pe, pinned.numpy(), stream)
     run_steps(lbm, h, args.steps, snapshot)
-    lbm.lbm_moments(h, rho_h.numpy(), ux_h.numpy(), uy_h.numpy())
+    lbm.lbm_moments(h, rho_h.numpy())
     mass = lbm.lbm_reduce(h, lbm.LBM_REDUCE_MASS)[0]
     t1 = time.perf_counter()
     lbm.lbm_destroy(h)
+    del ws
     ms, units = aggregate((t1 - t0) * 1e3, float(nodes) * args.steps, torch)
     return {
         "value": units / (ms / 1e3) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * nodes / args.steps,
-        "d2h_bytes_per_step": (3 * 8 * nodes + 8) / args.steps, "mass": mass,
-        "what": "lbm_init from pinned host rho0 + K steps + lbm_moments(rho, ux, uy) to host + "
-                "lbm_reduce(MASS), library-allocated device memory, host clock",
+        "d2h_bytes_per_step": (8 * nodes + 8) / args.steps, "mass": mass, "seconds": (t1 - t0),
+        "what": "lbm_init from pinned host rho0 + K steps + lbm_moments(rho) to pinned host + lbm_reduce(MASS), "
+                "workspace allocated before the timed region, host clock",
     }
+
+
+# ---------------------------------------------------------------- FP32 against FP64 on the domain
+PRECISION_STEPS = 400  # inside the workload's physical window (~500 steps)
+
+
+def precision_report(lbm, rho0, Tc, steps=PRECISION_STEPS, every=100):
+    """The FP32 path against the FP64 GPU run of the same workload and initial state (the
+    FP64 run matches the FP64 oracle to 1e-12, tests/test_gpu_parity.py): every `every`
+    steps, max |rho_32 - rho_64| over the domain, the interface height (first crossing of the
+    coexistence midpoint by the x-averaged profile, LBM_REDUCE_INTERFACE_Y) and the liquid /
+    vapour densities (max / min of that profile, LBM_REDUCE_RHO_LV) of both."""
+    import numpy as np
+
+    hs = {}
+    for prec in ("fp32", "fp64"):
+        q = lbm.make_params(NX, NY, TR * Tc, prec, a=A, b=B, R=R, form=2, g=(0.0, GY))
+        hs[prec] = lbm.lbm_init(q, rho0)
+    rows = []
+    try:
+        rho = {k: np.empty((NY, NX)) for k in hs}
+        done = 0
+        while done < steps:
+            n = min(every, steps - done)
+            for h in hs.values():
+                lbm.lbm_step(h, n)
+            done += n
+            row = {"step": done}
+            for k, h in hs.items():
+                lbm.lbm_moments(h, rho[k])
+                row[f"interface_{k}"] = lbm.lbm_reduce(h, lbm.LBM_REDUCE_INTERFACE_Y)[0]
+                row[f"rho_l_{k}"], row[f"rho_v_{k}"] = lbm.lbm_reduce(h, lbm.LBM_REDUCE_RHO_LV)[:2]
+                row[f"status_{k}"] = lbm.lbm_status(h)
+            row["max_abs_drho"] = float(np.max(np.abs(rho["fp32"] - rho["fp64"])))
+            row["interface_error"] = row["interface_fp32"] - row["interface_fp64"]
+            row["rho_l_rel_error"] = row["rho_l_fp32"] / row["rho_l_fp64"] - 1.0
+            row["rho_v_rel_error"] = row["rho_v_fp32"] / row["rho_v_fp64"] - 1.0
+            rows.append(row)
+    finally:
+        for h in hs.values():
+            lbm.lbm_destroy(h)
+    return {"what": "FP32 populations (FP64 reductions) against the FP64 GPU run, same initial state",
+            "steps": steps, "samples": rows,
+            "max_abs_drho": max(r["max_abs_drho"] for r in rows),
+            "max_abs_interface_error": max(abs(r["interface_error"]) for r in rows),
+            "max_abs_rho_l_rel_error": max(abs(r["rho_l_rel_error"]) for r in rows),
+            "max_abs_rho_v_rel_error": max(abs(r["rho_v_rel_error"]) for r in rows)}
 
 
 # ---------------------------------------------------------------- batched columns
@@ -398,6 +531,160 @@ def run_columns(args):
     }
     print(json.dumps(out), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- time to steady state (default line)
+STEADY_HEIGHTS = (64, 128, 256, 512, 1024)
+
+
+def column_stats(rho, cols, lbm):
+    """Per column of a concatenated density field (4 x H columns): the x-averaged profile's
+    first crossing of the coexistence midpoint at the column's T (interface height), its
+    max (liquid) and min (vapour)."""
+    import numpy as np
+
+    out = np.full((len(cols), 3), np.nan)
+    off = 0
+    for c, col in enumerate(cols):
+        n = 4 * col["ny"]
+        prof = rho[off:off + n].reshape(col["ny"], 4).mean(axis=1)
+        off += n
+        rv, rl, _ = lbm.lbm_coexistence(A, B, R, col["T"])
+        d = prof - 0.5 * (rv + rl)
+        k = np.nonzero(d[:-1] * d[1:] <= 0.0)[0]
+        k = k[d[k] != d[k + 1]]
+        if k.size:
+            y = int(k[0])
+            out[c, 0] = y + d[y] / (d[y] - d[y + 1])
+        out[c, 1], out[c, 2] = prof.max(), prof.min()
+    return out
+
+
+def _path_summary(seconds, steps, res, status, col_sec, cols, ok):
+    import numpy as np
+
+    hs = np.array([c["ny"] for c in cols])
+    by_h = {}
+    for H in sorted(set(hs.tolist())):
+        m = hs == H
+        mk = m & ok
+        by_h[str(H)] = {"columns": int(m.sum()), "converged": int(mk.sum()),
+                        "median_steps": float(np.median(steps[mk])) if mk.any() else None,
+                        "median_seconds": float(np.median(col_sec[mk])) if mk.any() else None}
+    return {"makespan_s": seconds, "converged": int(ok.sum()), "columns": len(cols),
+            "nonphysical": int((status != 0).sum()),
+            "median_steps_converged": float(np.median(steps[ok])) if ok.any() else None,
+            "median_column_seconds_converged": float(np.median(col_sec[ok])) if ok.any() else None,
+            "by_height": by_h}
+
+
+def _error_summary(stats, ref, rho, rho_ref, cols, mask):
+    """Per-column errors of a path's densities against the FP64 run's (columns in mask)."""
+    import numpy as np
+
+    off = np.cumsum([0] + [4 * c["ny"] for c in cols])
+    dmax = np.array([np.max(np.abs(rho[off[i]:off[i + 1]] - rho_ref[off[i]:off[i + 1]])) for i in range(len(cols))])
+    both = mask & np.isfinite(stats[:, 0]) & np.isfinite(ref[:, 0])
+    def q(v, m):
+        return {"median": float(np.median(v[m])), "max": float(np.max(v[m]))} if m.any() else None
+    return {"columns": int(mask.sum()), "max_abs_drho": q(dmax, mask),
+            "abs_interface_error": q(np.abs(stats[:, 0] - ref[:, 0]), both),
+            "rho_l_rel_error": q(np.abs(stats[:, 1] / ref[:, 1] - 1.0), mask),
+            "rho_v_rel_error": q(np.abs(stats[:, 2] / ref[:, 2] - 1.0), mask)}
+
+
+def time_to_steady(args, lbm, inputs, world, rank, torch):
+    """Time to steady state (residual max |rho_t - rho_(t-1)| <= 1e-10, checked every 100
+    steps) of the batched 4 x H columns with the heights, temperatures, gravities and forms
+    of the batched workload: plain FP64 against FP32 down to its rounding floor then
+    double-float (FP32-pair) arithmetic, both capped at args.steady_cap steps per phase.
+    With N ranks every rank runs its share of the columns (partition.column_shares, no
+    exchange); makespans are the max over ranks. Per column: the device seconds its CTA
+    spent on it (lbm_batch_column_seconds) and its steps; the FP32 phase's end state and
+    the final double-float state against the FP64 run's: max |drho|, interface height,
+    liquid and vapour densities."""
+    import numpy as np
+
+    from paper_2301_12869_gb300 import partition
+
+    cols_all, rho_all = column_set(args.steady_columns, SEED, STEADY_HEIGHTS, lbm, inputs)
+    offs = np.cumsum([0] + [4 * c["ny"] for c in cols_all])
+    share = partition.column_shares([c["ny"] for c in cols_all], world)[rank]
+    cols = [cols_all[i] for i in share]
+    rho = np.concatenate([rho_all[offs[i]:offs[i + 1]] for i in share])
+    n, cap = len(cols), args.steady_cap
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    tuned = {}
+    # plain FP64
+    b = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp64", a=A, b=B, R=R), cols, rho)
+    tuned["fp64"] = lbm.lbm_batch_autotune(b, TUNE_STEPS)
+    t64 = lbm.lbm_batch_run(b, 1e-10, cap, 100)
+    st64, res64, s64 = lbm.lbm_batch_results(b, n, check=False)
+    sec64 = lbm.lbm_batch_column_seconds(b, n)
+    rho64 = np.empty(rho.size)
+    lbm.lbm_batch_moments(b, rho=rho64)
+    lbm.lbm_batch_destroy(b)
+    # FP32 to its floor, then double-float
+    b32 = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols, rho)
+    tuned["fp32"] = lbm.lbm_batch_autotune(b32, TUNE_STEPS)
+    lbm.lbm_batch_set_acceleration(b32, ACCEL_CHECKS)
+    t32 = lbm.lbm_batch_run_stall(b32, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
+    st32, res32, s32 = lbm.lbm_batch_results(b32, n, check=False)
+    rho32 = np.empty(rho.size)
+    lbm.lbm_batch_moments(b32, rho=rho32)
+    bd = lbm.lbm_batch_convert(b32, lbm.LBM_DOUBLE_FLOAT)
+    lbm.lbm_batch_destroy(b32)
+    tuned["dd_after_fp32"] = lbm.lbm_batch_autotune(bd, TUNE_STEPS)
+    lbm.lbm_batch_set_acceleration(bd, ACCEL_CHECKS)
+    tdd = lbm.lbm_batch_run(bd, 1e-10, cap, 100)
+    stdd, resdd, sdd = lbm.lbm_batch_results(bd, n, check=False)
+    secdd = lbm.lbm_batch_column_seconds(bd, n)  # FP32 + double-float phases of each column
+    rhodd = np.empty(rho.size)
+    lbm.lbm_batch_moments(bd, rho=rhodd)
+    lbm.lbm_batch_destroy(bd)
+    local = dict(idx=share, cols=cols, t64=t64, t32=t32, tdd=tdd, st64=st64, res64=res64, s64=s64, sec64=sec64,
+                 st32=st32, s32=s32, stdd=stdd, resdd=resdd, sdd=sdd, secdd=secdd,
+                 stats64=column_stats(rho64, cols, lbm), stats32=column_stats(rho32, cols, lbm),
+                 statsdd=column_stats(rhodd, cols, lbm), tuned=tuned)
+    ok64 = (res64 <= 1e-10) & (s64 == 0)
+    okdd = (resdd <= 1e-10) & (sdd == 0)
+    local["prec32"] = _error_summary(local["stats32"], local["stats64"], rho32, rho64, cols, ok64 & (s32 == 0))
+    local["precdd"] = _error_summary(local["statsdd"], local["stats64"], rhodd, rho64, cols, ok64 & okdd)
+    if world > 1:
+        import torch.distributed as dist
+
+        gathered = [None] * world
+        dist.all_gather_object(gathered, {k: v for k, v in local.items()})
+    else:
+        gathered = [local]
+    if rank != 0:
+        return None
+    cat = lambda k: np.concatenate([g[k] for g in gathered])  # noqa: E731
+    cols_g = [c for g in gathered for c in g["cols"]]
+    T64 = max(g["t64"] for g in gathered)
+    T32DD = max(g["t32"] + g["tdd"] for g in gathered)
+    ok64 = (cat("res64") <= 1e-10) & (cat("s64") == 0)
+    okdd = (cat("resdd") <= 1e-10) & (cat("sdd") == 0)
+    both = ok64 & okdd
+    sec64, secdd = cat("sec64"), cat("secdd")
+    out = {
+        "what": "time to residual 1e-10 of batched 4xH columns: plain FP64 vs FP32 then double-float",
+        "workload": f"{len(cols_g)} seeded 4xH liquid columns, H in {STEADY_HEIGHTS}, step cap {args.steady_cap} per phase",
+        "ranks": world, "partition": "disjoint column sets balanced by nodes, no exchange" if world > 1 else None,
+        "check_every": 100, "fp32_tol": FP32_TOL, "fp32_stall_checks": FP32_STALL_CHECKS, "accel_checks": ACCEL_CHECKS,
+        "fp64_plain": _path_summary(T64, cat("st64"), cat("res64"), cat("s64"), sec64, cols_g, ok64),
+        "fp32_then_double_float": _path_summary(T32DD, cat("stdd"), cat("resdd"), cat("sdd"), secdd, cols_g, okdd)
+        | {"fp32_makespan_s": max(g["t32"] for g in gathered)},
+        "makespan_speedup": T64 / T32DD,
+        "converged_in_both": int(both.sum()),
+        "median_column_seconds_both": {"fp64_plain": float(np.median(sec64[both])) if both.any() else None,
+                                       "fp32_then_double_float": float(np.median(secdd[both])) if both.any() else None},
+        "median_column_speedup_both": float(np.median(sec64[both] / secdd[both])) if both.any() else None,
+        "precision_vs_fp64": {"fp32_end_of_phase": gathered[0]["prec32"] if world == 1 else [g["prec32"] for g in gathered],
+                              "fp32_then_double_float": gathered[0]["precdd"] if world == 1 else [g["precdd"] for g in gathered]},
+        "block_threads": tuned_summary(gathered[0]["tuned"]),
+    }
+    return out
 
 
 # ---------------------------------------------------------------- thermal variant
@@ -839,6 +1126,11 @@ def main(argv=None):
     ap.add_argument("--gemm-m", type=int, default=65536, help="rows of the network-shaped GEMM")
     ap.add_argument("--boiling-steps", type=int, default=1000000)
     ap.add_argument("--boiling-prerun-cap", type=int, default=4000000)
+    ap.add_argument("--steady-columns", type=int, default=4096,
+                    help="columns of the time-to-steady block of the default line")
+    ap.add_argument("--steady-cap", type=int, default=20000, help="step cap per phase of that block")
+    ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady block")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32-vs-FP64 report")
     ap.add_argument("--mlp-iters", type=int, default=6000)
     ap.add_argument("--mlp-batch", type=int, default=8192)
     args = ap.parse_args(argv)
@@ -899,6 +1191,7 @@ def main(argv=None):
     # ---- device-resident run (value)
     lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
     info = lbm.lbm_launch_info(lat.h)
+    nvml = NvmlClocks(local).start()  # clocks from before the warm-up to the end of the timed region
     lat.step(args.warmup)
     snapshot = torch.empty((9, NY, NX), dtype=torch.float64, device="cuda")
     lbm.lbm_get_state(lat.h, snapshot)
@@ -908,11 +1201,14 @@ def main(argv=None):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local) as smi:
+        t_host0 = time.perf_counter()
         start.record(stream)
         restores = run_steps(lbm, lat.h, args.steps, snapshot)
         end.record(stream)
         torch.cuda.synchronize()
+        t_host1 = time.perf_counter()
+    nvml.stop()
     if world > 1:
         torch.distributed.barrier()
     local_ms = start.elapsed_time(end)
@@ -935,6 +1231,13 @@ def main(argv=None):
     if not args.no_e2e:
         e2e = run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot)
     del snapshot
+    torch.cuda.empty_cache()
+    # the metric's second half: time to steady state of the batched columns (all ranks, each
+    # on its share of the columns)
+    steady = None if args.no_steady else time_to_steady(args, lbm, inputs, world, rank, torch)
+    precision = None
+    if rank == 0 and not args.no_precision:
+        precision = precision_report(lbm, rho0, Tc)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -953,9 +1256,11 @@ def main(argv=None):
         },
         "cpu_baseline": cpu_base,
         "e2e": e2e,
+        "time_to_steady": steady,
+        "precision": precision,
         "gpu_launches": args.steps + restores * (9 + 1),
         "restores": restores,
-        "clocks": clocks.summary(),
+        "clocks": nvml.summary(t_host0, t_host1) | {"warmup_and_timed": nvml.summary(), "nvidia_smi": smi.summary()},
         "status": status,
         "mass": mass,
     }

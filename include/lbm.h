@@ -223,7 +223,8 @@ typedef struct lbm_column {
 
 typedef struct lbm_batch lbm_batch;
 
-/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->thermal and p->wall must be 0;
+/* Create a batch. p: shared parameters (p->nx = column width <= 64; p->thermal must be 0; p->wall
+ * LBM_WALL_BOUNCE_BACK or LBM_WALL_ZOU_HE for every column (Zou-He: ny_c >= 3);
  * p->ny, p->T, p->gx, p->gy, p->gravity_form and p->workspace are ignored; p->rho_ref NaN means: each column's
  * mean rho0 in FP32, 0 in FP64). cols: ncols descriptors (host). rho0: the columns' initial
  * densities concatenated, column c holding nx * ny_c doubles [y][x], in host or device
@@ -279,6 +280,13 @@ int lbm_batch_autotune(lbm_batch* b, int steps, int* threads, double* us);
  * (+inf before the first check), status (LBM_OK or LBM_ENONPHYS). Returns LBM_ENONPHYS if
  * any column is non-physical. Synchronises. */
 int lbm_batch_results(const lbm_batch* b, int64_t* steps, double* residual, int* status);
+
+/* Per column (host array of ncols): device seconds that the persistent launches spent on the
+ * column - from the moment a CTA took it to the moment it stopped - summed over every run
+ * since lbm_batch_init (and carried over by lbm_batch_convert), from the GPU's global
+ * timer. The time to steady state of one column, where a run's duration is the makespan
+ * of all. Synchronises. */
+int lbm_batch_column_seconds(const lbm_batch* b, double* seconds);
 
 /* rho and u of every column as the next step evaluates them, concatenated like rho0, in
  * host or device memory per `where` (any pointer may be NULL). Synchronises. */
@@ -369,6 +377,46 @@ int lbm_mlp_gemm_enqueue(const uint16_t* A, int lda, const uint16_t* B, int ldb,
                          int K, int k_split, int accumulate, int* status, void* stream);
 /* Release a network. NULL is accepted. */
 int lbm_mlp_destroy(lbm_mlp* h);
+
+/* ---- slabs of one domain across GPUs (one process per GPU; the paper has a single domain)
+ *
+ * The domain nx x p->ny is cut into horizontal slabs of rows. Slab s holds its own rows
+ * [s->y0, s->y0 + s->ny_own) and LBM_SLAB_HALO ghost rows below and above in a caller-owned
+ * DEVICE buffer real[9][ny_own + 2 LBM_SLAB_HALO][nx] (deviations f_i - w_i rho_ref, order of
+ * Eq. VelocitySet; buffer row j is domain row y0 - LBM_SLAB_HALO + j). Two ghost rows are
+ * what one step needs: pull streaming (Eq. LBE) reads the row next to the slab, and the
+ * Shan-Chen force (Eq. ShanChenForce) on the slab's edge row needs psi of that row, which
+ * pulls from the next one. Walls (p->wall) act where the slab meets row 0 or row p->ny - 1;
+ * elsewhere the caller refreshes the ghost rows after every step with its neighbours' edge
+ * rows (2 rows x 9 planes each way) and sums the slabs' mass for <rho> of Eq. Gravity_2 over
+ * the whole domain (both by its own communication, e.g. NCCL). p->rho_ref must be the same
+ * on every slab (NaN means 0). These calls allocate nothing, are asynchronous on `stream`
+ * (a cudaStream_t, NULL = default) and take only device pointers. Isothermal only. A slab
+ * with a neighbour needs ny_own >= LBM_SLAB_HALO. Errors: LBM_EINVAL, LBM_ECUDA. */
+#define LBM_SLAB_HALO 2
+typedef struct lbm_slab {
+  int32_t y0;       /* first own row of the domain */
+  int32_t ny_own;   /* own rows */
+  int32_t reserved; /* must be 0 */
+  int32_t reserved2;
+} lbm_slab;
+
+/* Number of FP64 partial sums (`part` below) a slab step writes. */
+int lbm_slab_partials(const lbm_params* p, const lbm_slab* s, int* count);
+/* Own rows of f = the rest equilibrium of rho0 (ny_own x nx doubles [y][x], device); ghost
+ * rows untouched. */
+int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, void* f, void* stream);
+/* mass[0] = sum of the stored deviations over the own rows of f (device; part: scratch of
+ * lbm_slab_partials doubles). Summed over all slabs this is sum(rho - rho_ref) of the domain. */
+int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, double* mass, void* stream);
+/* One time step of the own rows, f_out = step(f_in) (distinct buffers; f_in's ghost rows must
+ * hold the neighbours' rows of the same state). mass_in: device double = the domain-wide sum
+ * of lbm_slab_mass / mass_out over all slabs for f_in (read for Eq. Gravity_2 only, may be
+ * NULL otherwise). Writes part (lbm_slab_partials doubles) and mass_out[0] = this slab's mass
+ * of f_out. status: device int the kernel ORs LBM status bits into (1: non-physical, 2: a
+ * bounded wait timed out); the caller zeroes it and reads it after the stream completes. */
+int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* mass_in,
+                  double* part, double* mass_out, int* status, void* stream);
 
 /* ---- one step without device allocation (this entry point has no counterpart in the paper)
  *

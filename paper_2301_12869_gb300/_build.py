@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "liblbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_thermal.cu", "lbm_mlp.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_thermal.cu", "lbm_mlp.cu", "lbm_slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -177,6 +177,11 @@ int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int
   long nstrips = std::max(1L, std::min<long>(p.ny, target / t->nbands));
   t->strip_h = int((p.ny + nstrips - 1) / nstrips);
   t->nstrips = (p.ny + t->strip_h - 1) / t->strip_h;
+  t->y_begin = 0;
+  t->y_end = p.ny;
+  t->ylo = 0;
+  t->yhi = p.ny - 1;
+  t->n_total = double(p.nx) * double(p.ny);
   return LBM_OK;
 }
 

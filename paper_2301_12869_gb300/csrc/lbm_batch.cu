@@ -70,7 +70,15 @@ struct BatchArgs {
   double* rho_out;  // MODE_MOMENTS outputs, concatenated like rho0
   double* ux_out;
   double* uy_out;
+  long long* col_ns;  // per column: device nanoseconds its CTAs spent on it, summed over runs
+  int zh;             // Zou-He wet-node walls on rows 0 and ny - 1 (else halfway bounce-back)
 };
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 template <typename T>
 __device__ lbm::PhysT<T> column_phys(const BatchArgs& a, const BatchCol& c) {
@@ -278,6 +286,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
     __syncthreads();
     const int ci = s_col;
     if (ci >= a.ncols) break;
+    const long long t_start = global_ns();
     const int c = a.order[ci];
     const BatchCol col = a.cols[c];
     const int nx = a.nx, ny = col.ny, N = nx * ny;
@@ -346,6 +355,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
         const int x = n % nx, y = n / nx;
         T g[9];
         pull_col(cur, nx, ny, N, x, y, g);
+        if (a.zh && (y == 0 || y == ny - 1)) lbm::zou_he(g, y == 0, dmean, k);
         const T rho = k.rho_ref + lbm::sum9(g);
         psi_s[n] = lbm::psi_of<T>(rho, k, flag);
         if (save) rho_prev[n] = sum9_fp64(g);
@@ -360,6 +370,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
         const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
         T g[9];
         pull_col(cur, nx, ny, N, x, y, g);
+        if (a.zh && (y == 0 || y == ny - 1)) lbm::zou_he(g, y == 0, dmean, k);
         T Sx = lbm::cst<T>(0.0), Sy = lbm::cst<T>(0.0);
         if (y > 0 && y < ny - 1) {  // stencil w(1) = 1/3, w(2) = 1/12; zero on the wall rows
           const T* pc = psi_s + y * nx;
@@ -456,6 +467,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
       a.steps[c] += it;
       a.resid[c] = res;
       if (any) a.status[c] |= lbm::STATUS_NONPHYS;
+      a.col_ns[c] += global_ns() - t_start;
     }
   }
 }
@@ -521,6 +533,7 @@ struct lbm_batch {
   long long* steps_d = nullptr;
   double* resid_d = nullptr;
   int* status_d = nullptr;
+  long long* ns_d = nullptr;  // per column device nanoseconds, summed over runs
   int grid = 0;
   size_t smem = 0;
   cudaGraphExec_t graph = nullptr;
@@ -605,6 +618,8 @@ BatchArgs make_args(const lbm_batch* b) {
   a.steps = b->steps_d;
   a.resid = b->resid_d;
   a.status = b->status_d;
+  a.col_ns = b->ns_d;
+  a.zh = b->p.wall == LBM_WALL_ZOU_HE;
   return a;
 }
 
@@ -639,7 +654,7 @@ void free_batch(lbm_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (void* ptr : {(void*)b->cols_d, (void*)b->order_d, b->fA, b->fB, (void*)b->counter, (void*)b->run_d,
-                    (void*)b->steps_d, (void*)b->resid_d, (void*)b->status_d, b->snap})
+                    (void*)b->steps_d, (void*)b->resid_d, (void*)b->status_d, (void*)b->ns_d, b->snap})
     if (ptr) cudaFree(ptr);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -663,7 +678,6 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   int rc = lbm::validate_params(&q, err);
   if (rc) return bfail(rc, err);
   if (p->thermal) return bfail(LBM_EINVAL, "batched columns are isothermal (thermal must be 0)");
-  if (p->wall != LBM_WALL_BOUNCE_BACK) return bfail(LBM_EINVAL, "batched columns use bounce-back walls (wall must be 0)");
   if (p->nx > 64) return bfail(LBM_EINVAL, "batched columns are at most 64 nodes wide");
   if (rho0_where != LBM_HOST && rho0_where != LBM_DEVICE) return bfail(LBM_EINVAL, "rho0_where must be LBM_HOST or LBM_DEVICE");
   lbm_batch* b = new (std::nothrow) lbm_batch();
@@ -740,6 +754,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   alloc((void**)&b->steps_d, sizeof(long long) * ncols);
   alloc((void**)&b->resid_d, sizeof(double) * ncols);
   alloc((void**)&b->status_d, sizeof(int) * ncols);
+  alloc((void**)&b->ns_d, sizeof(long long) * ncols);
   if (e != cudaSuccess) return fail(LBM_ENOMEM, "device allocation for the batch failed");
   // tallest columns first (longest work first balances the work-stealing queue)
   std::vector<int> order(ncols);
@@ -751,6 +766,7 @@ int lbm_batch_init(const lbm_params* p, const lbm_column* cols, int ncols, const
   if (e == cudaSuccess) e = cudaMemsetAsync(b->steps_d, 0, sizeof(long long) * ncols, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->resid_d, inf.data(), sizeof(double) * ncols, cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->status_d, 0, sizeof(int) * ncols, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ns_d, 0, sizeof(long long) * ncols, b->stream);
   // rho0 on the device: a host rho0 is staged through the second buffer (8 bytes per node
   // fit in its 9 * sizeof(real) bytes per node)
   double* rho_d = const_cast<double*>(rho0);
@@ -925,6 +941,16 @@ int lbm_batch_results(const lbm_batch* b, int64_t* steps, double* residual, int*
   return bad ? bfail(LBM_ENONPHYS, "at least one column became non-physical") : LBM_OK;
 }
 
+int lbm_batch_column_seconds(const lbm_batch* b, double* seconds) {
+  if (!b || !seconds) return bfail(LBM_EINVAL, "batch and seconds must not be NULL");
+  std::vector<long long> ns(b->ncols);
+  cudaError_t e = cudaMemcpyAsync(ns.data(), b->ns_d, sizeof(long long) * b->ncols, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  for (int c = 0; c < b->ncols; ++c) seconds[c] = 1e-9 * double(ns[c]);
+  return LBM_OK;
+}
+
 int lbm_batch_moments(lbm_batch* b, double* rho, double* ux, double* uy, int where) {
   if (!b) return bfail(LBM_EINVAL, "batch is NULL");
   if (where != LBM_HOST && where != LBM_DEVICE) return bfail(LBM_EINVAL, "where must be LBM_HOST or LBM_DEVICE");
@@ -1009,6 +1035,7 @@ int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->steps_d, src->steps_d, sizeof(long long) * b->ncols, cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->ns_d, src->ns_d, sizeof(long long) * b->ncols, cudaMemcpyDeviceToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
       lbm_batch_destroy(b);

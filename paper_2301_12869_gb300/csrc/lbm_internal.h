@@ -28,12 +28,20 @@ struct StepPhys {
 };
 
 // Tiling of the fused step: CTA b covers band (b % nbands) of width band_w along x
-// and strip (b / nbands) of strip_h rows.
+// and strip (b / nbands) of strip_h rows, counted from row y_begin.
 struct StepTiling {
-  int nx, ny;
+  int nx, ny;                // buffer rows and columns (the state is real[9][ny][nx])
   int band_w, nbands, strip_h, nstrips;
   int threads, smem_bytes;
-  int variant;  // index into the kernel's tile variants (0 = default)
+  int variant;               // index into the kernel's tile variants (0 = default)
+  // Rows the step collides and writes: [y_begin, y_end). Rows ylo and yhi are the wall
+  // rows (halfway bounce-back beyond them, Zou-He on them, no Shan-Chen force there);
+  // a buffer row outside [ylo, yhi] is never read. A whole domain: 0, ny, 0, ny - 1. A
+  // slab of a larger domain with ghost rows: its own rows, and ylo / yhi at its own first /
+  // last row where it meets a wall, else at the buffer's edge (the ghost rows are read,
+  // not written).
+  int y_begin, y_end, ylo, yhi;
+  double n_total;            // nodes of the whole domain: <rho> = (sum of rho) / n_total
 };
 
 enum StepMode : int { MODE_STEP = 0, MODE_MOMENTS = 1 };

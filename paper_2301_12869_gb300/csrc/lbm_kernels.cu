@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   const int nx = tl.nx, ny = tl.ny;
   const int band = blockIdx.x % tl.nbands, strip = blockIdx.x / tl.nbands;
   const int xa = band * tl.band_w, xb = min(xa + tl.band_w, nx), w = xb - xa;
-  const int ya = strip * tl.strip_h, yb = min(ya + tl.strip_h, ny);
+  const int ya = tl.y_begin + strip * tl.strip_h, yb = min(ya + tl.strip_h, tl.y_end);
 
   // <rho> - rho_ref of Eq. Gravity_2: the previous step's partials, finished in a fixed order
   V dmean = cst<V>(0.0);
@@ -166,14 +166,14 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
       if (lane == 0) red[32] = s;
     }
     __syncthreads();
-    dmean = cst<V>(red[32] / (double(nx) * double(ny)));
+    dmean = cst<V>(red[32] / tl.n_total);
   }
   if (ya >= yb || w <= 0) {  // empty tile (uniform across the CTA)
     if (MODE == MODE_STEP && tid == 0) io.part_out[blockIdx.x] = 0.0;
     return;
   }
 
-  const int r_lo = max(ya - 1, 0), r_hi = min(yb, ny - 1);
+  const int r_lo = max(ya - 1, tl.ylo), r_hi = min(yb, tl.yhi);
   const int nrows = r_hi - r_lo + 1;
   const bool up = (strip & 1) == 0;
   auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
     for (int c = lane; c < 9 * npc; c += 32) {
       const int i = c / npc, pc = c - i * npc;
       int plane = i, row = q - cy_of(i);
-      if (row < 0 || row >= ny) {
+      if (row < tl.ylo || row > tl.yhi) {
         plane = opp_of(i);
         row = q;
       }
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
   auto collide_row = [&](int y, int s, auto full_band) {
     constexpr bool FULL = decltype(full_band)::value;  // w == BW: no per-node bounds checks
     const T* st = stage + size_t(s) * 9 * SW;
-    const bool lo_wall = (y == 0), hi_wall = (y == ny - 1);
+    const bool lo_wall = (y == tl.ylo), hi_wall = (y == tl.yhi);
     const bool interior = !lo_wall && !hi_wall;
     const T* pc = ring + (y & 3) * RW;
     const T* pn = ring + ((y + 1) & 3) * RW;
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
     if (ok) {
       // rho and psi of pulled row q for the band and one halo node on each side
       const T* st = stage + size_t(s) * 9 * SW;
-      const bool lo_wall = (q == 0), hi_wall = (q == ny - 1);
+      const bool lo_wall = (q == tl.ylo), hi_wall = (q == tl.yhi);
       T* pr = ring + (q & 3) * RW;
       auto psi_row = [&](auto full_band) {
         constexpr bool FULL = decltype(full_band)::value;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
   const int nx = tl.nx, ny = tl.ny;
   const int band = blockIdx.x % tl.nbands, strip = blockIdx.x / tl.nbands;
   const int xa = band * tl.band_w, xb = min(xa + tl.band_w, nx), w = xb - xa;
-  const int ya = strip * tl.strip_h, yb = min(ya + tl.strip_h, ny);
+  const int ya = tl.y_begin + strip * tl.strip_h, yb = min(ya + tl.strip_h, tl.y_end);
 
   V dmean = cst<V>(0.0);
   if (k.form == 2) {
@@ -461,14 +461,14 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       if (lane == 0) red[NWC + 1] = s;
     }
     __syncthreads();
-    dmean = cst<V>(red[NWC + 1] / (double(nx) * double(ny)));
+    dmean = cst<V>(red[NWC + 1] / tl.n_total);
   }
   if (ya >= yb || w <= 0) {
     if (MODE == MODE_STEP && tid == 0) io.part_out[blockIdx.x] = 0.0;
     return;
   }
 
-  const int r_lo = max(ya - 1, 0), r_hi = min(yb, ny - 1);
+  const int r_lo = max(ya - 1, tl.ylo), r_hi = min(yb, tl.yhi);
   const int nrows = r_hi - r_lo + 1;
   const bool up = (strip & 1) == 0;
   auto row_of = [&](int kk) { return up ? r_lo + kk : r_hi - kk; };
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
       for (int c = lane; c < 9 * npc; c += 32) {
         const int i = c / npc, pc = c - i * npc;
         int plane = i, row = q - cy_of(i);
-        if (row < 0 || row >= ny) {
+        if (row < tl.ylo || row > tl.yhi) {
           plane = opp_of(i);
           row = q;
         }
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     };
     // g: the pulled populations of row y, kept in registers since its psi pass
     auto collide = [&](int y, const V (&g)[9], const PsiRow& ps, const PsiRow& pc, const PsiRow& pn) {
-      const bool lo_wall = (y == 0), hi_wall = (y == ny - 1);
+      const bool lo_wall = (y == tl.ylo), hi_wall = (y == tl.yhi);
       V Sx = cst<V>(0.0), Sy = cst<V>(0.0);
       if (!lo_wall && !hi_wall) {  // Eq. ShanChenForce stencil: w(1) = 1/3, w(2) = 1/12
         // per row: west (psi(j-1), psi(j)), east (psi(j+1), psi(j+2)), centre (psi(j), psi(j+1))
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
         const size_t plane = size_t(ny) * nx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) *reinterpret_cast<V*>(fout + node + i * plane) = o[i];
-        acc.add9(o);
+        acc.add(sum9(o));  // the node pair's stored values, summed in FP32 first
       } else {
         if (io.rho_out) { io.rho_out[node] = lo(rho); io.rho_out[node + 1] = hi(rho); }
         if (io.ux_out) { io.ux_out[node] = lo(ux); io.ux_out[node + 1] = hi(ux); }
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
         break;
       }
       const T* st = stage + size_t(s) * 9 * SW;
-      const bool lo_wall = (q == 0), hi_wall = (q == ny - 1);
+      const bool lo_wall = (q == tl.ylo), hi_wall = (q == tl.yhi);
       V g[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = cst<V>(0.0);
@@ -896,6 +896,7 @@ const VariantF kVariantsF[] = {
     make_p<512, 4, 2>(),     // two pairs per thread, 4 warps, 83 KB shared
     make_ws<4, 6, 3>(),      // barrier-free, 6 stages, 57 KB
     make_ws<2, 6, 6>(),      // barrier-free, 2 consumer warps, 29 KB
+    make_ws<8, 3, 3>(),      // barrier-free, 8 consumer warps, 3 stages, 3 CTAs per SM (72 registers)
 };
 const VariantD kVariantsD[] = {
     make_d_ext<128, 1, 4>(),  // (+ thermal, Zou-He)

@@ -89,6 +89,9 @@ struct Acc<double> {
 };
 template <typename V>
 struct Acc {  // float or f2: two-sum (Knuth) pairs, error-free to FP32 x FP32 precision
+  // (add9 adds every value; the default FP32 step kernel adds each node's FP32 sum of its
+  // stored values once: a rounding of 2^-24 relative per node, which can add up coherently
+  // over identical nodes - at most ~1e-8 of <rho>, a force change of |g| 1e-8 <rho>)
   V hi[3] = {cst<V>(0.0), cst<V>(0.0), cst<V>(0.0)};
   V lo[3] = {cst<V>(0.0), cst<V>(0.0), cst<V>(0.0)};
   __device__ void add(V x, int c = 0) {

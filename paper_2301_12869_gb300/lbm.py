@@ -41,11 +41,11 @@ EXPORTS = (
     "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
     "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
-    "lbm_batch_convert", "lbm_batch_destroy",
+    "lbm_batch_convert", "lbm_batch_destroy", "lbm_batch_column_seconds",
     "lbm_batch_set_threads", "lbm_batch_autotune", "lbm_wait_bound_selftest",
     "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
     "lbm_mlp_predict", "lbm_mlp_features", "lbm_mlp_warm_start", "lbm_mlp_gemm", "lbm_mlp_gemm_enqueue",
-    "lbm_mlp_destroy",
+    "lbm_mlp_destroy", "lbm_slab_partials", "lbm_slab_init", "lbm_slab_mass", "lbm_slab_step",
 )
 
 MLP_WIDTH, MLP_INPUTS, MLP_IN_PAD = 128, 5, 16
@@ -73,6 +73,14 @@ class lbm_params(ctypes.Structure):
 class lbm_column(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int32), ("gravity_form", ctypes.c_int32), ("T", ctypes.c_double),
                 ("gx", ctypes.c_double), ("gy", ctypes.c_double)]
+
+
+class lbm_slab(ctypes.Structure):
+    _fields_ = [("y0", ctypes.c_int32), ("ny_own", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
+
+
+LBM_SLAB_HALO = 2
 
 
 class LbmError(RuntimeError):
@@ -128,6 +136,7 @@ def load(path: str = LIB_PATH):
         "lbm_batch_get_state": (i32, [vp, vp, i32]),
         "lbm_batch_convert": (i32, [vp, i32, P(vp)]),
         "lbm_batch_destroy": (i32, [vp]),
+        "lbm_batch_column_seconds": (i32, [vp, vp]),
         "lbm_mlp_create": (i32, [vp, i32, vp, P(vp)]),
         "lbm_mlp_set_params": (i32, [vp, vp]),
         "lbm_mlp_get_params": (i32, [vp, vp]),
@@ -139,6 +148,10 @@ def load(path: str = LIB_PATH):
         "lbm_mlp_gemm": (i32, [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp]),
         "lbm_mlp_gemm_enqueue": (i32, [vp, i32, vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp]),
         "lbm_mlp_destroy": (i32, [vp]),
+        "lbm_slab_partials": (i32, [P(lbm_params), P(lbm_slab), P(i32)]),
+        "lbm_slab_init": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp]),
+        "lbm_slab_mass": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, vp]),
+        "lbm_slab_step": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -318,6 +331,43 @@ def lbm_step_noalloc(p, f_in, f_out, stream=None):
     _check(load().lbm_step_noalloc(ctypes.byref(p), a_in, a_out, stream))
 
 
+def _dev(t, name):
+    """Device address of a contiguous torch CUDA tensor (slab calls take device pointers only)."""
+    if t is None:
+        return None
+    if not (hasattr(t, "data_ptr") and t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous torch CUDA tensor")
+    return t.data_ptr()
+
+
+def make_slab(y0, ny_own):
+    s = lbm_slab()
+    s.y0, s.ny_own = int(y0), int(ny_own)
+    return s
+
+
+def lbm_slab_partials(p, s):
+    n = ctypes.c_int()
+    _check(load().lbm_slab_partials(ctypes.byref(p), ctypes.byref(s), ctypes.byref(n)))
+    return n.value
+
+
+def lbm_slab_init(p, s, rho0, f, stream=None):
+    """Own rows of the slab buffer f = rest equilibrium of rho0 (ny_own x nx, device FP64)."""
+    _check(load().lbm_slab_init(ctypes.byref(p), ctypes.byref(s), _dev(rho0, "rho0"), _dev(f, "f"), stream))
+
+
+def lbm_slab_mass(p, s, f, part, mass, stream=None):
+    _check(load().lbm_slab_mass(ctypes.byref(p), ctypes.byref(s), _dev(f, "f"), _dev(part, "part"),
+                                _dev(mass, "mass"), stream))
+
+
+def lbm_slab_step(p, s, f_in, f_out, mass_in, part, mass_out, status, stream=None):
+    _check(load().lbm_slab_step(ctypes.byref(p), ctypes.byref(s), _dev(f_in, "f_in"), _dev(f_out, "f_out"),
+                                _dev(mass_in, "mass_in"), _dev(part, "part"), _dev(mass_out, "mass_out"),
+                                _dev(status, "status"), stream))
+
+
 def lbm_batch_init(p, columns, rho0, stream=None):
     """columns: sequence of dicts with ny, gravity_form (or form), T, gx, gy."""
     arr = (lbm_column * len(columns))()
@@ -408,6 +458,13 @@ def lbm_batch_results(b, ncols, check=True):
     if check and rc != LBM_ENONPHYS:
         _check(rc)
     return steps, res, status
+
+
+def lbm_batch_column_seconds(b, ncols):
+    """Per column: device seconds the persistent launches spent on it, summed over runs."""
+    sec = np.empty(ncols)
+    _check(load().lbm_batch_column_seconds(b, sec.ctypes.data))
+    return sec
 
 
 def lbm_batch_moments(b, rho=None, ux=None, uy=None):

@@ -57,7 +57,8 @@ def batch_params(precision, **kw):
 def oracle_column(col, p):
     return olbm.Params(nx=NX, ny=col["ny"], a=A, b=B, R=R, T=col["T"], G=p.G, sigma=p.sigma, tau_rho=p.tau_rho,
                        tau_e=p.tau_e, tau_varsigma=p.tau_varsigma, tau_j=p.tau_j, tau_q=p.tau_q, tau_nu=p.tau_nu,
-                       g=(col["gx"], col["gy"]), form=col["form"])
+                       g=(col["gx"], col["gy"]), form=col["form"],
+                       wall="zou-he" if p.wall == lbm.LBM_WALL_ZOU_HE else "bounce-back")
 
 
 def split_state(f_all, cols):
@@ -123,6 +124,87 @@ def test_tall_columns_match_oracle(precision, tol, threads):
         for col, g0, g1 in zip(cols, split_state(f0, cols), split_state(f1, cols)):
             want = olbm.run(g0, oracle_column(col, p), 32)
             assert np.max(np.abs(g1 - want)) <= tol, col
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("precision, steps, tol, taus", [
+    ("fp64", 7, 1e-14, {}),
+    ("fp64", 7, 1e-14, dict(tau_e=0.8, tau_varsigma=1.1, tau_q=1.2, tau_nu=0.7)),
+    ("fp32", 50, 1e-6 * math.sqrt(50) + 1e-6, {}),
+    ("dd", 7, 1e-12, {}),
+])
+def test_zou_he_columns_match_oracle(precision, steps, tol, taus):
+    """The paper's wet-node walls (Sec. III) in the batch kernel: every column against the
+    oracle's Zou-He column, both gravity forms, heights 8..64 (and one of 3 rows, the
+    smallest the closure allows)."""
+    cols, rhos = make_columns(13, seed=41)
+    cols[-1]["ny"] = 3
+    rhos[-1] = np.full((3, NX), 0.15)
+    p = batch_params(precision, wall=lbm.LBM_WALL_ZOU_HE, **taus)
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        total = sum(9 * NX * c["ny"] for c in cols)
+        f0, f1 = np.empty(total), np.empty(total)
+        lbm.lbm_batch_get_state(b, f0)
+        lbm.lbm_batch_run(b, 0.0, steps, check_every=1000)
+        lbm.lbm_batch_get_state(b, f1)
+        st, _, status = lbm.lbm_batch_results(b, len(cols))
+        assert np.all(st == steps) and np.all(status == 0)
+        for col, g0, g1 in zip(cols, split_state(f0, cols), split_state(f1, cols)):
+            want = olbm.run(g0, oracle_column(col, p), steps)
+            assert np.max(np.abs(g1 - want)) <= tol, col
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_zou_he_batch_column_equals_single_lattice_handle():
+    """Zou-He columns of a batch run to a residual target equal lbm_step on the same column
+    (FP64), and the batch's moments match the handle's."""
+    cols, rhos = make_columns(3, seed=43, heights=(40, 24))
+    p = batch_params("fp64", wall=lbm.LBM_WALL_ZOU_HE)
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_run(b, 0.0, 500, check_every=1000)
+        f = np.empty(sum(9 * NX * c["ny"] for c in cols))
+        lbm.lbm_batch_get_state(b, f)
+        rho_b = np.empty(sum(NX * c["ny"] for c in cols))
+        lbm.lbm_batch_moments(b, rho=rho_b)
+        off = 0
+        for col, rho0, g in zip(cols, rhos, split_state(f, cols)):
+            q = lbm.make_params(NX, col["ny"], col["T"], "fp64", a=A, form=col["form"], g=(col["gx"], col["gy"]),
+                                wall=lbm.LBM_WALL_ZOU_HE)
+            h = lbm.lbm_init(q, rho0)
+            lbm.lbm_step(h, 500)
+            fh = np.empty((9, col["ny"], NX))
+            lbm.lbm_get_state(h, fh)
+            rh = np.empty((col["ny"], NX))
+            lbm.lbm_moments(h, rh)
+            lbm.lbm_destroy(h)
+            assert np.max(np.abs(fh - g)) <= 1e-13
+            assert np.max(np.abs(rh.ravel() - rho_b[off:off + rh.size])) <= 1e-13
+            off += rh.size
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_column_seconds_bound_by_the_run():
+    """lbm_batch_column_seconds: every column's device time is positive, no longer than the
+    run that contains it, summed over runs and carried over by lbm_batch_convert."""
+    cols, rhos = make_columns(40, seed=47)
+    b = lbm.lbm_batch_init(batch_params("fp32"), cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        t1 = lbm.lbm_batch_run(b, 0.0, 300, check_every=100)
+        s1 = lbm.lbm_batch_column_seconds(b, len(cols))
+        assert np.all(s1 > 0) and np.all(s1 <= t1 * 1.001 + 1e-5)
+        t2 = lbm.lbm_batch_run(b, 0.0, 300, check_every=100)
+        s2 = lbm.lbm_batch_column_seconds(b, len(cols))
+        assert np.all(s2 > s1) and np.all(s2 - s1 <= t2 * 1.001 + 1e-5)
+        bc = lbm.lbm_batch_convert(b, lbm.LBM_FP64)
+        try:
+            assert np.array_equal(lbm.lbm_batch_column_seconds(bc, len(cols)), s2)
+        finally:
+            lbm.lbm_batch_destroy(bc)
     finally:
         lbm.lbm_batch_destroy(b)
 
