@@ -10,11 +10,15 @@ fused kernel). Metric: MLUPS (million lattice-node updates per second).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica
-of the domain (the single-domain workload has no independent partition): the
-JSON line reports the aggregate over ranks with the max-over-ranks time.
-``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
-slice of the same workload.
+With N > 1 (torchrun, one rank per GPU) the domain is cut into N slabs of rows,
+one per GPU (strong scaling): every step each rank runs the fused step on its rows,
+sums the domain's mass with the others (NCCL all-reduce, for <rho> of Eq.
+Gravity_2) and swaps two ghost rows with each neighbour (NCCL send / receive);
+``--partition replicas`` runs N independent copies instead. The time-to-steady
+block splits its columns over the ranks with no exchange. The JSON line reports
+the aggregate over ranks with the max-over-ranks time. ``--impl reference``
+times the FP64 CPU oracle on the host cores on a bounded slice of the same
+workload.
 """
 from __future__ import annotations
 
@@ -390,6 +394,76 @@ def precision_report(lbm, rho0, Tc, steps=PRECISION_STEPS, every=100):
             "max_abs_interface_error": max(abs(r["interface_error"]) for r in rows),
             "max_abs_rho_l_rel_error": max(abs(r["rho_l_rel_error"]) for r in rows),
             "max_abs_rho_v_rel_error": max(abs(r["rho_v_rel_error"]) for r in rows)}
+
+
+# ---------------------------------------------------------------- the domain as slabs (N GPUs)
+def run_slabs(args, torch, lbm, inputs, world, rank, local, rho0, Tc):
+    """The 1024 x 4096 domain cut into `world` slabs of rows, one per GPU (strong scaling:
+    the domain stays the same as N grows). Per step each rank runs the fused step on its
+    rows (lbm_slab_step), then sums the domain's mass over ranks (NCCL all-reduce of one
+    double, for <rho> of Eq. Gravity_2) and swaps 2 ghost rows x 9 planes with each
+    neighbour (NCCL send / receive). Returns (local ms, local node updates, restores,
+    per-step bytes exchanged, end-to-end dict or None)."""
+    from paper_2301_12869_gb300 import partition
+
+    rho_ref = float(rho0.mean()) if args.precision == "fp32" else 0.0
+    p = lbm.make_params(NX, NY, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY), rho_ref=rho_ref)
+    plan = partition.SlabPlan(NY, world)
+    sl = plan[rank]
+    if world > 1:
+        import torch.distributed as dist
+
+        comm = partition.TorchComm(dist)
+    else:
+        comm = partition.SingleComm()
+    own = np.ascontiguousarray(rho0[sl.y0:sl.y0 + sl.ny_own])
+    lat = partition.SlabLattice(p, sl, torch.from_numpy(own).cuda(), comm)
+    lat.step(args.warmup)
+    snap = lat.snapshot()
+    stream = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    done = restores = 0
+    while done < args.steps:
+        n = min(WINDOW, args.steps - done)
+        lat.step(n)
+        done += n
+        if done < args.steps:
+            lat.restore(snap)
+            restores += 1
+    end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    local_ms = start.elapsed_time(end)
+    status = lat.status_code()
+    del lat, snap
+    torch.cuda.empty_cache()
+    # end to end: this rank's rows of rho0 from pinned host memory, the slab's set-up and K
+    # steps, the domain's mass read back to the host
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(own.shape, dtype=torch.float64, pin_memory=True)
+        pinned.copy_(torch.from_numpy(own))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat = partition.SlabLattice(p, sl, pinned.cuda(non_blocking=True), comm)
+        lat.step(args.steps)
+        mass = float(lat.mass[lat.cur].item()) + rho_ref * NX * NY
+        t1 = time.perf_counter()
+        ms_e, units_e = aggregate((t1 - t0) * 1e3, float(NX * sl.ny_own) * args.steps, torch)
+        e2e = {"value": units_e / (ms_e / 1e3) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * NX * NY / args.steps,
+               "d2h_bytes_per_step": 8 * world / args.steps, "mass": mass,
+               "what": "each rank: its rows of rho0 from pinned host memory, slab set-up, K steps with the "
+                       "exchanges, the domain mass to the host; host clock, max over ranks"}
+        del lat
+    halo_bytes = 2 * 2 * partition.HALO * 9 * NX * (4 if args.precision == "fp32" else 8)
+    return local_ms, float(NX * sl.ny_own) * args.steps, restores, halo_bytes, e2e, status, sl
 
 
 # ---------------------------------------------------------------- batched columns
@@ -1103,6 +1177,9 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--partition", choices=["auto", "slabs", "replicas"], default="auto",
+                    help="N > 1: the domain as slabs, one per GPU (auto) or N independent replicas; "
+                         "slabs also runs at N = 1 (one slab = the whole domain)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
     ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling", "gemm", "small"],
@@ -1188,50 +1265,77 @@ def main(argv=None):
     p = lbm.make_params(NX, NY, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY))
     nodes = NX * NY
 
-    # ---- device-resident run (value)
-    lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
-    info = lbm.lbm_launch_info(lat.h)
-    nvml = NvmlClocks(local).start()  # clocks from before the warm-up to the end of the timed region
-    lat.step(args.warmup)
-    snapshot = torch.empty((9, NY, NX), dtype=torch.float64, device="cuda")
-    lbm.lbm_get_state(lat.h, snapshot)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as smi:
-        t_host0 = time.perf_counter()
-        start.record(stream)
-        restores = run_steps(lbm, lat.h, args.steps, snapshot)
-        end.record(stream)
-        torch.cuda.synchronize()
-        t_host1 = time.perf_counter()
-    nvml.stop()
-    if world > 1:
-        torch.distributed.barrier()
-    local_ms = start.elapsed_time(end)
-    status = lat.status()
-    ms, units = aggregate(local_ms, float(nodes) * args.steps, torch)
-    value = units / (ms / 1e3) / 1e6
-    # one fused-kernel launch per step, back to back; the restores are counted against it
-    kernel_s = local_ms / 1e3 / args.steps
-    alg_bytes = BYTES_PER_NODE[args.precision] * nodes
+    use_slabs = args.partition == "slabs" or (args.partition == "auto" and world > 1)
     peaks, peak_kind = measured_peaks()
-    achieved = alg_bytes / kernel_s / 1e9
-    mass = lat.reduce(lbm.LBM_REDUCE_MASS)[0]
-    lat.close()
-    del lat
-    torch.cuda.empty_cache()
-
-    # ---- end to end through the C ABI with host buffers (init from pinned host rho0,
-    #      K steps, moments and mass read back to host), library-allocated memory
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot)
-    del snapshot
-    torch.cuda.empty_cache()
+    if use_slabs:
+        # ---- the domain cut into slabs, one per GPU (strong scaling), NCCL exchanges per step
+        nvml = NvmlClocks(local).start()
+        with ClockSampler(local) as smi:
+            t_host0 = time.perf_counter()
+            local_ms, local_units, restores, halo_bytes, e2e, status, sl = run_slabs(
+                args, torch, lbm, inputs, world, rank, local, rho0, Tc)
+            t_host1 = time.perf_counter()
+        nvml.stop()
+        ms, units = aggregate(local_ms, local_units, torch)
+        value = units / (ms / 1e3) / 1e6
+        kernel_s = ms / 1e3 / args.steps  # the slowest rank's step, exchanges included
+        alg_bytes = BYTES_PER_NODE[args.precision] * NX * sl.ny_own
+        achieved = alg_bytes / kernel_s / 1e9
+        mass = e2e["mass"] if e2e else None
+        info = {"slab_rows_rank0": sl.ny_own, "ghost_rows_per_side": 2, "exchange_bytes_per_step_per_rank": halo_bytes,
+                "exchanges_per_step": "NCCL all-reduce of the mass (8 B) + send/receive of 2 ghost rows x 9 planes "
+                                      "with each neighbour"}
+        scaling, parallelism = "strong", f"y-slabs x{world}"
+        launches = 2 * args.steps  # slab step + its partial-sum kernel per step
+        kernel_name = "step_kernel_ws on the rank's slab (+ exchanges, per step)"
+        torch.cuda.empty_cache()
+    else:
+        # ---- device-resident run (value)
+        lat = lbm.Lattice(p, torch.from_numpy(rho0).cuda())
+        info = lbm.lbm_launch_info(lat.h)
+        nvml = NvmlClocks(local).start()  # clocks from before the warm-up to the end of the timed region
+        lat.step(args.warmup)
+        snapshot = torch.empty((9, NY, NX), dtype=torch.float64, device="cuda")
+        lbm.lbm_get_state(lat.h, snapshot)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as smi:
+            t_host0 = time.perf_counter()
+            start.record(stream)
+            restores = run_steps(lbm, lat.h, args.steps, snapshot)
+            end.record(stream)
+            torch.cuda.synchronize()
+            t_host1 = time.perf_counter()
+        nvml.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        local_ms = start.elapsed_time(end)
+        status = lat.status()
+        ms, units = aggregate(local_ms, float(nodes) * args.steps, torch)
+        value = units / (ms / 1e3) / 1e6
+        # one fused-kernel launch per step, back to back; the restores are counted against it
+        kernel_s = local_ms / 1e3 / args.steps
+        alg_bytes = BYTES_PER_NODE[args.precision] * nodes
+        achieved = alg_bytes / kernel_s / 1e9
+        mass = lat.reduce(lbm.LBM_REDUCE_MASS)[0]
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        # ---- end to end through the C ABI with host buffers (init from pinned host rho0,
+        #      K steps, rho and the mass read back to host)
+        e2e = None
+        if not args.no_e2e:
+            e2e = run_e2e(args, rho0, Tc, nodes, world, torch, lbm, snapshot)
+        del snapshot
+        torch.cuda.empty_cache()
+        scaling, parallelism = "weak", (f"replicas x{world}" if world > 1 else "single GPU")
+        launches = args.steps + restores * (9 + 1)
+        kernel_name = (f"step_kernel_ws<8 consumer warps, {info['stages']} stages>" if args.precision == "fp32"
+                       else "step_kernel<double, 128-node bands>")
     # the metric's second half: time to steady state of the batched columns (all ranks, each
     # on its share of the columns)
     steady = None if args.no_steady else time_to_steady(args, lbm, inputs, world, rank, torch)
@@ -1244,21 +1348,19 @@ def main(argv=None):
         return 0
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": scaling,
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": workload_config(args.precision) | {"launch": info, "replicas": world},
+        "config": workload_config(args.precision) | {"launch": info, "parallelism": parallelism},
         "roofline": {
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profile(args.precision),
-            "peak_kind": peak_kind, "kernel": (f"step_kernel_ws<8 consumer warps, {info['stages']} stages>" if args.precision == "fp32"
-                                                else "step_kernel<double, 128-node bands>"),
-            "algorithmic_bytes_per_launch": alg_bytes,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None if use_slabs else traffic_from_profile(args.precision),
+            "peak_kind": peak_kind, "kernel": kernel_name, "algorithmic_bytes_per_launch": alg_bytes,
         },
         "cpu_baseline": cpu_base,
         "e2e": e2e,
         "time_to_steady": steady,
         "precision": precision,
-        "gpu_launches": args.steps + restores * (9 + 1),
+        "gpu_launches": launches,
         "restores": restores,
         "clocks": nvml.summary(t_host0, t_host1) | {"warmup_and_timed": nvml.summary(), "nvidia_smi": smi.summary()},
         "status": status,

@@ -331,7 +331,7 @@ def lbm_step_noalloc(p, f_in, f_out, stream=None):
     _check(load().lbm_step_noalloc(ctypes.byref(p), a_in, a_out, stream))
 
 
-def _dev(t, name):
+def _slab_ptr(t, name):
     """Device address of a contiguous torch CUDA tensor (slab calls take device pointers only)."""
     if t is None:
         return None
@@ -354,18 +354,18 @@ def lbm_slab_partials(p, s):
 
 def lbm_slab_init(p, s, rho0, f, stream=None):
     """Own rows of the slab buffer f = rest equilibrium of rho0 (ny_own x nx, device FP64)."""
-    _check(load().lbm_slab_init(ctypes.byref(p), ctypes.byref(s), _dev(rho0, "rho0"), _dev(f, "f"), stream))
+    _check(load().lbm_slab_init(ctypes.byref(p), ctypes.byref(s), _slab_ptr(rho0, "rho0"), _slab_ptr(f, "f"), stream))
 
 
 def lbm_slab_mass(p, s, f, part, mass, stream=None):
-    _check(load().lbm_slab_mass(ctypes.byref(p), ctypes.byref(s), _dev(f, "f"), _dev(part, "part"),
-                                _dev(mass, "mass"), stream))
+    _check(load().lbm_slab_mass(ctypes.byref(p), ctypes.byref(s), _slab_ptr(f, "f"), _slab_ptr(part, "part"),
+                                _slab_ptr(mass, "mass"), stream))
 
 
 def lbm_slab_step(p, s, f_in, f_out, mass_in, part, mass_out, status, stream=None):
-    _check(load().lbm_slab_step(ctypes.byref(p), ctypes.byref(s), _dev(f_in, "f_in"), _dev(f_out, "f_out"),
-                                _dev(mass_in, "mass_in"), _dev(part, "part"), _dev(mass_out, "mass_out"),
-                                _dev(status, "status"), stream))
+    _check(load().lbm_slab_step(ctypes.byref(p), ctypes.byref(s), _slab_ptr(f_in, "f_in"), _slab_ptr(f_out, "f_out"),
+                                _slab_ptr(mass_in, "mass_in"), _slab_ptr(part, "part"), _slab_ptr(mass_out, "mass_out"),
+                                _slab_ptr(status, "status"), stream))
 
 
 def lbm_batch_init(p, columns, rho0, stream=None):

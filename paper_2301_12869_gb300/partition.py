@@ -215,3 +215,15 @@ class SlabLattice:
         if st & 1:
             return self._lbm.LBM_ENONPHYS
         return self._lbm.LBM_OK
+
+
+class SingleComm:
+    """The comm of a single rank (one slab = the whole domain): nothing to exchange."""
+
+    def exchange(self, sends):
+        if sends:
+            raise ValueError("a single rank has no neighbours")
+        return {}
+
+    def sum_(self, t):
+        return t

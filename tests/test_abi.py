@@ -112,3 +112,34 @@ def test_coexistence_rejects_supercritical(lib):
     _, Tc, _ = lbm.lbm_critical_point(0.25, 4.0, 1.0)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_coexistence(0.25, 4.0, 1.0, 1.01 * Tc)
+
+
+def test_binding_defines_each_name_once():
+    """A later `def` of the same name would silently replace an earlier one in the binding."""
+    import ast
+
+    for mod in ("lbm.py", "partition.py"):
+        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2301_12869_gb300", mod)
+        tree = ast.parse(open(path).read())
+        names = [n.name for n in tree.body if isinstance(n, (ast.FunctionDef, ast.ClassDef))]
+        dup = {n for n in names if names.count(n) > 1}
+        assert not dup, (mod, dup)
+
+
+def test_slab_calls_reach_the_library_without_a_gpu():
+    """The slab wrappers marshal their arguments and the library answers (no device here:
+    LBM_ECUDA from the device query, or the binding's own refusal of host tensors)."""
+    import torch
+
+    p = lbm.make_params(16, 10, 0.02, "fp64", a=0.25)
+    s = lbm.make_slab(0, 5)
+    try:
+        n = lbm.lbm_slab_partials(p, s)
+        assert n >= 1  # a machine with a GPU
+    except lbm.LbmError as exc:
+        assert exc.code == lbm.LBM_ECUDA
+    with pytest.raises(lbm.LbmError, match="outside"):
+        lbm.lbm_slab_partials(p, lbm.make_slab(8, 4))
+    f = torch.zeros((9, 9, 16), dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        lbm.lbm_slab_step(p, s, f, f, None, f, f, f)
