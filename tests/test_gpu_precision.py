@@ -38,7 +38,7 @@ def test_fp32_against_fp64_on_the_domain_workload():
     rep = bench.precision_report(lbm, rho0, Tc)
     for row in rep["samples"]:
         assert row["status_fp32"] == lbm.LBM_OK and row["status_fp64"] == lbm.LBM_OK
-    assert rep["max_abs_drho"] <= 1e-4
-    assert rep["max_abs_interface_error"] <= 1e-2
-    assert rep["max_abs_rho_l_rel_error"] <= 1e-5
-    assert rep["max_abs_rho_v_rel_error"] <= 1e-4
+    assert rep["max_abs_drho"] <= 1.5e-5                # measured 4.2e-6
+    assert rep["max_abs_interface_error"] <= 2e-4       # measured 4.5e-5 lattice units
+    assert rep["max_abs_rho_l_rel_error"] <= 2.5e-6     # measured 7.1e-7
+    assert rep["max_abs_rho_v_rel_error"] <= 2e-4       # measured 6.6e-5 (the vapour thins as it falls)
