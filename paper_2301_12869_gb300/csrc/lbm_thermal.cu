@@ -10,14 +10,11 @@
 // walls, T held at T_bot and T_top on the wall rows 0 and ny - 1 themselves. rho and u come
 // from the moments pass that follows each LBM step.
 //
-// One launch does the whole Heun step. A CTA owns a TX x TY tile of nodes and stages T, u
-// with a halo of two nodes in shared memory, and for the tile plus its one-node ring the
-// two coefficients of the right-hand side that depend on rho alone (kappa/(rho c_v) and
-// R Z(eta)/c_v: the rho of (dp/dT)_rho = rho R Z cancels against 1/(rho c_v)), each
-// evaluated once per node. Stage 1 (k1, T* = T + k1) runs on the tile plus its ring,
-// stage 2 (k2) on the tile, so no grid-wide barrier separates the stages. The new field
-// goes to a second buffer. rho and u come in the field's own precision (FP32 handles get
-// them as floats from the moments pass: FP64 conversions are slow on GB300).
+// One launch does the whole Heun step (heun_strip_kernel below): each warp walks a strip
+// of rows with the stencil's rows held in registers, computing k1 and T* = T + k1 one row
+// ahead of k2, so both Heun stages run in one pass without shared memory or CTA
+// barriers. rho and u come in the field's own precision (FP32 handles get them as floats
+// from the moments pass: FP64 conversions are slow on GB300).
 #include "lbm_internal.h"
 #include "lbm_physics.cuh"
 #include "lbm_ptx.cuh"
@@ -27,10 +24,6 @@
 namespace lbm {
 namespace {
 
-constexpr int TX = 32, TY = 16;
-constexpr int W2 = TX + 4, H2 = TY + 4;  // T, u, v: two-node halo
-constexpr int W1 = TX + 2, H1 = TY + 2;  // coefficients, T*, k1: one-node halo
-
 template <typename T>
 struct EnergyArgs {
   int nx, ny;
@@ -38,121 +31,127 @@ struct EnergyArgs {
   T R, b4, c_v, kappa, twoTbot, twoTtop;
 };
 
-// D2Q9 direction i: (cx, cy) in the order of Eq. VelocitySet
-__device__ __forceinline__ int cx_of(int i) { return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0); }
-
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// Right-hand side of the energy equation at the node whose T sits at Ts[c] (row stride sw)
-// and whose u, v sit at U[cu], V[cu] (row stride uw); ck = kappa/(rho c_v), cz = R Z/c_v.
+// ---- the strip kernel: one warp walks kStripRows rows of kOwn columns
+//
+// Lane l of a warp holds column x0 - 2 + l (x periodic); lanes 2 .. 29 own their column,
+// lanes 0, 1, 30, 31 are its halo. x neighbours come from the adjacent lanes by shuffles,
+// y neighbours from a window of rows in registers: walking up, input row q (T, u, v and
+// the two rho coefficients) is loaded, k1 and T* = T + k1 are formed for row q - 1, and
+// k2 and T_new = T + (k1 + k2)/2 for row q - 2. Lanes 1 .. 30 get valid k1 (their
+// neighbours are loaded), so the owned lanes 2 .. 29 have T* on both sides. Each input
+// value is loaded once per warp (plus the 4 halo lanes and 2 + 2 halo rows of the strip).
+constexpr int kOwn = 28;
+constexpr int kStripRows = 16;
+constexpr int kStripWarps = 8;  // warps per CTA: consecutive strips of the same columns
+
 template <typename T>
-__device__ __forceinline__ T rate(const T* Ts, int c, int sw, const T* U, const T* V, int cu, int uw, T ck, T cz) {
-  const T tc = Ts[c];
-  T gx = T(0), gy = T(0), lap = T(0), div = T(0);
-#pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    const int cx = cx_of(i), cy = cy_of(i);
-    const T w = T(w_of(i));
-    const T tn = Ts[c + cy * sw + cx];
-    gx += w * T(cx) * tn;
-    gy += w * T(cy) * tn;
-    lap += w * (tn - tc);
-    div += w * (T(cx) * U[cu + cy * uw + cx] + T(cy) * V[cu + cy * uw + cx]);
-  }
-  return -(U[cu] * (T(3) * gx) + V[cu] * (T(3) * gy)) + ck * (T(6) * lap) - tc * cz * (T(3) * div);
+struct Nb {  // a value at the lane's column and at its left and right neighbours
+  T c, l, r;
+};
+template <typename T>
+__device__ __forceinline__ Nb<T> nb(T v) {
+  return {v, __shfl_up_sync(0xffffffffu, v, 1), __shfl_down_sync(0xffffffffu, v, 1)};
+}
+template <typename T>
+__device__ __forceinline__ Nb<T> affine(T a, T s, const Nb<T>& v) {  // a + s v, pointwise
+  return {a + s * v.c, a + s * v.l, a + s * v.r};
+}
+
+// Right-hand side of Eq. Energy_Equation at the lane's node of row r from T on rows
+// r-1 (ts), r (tc), r+1 (tn), u, v on the same rows and the node's coefficients: the
+// D2Q9-weighted differences with w = 1/9 (axes) and 1/36 (diagonals).
+template <typename T>
+__device__ __forceinline__ T rate_nb(const Nb<T>& ts, const Nb<T>& tc, const Nb<T>& tn, const Nb<T>& us,
+                                     const Nb<T>& uc, const Nb<T>& un, const Nb<T>& vs, const Nb<T>& vc,
+                                     const Nb<T>& vn, T ck, T cz) {
+  const T w1 = T(1.0 / 9.0), w2 = T(1.0 / 36.0);
+  const T gx = w1 * (tc.r - tc.l) + w2 * ((tn.r - tn.l) + (ts.r - ts.l));
+  const T gy = w1 * (tn.c - ts.c) + w2 * ((tn.r + tn.l) - (ts.r + ts.l));
+  const T lap = w1 * ((tc.r + tc.l) + (tn.c + ts.c)) + w2 * ((tn.r + tn.l) + (ts.r + ts.l)) - T(5.0 / 9.0) * tc.c;
+  const T div = w1 * ((uc.r - uc.l) + (vn.c - vs.c)) + w2 * (((un.r - un.l) + (us.r - us.l)) + ((vn.r + vn.l) - (vs.r + vs.l)));
+  return -(uc.c * (T(3) * gx) + vc.c * (T(3) * gy)) + ck * (T(6) * lap) - tc.c * cz * (T(3) * div);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TX * TY) heun_kernel(const EnergyArgs<T> a, const T* __restrict__ rho,
-                                                      const T* __restrict__ ux, const T* __restrict__ uy,
-                                                      const T* __restrict__ Tin, T* __restrict__ Tout) {
-  __shared__ T sT[H2 * W2], sU[H2 * W2], sV[H2 * W2];
-  __shared__ T sK[H1 * W1], sZ[H1 * W1], sS[H1 * W1], sk1[H1 * W1];  // kappa/(rho c_v), R Z/c_v, T*, k1
+__global__ void __launch_bounds__(32 * kStripWarps) heun_strip_kernel(const EnergyArgs<T> a, const T* __restrict__ rho,
+                                                                      const T* __restrict__ ux, const T* __restrict__ uy,
+                                                                      const T* __restrict__ Tin, T* __restrict__ Tout) {
   griddep_wait();  // launched as a dependent of the moments pass: rho, u are complete
   griddep_launch_dependents();
-  const int nx = a.nx, ny = a.ny;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-  // x in [x0 - 2, x0 + TX + 1]: one conditional shift unless the lattice is narrower than that
-  const bool wide = nx >= W2;
-  auto wrap = [nx, wide](int x) {
-    if (wide) return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  const int nx = a.nx, ny = a.ny, lane = threadIdx.x;
+  const int x0 = blockIdx.x * kOwn;
+  int x = x0 - 2 + lane;  // periodic; a narrow lattice wraps more than once
+  if (nx >= 32) {
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  } else {
     x %= nx;
-    return x < 0 ? x + nx : x;
-  };
-  const T inv_cv = recip(a.c_v);
-  const int x0 = blockIdx.x * TX;
-  for (int y0 = blockIdx.y * TY; y0 < ny; y0 += gridDim.y * TY) {
-    // T, u, v on rows y0-2 .. y0+TY+1: ghost rows -1 and ny by the wall rules, rows beyond
-    // them are never read
-    for (int k = tid; k < H2 * W2; k += TX * TY) {
-      const int r = k / W2, y = y0 - 2 + r, x = wrap(x0 - 2 + (k - r * W2));
-      T t = T(0), u = T(0), v = T(0);
-      if (y >= 0 && y < ny) {
-        const size_t n = size_t(y) * nx + x;
-        t = Tin[n];
-        u = ux[n];
-        v = uy[n];
-      } else if (y == -1 || y == ny) {
-        const size_t n = size_t(y < 0 ? 0 : ny - 1) * nx + x;
-        t = (y < 0 ? a.twoTbot : a.twoTtop) - Tin[n];
-        u = -ux[n];
-        v = -uy[n];
-      }
-      sT[k] = t;
-      sU[k] = u;
-      sV[k] = v;
-    }
-    // the rho-dependent coefficients on the tile and its ring (real rows)
-    for (int k = tid; k < H1 * W1; k += TX * TY) {
-      const int r = k / W1, y = y0 - 1 + r, x = wrap(x0 - 1 + (k - r * W1));
-      T ck = T(0), cz = T(0);
-      if (y >= 0 && y < ny) {
-        const T rh = rho[size_t(y) * nx + x];
+    if (x < 0) x += nx;
+  }
+  const bool own = lane >= 2 && lane < 2 + kOwn && x0 + lane - 2 < nx;
+  const int ya = (blockIdx.y * kStripWarps + threadIdx.y) * kStripRows;
+  if (ya >= ny) return;  // uniform over the warp
+  const int yb = min(ya + kStripRows, ny);
+  const bool walls = a.wall_nodes != 0;
+  const T inv_cv = recip(a.c_v), zero = T(0), half = T(0.5);
+  // windows (row index relative to the input row q of the current iteration)
+  Nb<T> t0{}, t1{}, t2{};            // T rows q-2, q-1, q
+  Nb<T> u0{}, u1{}, u2{}, u3{};      // u rows q-3 .. q
+  Nb<T> v0{}, v1{}, v2{}, v3{};      // v rows q-3 .. q
+  Nb<T> s0{}, s1{}, s2{};            // T* rows q-3, q-2, q-1
+  T ckA = zero, czA = zero, ckB = zero, czB = zero, ckC = zero, czC = zero;  // coefficients, rows q-2, q-1, q
+  T k1a = zero, k1b = zero;          // k1 of rows q-2 (a) and q-1 (b)
+  for (int q = ya - 2; q <= yb + 1; ++q) {
+    // ---- input row q: T, u, v with the wall ghosts, and the rho coefficients
+    T tq = zero, uq = zero, vq = zero, ckq = zero, czq = zero;
+    const bool real = q >= 0 && q < ny;
+    const bool ghost = !walls && (q == -1 || q == ny);
+    if (real || ghost) {
+      const size_t n = size_t(real ? q : (q < 0 ? 0 : ny - 1)) * nx + x;
+      tq = Tin[n];
+      uq = ux[n];
+      vq = uy[n];
+      if (ghost) {  // T(-1) = 2 T_bot - T(0), u(-1) = -u(0); likewise above the top row
+        tq = (q < 0 ? a.twoTbot : a.twoTtop) - tq;
+        uq = -uq;
+        vq = -vq;
+      } else {
+        const T rh = rho[n];
         const T eta = a.b4 * rh;
         const T om = T(1) - eta;
-        ck = a.kappa * recip(rh * a.c_v);
-        cz = a.R * (T(1) + eta * (T(1) + eta * (T(1) - eta))) * recip(om * om * om) * inv_cv;
-      }
-      sK[k] = ck;
-      sZ[k] = cz;
-    }
-    __syncthreads();
-
-    // stage 1 on the tile and its ring (real rows only): T* = T + k1
-    for (int k = tid; k < H1 * W1; k += TX * TY) {
-      const int r = k / W1, c = k - r * W1, y = y0 - 1 + r;
-      const int c2 = (r + 1) * W2 + (c + 1);
-      if (y >= 0 && y < ny) {
-        const T k1 = (a.wall_nodes && (y == 0 || y == ny - 1)) ? T(0) : rate(sT, c2, W2, sU, sV, c2, W2, sK[k], sZ[k]);
-        sk1[k] = k1;
-        sS[k] = sT[c2] + k1;
+        ckq = a.kappa * recip(rh * a.c_v);
+        czq = a.R * (T(1) + eta * (T(1) + eta * (T(1) - eta))) * recip(om * om * om) * inv_cv;
       }
     }
-    __syncthreads();
-    // ghost rows of T* from its first and last rows
-    for (int k = tid; k < H1 * W1; k += TX * TY) {
-      const int r = k / W1, y = y0 - 1 + r;
-      if (y == -1 && !a.wall_nodes) sS[k] = a.twoTbot - sS[k + W1];
-      if (y == ny && !a.wall_nodes) sS[k] = a.twoTtop - sS[k - W1];
-    }
-    __syncthreads();
-
-    // stage 2 on the tile: T_new = T + (k1 + k2)/2
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    if (x < nx && y < ny) {
-      const int c1 = (threadIdx.y + 1) * W1 + (threadIdx.x + 1);
-      const int c2 = (threadIdx.y + 2) * W2 + (threadIdx.x + 2);
-      const T t = sT[c2];
-      const T k1 = sk1[c1];
-      if (a.wall_nodes && (y == 0 || y == ny - 1)) {
-        Tout[size_t(y) * nx + x] = T(0.5) * (y == 0 ? a.twoTbot : a.twoTtop);  // wall node: T_bot / T_top
+    t0 = t1; t1 = t2; t2 = nb(tq);
+    u0 = u1; u1 = u2; u2 = u3; u3 = nb(uq);
+    v0 = v1; v1 = v2; v2 = v3; v3 = nb(vq);
+    ckA = ckB; czA = czB; ckB = ckC; czB = czC; ckC = ckq; czC = czq;
+    // ---- k1 and T* of row r1 = q - 1 (rows r1-1, r1, r1+1 are t0, t1, t2)
+    const int r1 = q - 1;
+    T k1 = zero;
+    if (r1 >= 0 && r1 < ny && !(walls && (r1 == 0 || r1 == ny - 1)))
+      k1 = rate_nb(t0, t1, t2, u1, u2, u3, v1, v2, v3, ckB, czB);
+    s0 = s1; s1 = s2;
+    s2 = nb(t1.c + k1);
+    if (!walls && r1 == 0) s1 = affine(a.twoTbot, T(-1), s2);     // T*(-1) = 2 T_bot - T*(0)
+    if (!walls && r1 == ny) s2 = affine(a.twoTtop, T(-1), s1);    // T*(ny) = 2 T_top - T*(ny-1)
+    k1a = k1b;
+    k1b = k1;
+    // ---- k2 and T_new of row r2 = q - 2 (T* rows r2-1 .. r2+1 are s0, s1, s2)
+    const int r2 = q - 2;
+    if (r2 >= ya && r2 < yb && own) {
+      T tn;
+      if (walls && (r2 == 0 || r2 == ny - 1)) {
+        tn = half * (r2 == 0 ? a.twoTbot : a.twoTtop);  // wall node: T_bot / T_top
       } else {
-        const T k2 = rate(sS, c1, W1, sU, sV, c2, W2, sK[c1], sZ[c1]);
-        Tout[size_t(y) * nx + x] = t + T(0.5) * (k1 + k2);
+        const T k2 = rate_nb(s0, s1, s2, u0, u1, u2, v0, v1, v2, ckA, czA);
+        tn = t0.c + half * (k1a + k2);
       }
+      Tout[size_t(r2) * nx + x] = tn;
     }
-    __syncthreads();  // the next tile of this CTA overwrites the shared arrays
   }
 }
 
@@ -174,16 +173,17 @@ unsigned rows_grid(int rows) { return unsigned(rows < 65535 ? rows : 65535); }
 cudaError_t launch_energy_step(int precision, int nx, int ny, int wall_nodes, double R, double b, double c_v,
                                double kappa, double T_bot, double T_top, const void* rho, const void* ux,
                                const void* uy, const void* Tin, void* Tout, cudaStream_t stream) {
-  const dim3 grid((nx + TX - 1) / TX, rows_grid((ny + TY - 1) / TY)), block(TX, TY);
+  const int strips = (ny + kStripRows - 1) / kStripRows;
+  const dim3 grid((nx + kOwn - 1) / kOwn, (strips + kStripWarps - 1) / kStripWarps), block(32, kStripWarps);
   if (precision == 1) {
     const EnergyArgs<float> a{nx, ny, wall_nodes, float(R), float(b / 4.0), float(c_v), float(kappa),
                               float(2.0 * T_bot), float(2.0 * T_top)};
-    return launch_dependent(heun_kernel<float>, grid, block, 0, stream, a, static_cast<const float*>(rho),
+    return launch_dependent(heun_strip_kernel<float>, grid, block, 0, stream, a, static_cast<const float*>(rho),
                             static_cast<const float*>(ux), static_cast<const float*>(uy),
                             static_cast<const float*>(Tin), static_cast<float*>(Tout));
   } else {
     const EnergyArgs<double> a{nx, ny, wall_nodes, R, b / 4.0, c_v, kappa, 2.0 * T_bot, 2.0 * T_top};
-    return launch_dependent(heun_kernel<double>, grid, block, 0, stream, a, static_cast<const double*>(rho),
+    return launch_dependent(heun_strip_kernel<double>, grid, block, 0, stream, a, static_cast<const double*>(rho),
                             static_cast<const double*>(ux), static_cast<const double*>(uy),
                             static_cast<const double*>(Tin), static_cast<double*>(Tout));
   }
