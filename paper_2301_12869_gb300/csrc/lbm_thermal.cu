@@ -103,22 +103,45 @@ __global__ void __launch_bounds__(32 * kStripWarps) heun_strip_kernel(const Ener
   Nb<T> s0{}, s1{}, s2{};            // T* rows q-3, q-2, q-1
   T ckA = zero, czA = zero, ckB = zero, czB = zero, ckC = zero, czC = zero;  // coefficients, rows q-2, q-1, q
   T k1a = zero, k1b = zero;          // k1 of rows q-2 (a) and q-1 (b)
-  for (int q = ya - 2; q <= yb + 1; ++q) {
+  // Input rows are loaded kAhead iterations before they are used (a ring of raw T, u, v,
+  // rho in registers), so the global-load latency overlaps the work of the rows before.
+  // A row outside the strip's range, or beyond the walls, loads nothing.
+  const int q_first = ya - 2, q_last = yb + 1;
+  auto fetch = [&](int q, T& t, T& u, T& v, T& r) {
+    const bool real = q >= 0 && q < ny;
+    const bool ghost = !walls && (q == -1 || q == ny);
+    t = u = v = r = zero;
+    if (q <= q_last && (real || ghost)) {
+      const size_t n = size_t(real ? q : (q < 0 ? 0 : ny - 1)) * nx + x;
+      t = Tin[n];
+      u = ux[n];
+      v = uy[n];
+      if (real) r = rho[n];
+    }
+  };
+  T pt0, pu0, pv0, pr0, pt1, pu1, pv1, pr1, pt2, pu2, pv2, pr2, pt3, pu3, pv3, pr3;  // rows q .. q + 3
+  fetch(q_first, pt0, pu0, pv0, pr0);
+  fetch(q_first + 1, pt1, pu1, pv1, pr1);
+  fetch(q_first + 2, pt2, pu2, pv2, pr2);
+  fetch(q_first + 3, pt3, pu3, pv3, pr3);
+  for (int q = q_first; q <= q_last; ++q) {
     // ---- input row q: T, u, v with the wall ghosts, and the rho coefficients
-    T tq = zero, uq = zero, vq = zero, ckq = zero, czq = zero;
+    T tq = pt0, uq = pu0, vq = pv0;
+    const T rq = pr0;
+    pt0 = pt1; pu0 = pu1; pv0 = pv1; pr0 = pr1;
+    pt1 = pt2; pu1 = pu2; pv1 = pv2; pr1 = pr2;
+    pt2 = pt3; pu2 = pu3; pv2 = pv3; pr2 = pr3;
+    fetch(q + 4, pt3, pu3, pv3, pr3);
+    T ckq = zero, czq = zero;
     const bool real = q >= 0 && q < ny;
     const bool ghost = !walls && (q == -1 || q == ny);
     if (real || ghost) {
-      const size_t n = size_t(real ? q : (q < 0 ? 0 : ny - 1)) * nx + x;
-      tq = Tin[n];
-      uq = ux[n];
-      vq = uy[n];
       if (ghost) {  // T(-1) = 2 T_bot - T(0), u(-1) = -u(0); likewise above the top row
         tq = (q < 0 ? a.twoTbot : a.twoTtop) - tq;
         uq = -uq;
         vq = -vq;
       } else {
-        const T rh = rho[n];
+        const T rh = rq;
         const T eta = a.b4 * rh;
         const T om = T(1) - eta;
         ckq = a.kappa * recip(rh * a.c_v);
