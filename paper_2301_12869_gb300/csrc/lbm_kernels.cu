@@ -897,7 +897,6 @@ const VariantF kVariantsF[] = {
     make_ws<4, 6, 3>(),      // barrier-free, 6 stages, 57 KB
     make_ws<2, 6, 6>(),      // barrier-free, 2 consumer warps, 29 KB
     make_ws<8, 3, 3>(),      // barrier-free, 8 consumer warps, 3 stages, 3 CTAs per SM (72 registers)
-    make_ws<8, 4, 2>(),      // barrier-free, 8 consumer warps, 4 stages, 75 KB
 };
 const VariantD kVariantsD[] = {
     make_d_ext<128, 1, 4>(),  // (+ thermal, Zou-He)

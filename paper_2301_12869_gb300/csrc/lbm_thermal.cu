@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(32 * kStripWarps) heun_strip_kernel(const Ener
   Nb<T> s0{}, s1{}, s2{};            // T* rows q-3, q-2, q-1
   T ckA = zero, czA = zero, ckB = zero, czB = zero, ckC = zero, czC = zero;  // coefficients, rows q-2, q-1, q
   T k1a = zero, k1b = zero;          // k1 of rows q-2 (a) and q-1 (b)
-  // Input rows are loaded kAhead iterations before they are used (a ring of raw T, u, v,
+  // Input rows are loaded four iterations before they are used (a ring of raw T, u, v,
   // rho in registers), so the global-load latency overlaps the work of the rows before.
   // A row outside the strip's range, or beyond the walls, loads nothing.
   const int q_first = ya - 2, q_last = yb + 1;
