@@ -454,16 +454,7 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
   const int xa = band * tl.band_w, xb = min(xa + tl.band_w, nx), w = xb - xa;
   const int ya = tl.y_begin + strip * tl.strip_h, yb = min(ya + tl.strip_h, tl.y_end);
 
-  V dmean = cst<V>(0.0);
-  if (k.form == 2) {
-    if (warp == 0) {
-      const double s = warp_sum_partials(io.part_in, io.npart_in);
-      if (lane == 0) red[NWC + 1] = s;
-    }
-    __syncthreads();
-    dmean = cst<V>(red[NWC + 1] / tl.n_total);
-  }
-  if (ya >= yb || w <= 0) {
+  if (ya >= yb || w <= 0) {  // empty tile (uniform across the CTA)
     if (MODE == MODE_STEP && tid == 0) io.part_out[blockIdx.x] = 0.0;
     return;
   }
@@ -486,8 +477,9 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
   __syncthreads();
 
   int flag = 0;
+  V dmean = cst<V>(0.0);  // <rho> - rho_ref of Eq. Gravity_2 (consumer warps only)
   if (warp == NWC) {
-    // ---------------- producer warp
+    // ---------------- producer warp (it starts copying at once: it does not need <rho>)
     int npc, g0, s0, n0, g1 = 0, s1 = 0, n1 = 0, g2 = 0, s2 = 0, n2 = 0;
     if (xa >= H) {
       g0 = xa - H; s0 = 0; n0 = w + H; npc = 1;
@@ -535,6 +527,16 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
         (void)mbar_wait_bounded(&full[q % S], uint32_t((q / S) & 1), kWaitCycles / 8);
     }
   } else {
+    // <rho> from the previous step's partials, finished in a fixed order by consumer warp 0
+    // while the producer's first copies are in flight; named barrier 1 spans the consumers
+    if (k.form == 2) {
+      if (warp == 0) {
+        const double s = warp_sum_partials(io.part_in, io.npart_in);
+        if (lane == 0) red[NWC + 1] = s;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(NWC * 32) : "memory");
+      dmean = cst<V>(red[NWC + 1] / tl.n_total);
+    }
     // ---------------- consumer warp: nodes j, j+1 of the band (x = xa + j - 1)
     const int j = 1 + 64 * warp + 2 * lane;
     const bool active = j <= w;  // w is a multiple of 4, so j + 1 <= w too
