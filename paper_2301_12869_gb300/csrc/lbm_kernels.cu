@@ -675,8 +675,11 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
     }
   }
 
-  if (__syncthreads_or(flag & STATUS_NONPHYS) && tid == 0) atomicOr(io.status, STATUS_NONPHYS);
-  if (__syncthreads_or(flag & STATUS_TIMEOUT) && tid == 0) atomicOr(io.status, STATUS_TIMEOUT);
+  // one barrier for both status bits; a warp with a bit set reports it (one atomic per warp)
+  if (__syncthreads_or(flag)) {
+    const int wf = __reduce_or_sync(0xffffffffu, flag);
+    if (lane == 0 && wf) atomicOr(io.status, wf);
+  }
   if (MODE == MODE_STEP && warp == 0) {
     const double t = warp_sum(lane < NWC ? red[lane] : 0.0);
     if (lane == 0) io.part_out[blockIdx.x] = t;
