@@ -421,6 +421,38 @@ def test_double_float_continuation_reaches_fp64_steady_states():
         lbm.lbm_batch_destroy(bdd)
 
 
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-13), ("fp32", 1e-6 * math.sqrt(30) + 1e-6), ("dd", 1e-11)])
+def test_stated_column_set_sampled(precision, tol):
+    """The time-to-steady block's column set as stated - 4096 seeded columns, H in {64, 128,
+    256, 512, 1024} - in its launch configuration (autotuned block size, extrapolation on for
+    FP32 and double-float as that block runs them): 30 steps of every column, then
+    sampled columns of every height against the oracle run on each column alone."""
+    import bench
+
+    cols, rho = bench.column_set(4096, bench.SEED, bench.STEADY_HEIGHTS, lbm, inputs)
+    cols = [dict(c, gx=0.0) for c in cols]
+    p = lbm.make_params(4, 8, 0.8 * T_C, precision, a=A, b=B, R=R)
+    b = lbm.lbm_batch_init(p, cols, rho)
+    try:
+        lbm.lbm_batch_autotune(b, 5)
+        if precision != "fp64":
+            lbm.lbm_batch_set_acceleration(b, bench.ACCEL_CHECKS)  # no snapshot within 30 steps
+        total = sum(9 * NX * c["ny"] for c in cols)
+        f0, f1 = np.empty(total), np.empty(total)
+        lbm.lbm_batch_get_state(b, f0)
+        lbm.lbm_batch_run(b, 0.0, 30, check_every=1000)
+        lbm.lbm_batch_get_state(b, f1)
+    finally:
+        lbm.lbm_batch_destroy(b)
+    g0s, g1s = split_state(f0, cols), split_state(f1, cols)
+    hs = np.array([c["ny"] for c in cols])
+    rng = np.random.default_rng(79)
+    picks = [int(rng.choice(np.nonzero(hs == H)[0])) for H in bench.STEADY_HEIGHTS for _ in range(2)]
+    for c in [0, len(cols) - 1] + picks:
+        want = olbm.run(g0s[c], oracle_column(cols[c], p), 30)
+        assert np.max(np.abs(g1s[c] - want)) <= tol, (c, cols[c]["ny"])
+
+
 @pytest.mark.parametrize("precision, tol", [("fp32", 1e-6 * math.sqrt(30) + 1e-6), ("dd", 1e-11)])
 def test_full_size_column_set_sampled(precision, tol):
     """The columns workload's 1024 seeded columns (H in {64, 128}) in its launch
