@@ -275,6 +275,175 @@ __global__ void __launch_bounds__(GT, 1)
   if (warp == 0) lbm::tmem_dealloc(tmem, BN);
 }
 
+// ------------------------------------------------------------------ fused forward pass
+// The whole network for 128-row tiles in one persistent kernel (inference: lbm_mlp_predict
+// and the warm start). The weights stay in shared memory for the CTA's lifetime (TMA, the
+// GEMM's 128-byte-swizzled K-major layout). The CTA runs two independent tile pipelines,
+// warps 0-3 and 4-7, each with its own activation buffer, TMEM accumulator (128 columns),
+// mbarrier and named barriers, so one group's MMAs overlap the other's epilogue. Per tile
+// the group's 128 threads (one row each) write their normalised bfloat16 inputs into the
+// A-operand buffer, one thread issues the layer's MMAs, and every thread reads its row
+// back (tcgen05.ld), adds the bias, applies SiLU and writes the bfloat16 activations
+// straight into the same A-operand buffer in the swizzled layout the next layer's
+// descriptor names (16-byte piece j of row r at piece position j ^ (r mod 8)). After the
+// third layer the output layer is a dot product with w4 in registers. Rounding points as
+// in the GEMM path: bfloat16 inputs, weights and H1, H2; FP32 accumulation, biases, H3
+// and output.
+constexpr int FF_THREADS = 256;                      // two groups of 4 warps
+constexpr int FF_BOX = BK * 128 * 2;                 // one 64-element x 128-row swizzled box: 16 KB
+constexpr int FF_W1 = 0;                             // W1 (K = 16, zero-filled to the box)
+constexpr int FF_W2 = FF_W1 + FF_BOX;                // W2: two K boxes
+constexpr int FF_W3 = FF_W2 + 2 * FF_BOX;            // W3: two K boxes
+constexpr int FF_H = FF_W3 + 2 * FF_BOX;             // per group: activations / inputs, two K boxes
+constexpr int FF_BAR = FF_H + 4 * FF_BOX;            // mbarriers, TMEM slot, error flag
+constexpr int FF_SMEM = FF_BAR + 64 + 1024;          // + alignment slack: 145 KB
+
+// 16-byte piece (8 bfloat16 values, k = 8 j .. 8 j + 7) of row r of a K-major operand held in
+// 128-byte-swizzled boxes of 64 K values
+__device__ __forceinline__ void ff_store8(uint8_t* base, int r, int j, const float (&v)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    w[i] = *reinterpret_cast<const uint32_t*>(&b);
+  }
+  uint8_t* dst = base + (j >> 3) * FF_BOX + r * 128 + (((j & 7) ^ (r & 7)) << 4);
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(lbm::smem_u32(dst)), "r"(w[0]), "r"(w[1]),
+               "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+
+// barrier among the 128 threads of group g (named barrier 1 + g) returning the AND of v
+__device__ __forceinline__ bool group_and(bool v, int g) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(uint32_t(v)), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(FF_THREADS, 1)
+    mlp_forward_kernel(const __grid_constant__ CUtensorMap mapW1, const __grid_constant__ CUtensorMap mapW2,
+                       const __grid_constant__ CUtensorMap mapW3, const float* __restrict__ P,
+                       const float* __restrict__ feat, long long n, float* __restrict__ y, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + FF_BAR);
+  uint64_t* mbars = wbar + 1;  // one per group
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int g = warp >> 2, r = tid & 127;  // group, and this thread's row within the tile
+  const long long ntiles = (n + 127) / 128;
+
+  if (tid == 0) {
+    lbm::mbar_init(wbar, 1);
+    lbm::mbar_init(&mbars[0], 1);
+    lbm::mbar_init(&mbars[1], 1);
+    lbm::fence_mbar_init();
+  }
+  if (warp == 0) {
+    lbm::tmem_alloc(tmem_slot, 256);
+    lbm::tmem_relinquish();
+  }
+  lbm::tc_fence_before();
+  __syncthreads();
+  lbm::tc_fence_after();
+  const uint32_t tmem = *tmem_slot + uint32_t(128 * g) + (uint32_t(32 * (warp & 3)) << 16);  // group columns, warp lanes
+  const uint32_t tmem_acc = *tmem_slot + uint32_t(128 * g);
+  uint8_t* sH = smem + FF_H + g * 2 * FF_BOX;
+  uint64_t* mbar = &mbars[g];
+  if (tid == 0) {  // the three weight matrices, once per CTA
+    mbar_expect_tx(wbar, uint32_t(5 * FF_BOX));
+    tma_load_2d(smem + FF_W1, &mapW1, 0, 0, wbar);
+    tma_load_2d(smem + FF_W2, &mapW2, 0, 0, wbar);
+    tma_load_2d(smem + FF_W2 + FF_BOX, &mapW2, BK, 0, wbar);
+    tma_load_2d(smem + FF_W3, &mapW3, 0, 0, wbar);
+    tma_load_2d(smem + FF_W3 + FF_BOX, &mapW3, BK, 0, wbar);
+  }
+  bool ok = __syncthreads_and(lbm::mbar_wait_bounded(wbar, 0u));
+  uint32_t uses = 0;  // completed phases of this group's mbarrier
+  // one layer: the group's A buffer is complete; one thread issues k_steps K = 16 MMAs of
+  // A (sH) and B (weights) into the group's accumulator and commits them to its mbarrier
+  auto mma_layer = [&](const uint8_t* sB, int k_steps) {
+    lbm::fence_proxy_async_smem();  // this group's st.shared of A -> visible to the tensor cores
+    lbm::tc_fence_before();
+    (void)group_and(true, g);
+    lbm::tc_fence_after();
+    if (r == 0) {
+      for (int j = 0; j < k_steps; ++j) {
+        const int off = (j >> 2) * FF_BOX + 32 * (j & 3);
+        lbm::tc_mma_f16(tmem_acc, smem_desc(sH + off), smem_desc(sB + off), kIdesc, j > 0 ? 1u : 0u);
+      }
+      lbm::tc_commit(mbar);
+    }
+    const bool done = lbm::mbar_wait_bounded(mbar, uses & 1u);
+    ++uses;
+    lbm::tc_fence_after();
+    return group_and(done, g);
+  };
+  for (long long t = 2LL * blockIdx.x + g; ok && t < ntiles; t += 2LL * gridDim.x) {
+    const long long m = t * 128 + r;  // this thread's row
+    {  // normalised inputs, bfloat16, K = 16 (5 used)
+      float a[8], b[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = b[j] = 0.0f;
+      if (m < n) {
+#pragma unroll
+        for (int j = 0; j < LBM_MLP_INPUTS; ++j) a[j] = (feat[m * LBM_MLP_INPUTS + j] - kCenter[j]) / kScale[j];
+      }
+      ff_store8(sH, r, 0, a);
+      ff_store8(sH, r, 1, b);
+    }
+    float out = __ldg(P + OFF_B4);
+#pragma unroll 1
+    for (int layer = 0; layer < 3; ++layer) {
+      const uint8_t* sB = smem + (layer == 0 ? FF_W1 : (layer == 1 ? FF_W2 : FF_W3));
+      if (!mma_layer(sB, layer == 0 ? 1 : 8)) {
+        ok = false;
+        break;
+      }
+      const float* bias = P + (layer == 0 ? OFF_B1 : (layer == 1 ? OFF_B2 : OFF_B3));
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {  // columns 32 cc .. 32 cc + 31 of this row
+        float v[32];
+        lbm::tmem_ld32(tmem + uint32_t(32 * cc), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = silu_f(v[i] + __ldg(bias + 32 * cc + i));
+        if (layer < 2) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float piece[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) piece[i] = v[8 * q + i];
+            ff_store8(sH, r, 4 * cc + q, piece);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) out = fmaf(v[i], __ldg(P + OFF_W4 + 32 * cc + i), out);
+        }
+      }
+      // every read of the accumulator is complete before the group's next MMAs overwrite it
+      lbm::tc_fence_before();
+    }
+    if (ok && m < n) y[m] = out;
+  }
+  if (!ok && r == 0) {
+    atomicOr(status, lbm::STATUS_TIMEOUT);
+    // the weight copies and this group's issued MMAs finish before the CTA goes (bounded)
+    (void)lbm::mbar_wait_bounded(wbar, 0u, kWaitCycles / 8);
+    lbm::tc_commit(mbar);
+    (void)lbm::mbar_wait_bounded(mbar, uses & 1u, kWaitCycles / 8);
+  }
+  lbm::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) lbm::tmem_dealloc(*tmem_slot, 256);
+}
+
 // ------------------------------------------------------------------ other kernels
 __device__ __forceinline__ uint64_t splitmix64(uint64_t counter, uint64_t seed) {
   uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
@@ -490,6 +659,8 @@ cudaError_t gemm_prepare() {
   for (const void* fn : {(const void*)gemm_kernel<EPI_STORE>, (const void*)gemm_kernel<EPI_ATOMIC>,
                          (const void*)gemm_kernel<EPI_FWD>, (const void*)gemm_kernel<EPI_BWD>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FF_SMEM);
   return e;
 }
 
@@ -802,13 +973,18 @@ int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y) {
   if (!h || !x || !y) return fail(LBM_EINVAL, "handle, x and y must not be NULL");
   if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
   if (!device_pointer(x) || !device_pointer(y)) return fail(LBM_EINVAL, "x and y must be device pointers");
-  for (long long first = 0; first < n; first += h->Bc) {
-    const int count = int(std::min<long long>(h->Bc, n - first));
-    int rc = gather(h, x, nullptr, n, first, count, false, 0, 0);
-    if (!rc) rc = run_pass(h, count, false);
-    if (rc) return rc;
-    MLP_CUDA(cudaMemcpyAsync(y + first, h->y, sizeof(float) * count, cudaMemcpyDeviceToDevice, h->stream));
-  }
+  if (n == 0) return LBM_OK;
+  // the fused forward kernel: one persistent CTA per SM at most, two 128-row tiles in flight each
+  CUtensorMap m1, m2, m3;
+  if (!make_map(&m1, h->W1, W, KIN, KIN) || !make_map(&m2, h->W2, W, W, W) || !make_map(&m3, h->W3, W, W, W))
+    return fail(LBM_ECUDA, "tensor maps of the weights");
+  int dev = 0, nsm = 0;
+  MLP_CUDA(cudaGetDevice(&dev));
+  MLP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const long long ntiles = (n + 127) / 128;
+  const int grid = int(std::min<long long>(nsm, (ntiles + 1) / 2));
+  mlp_forward_kernel<<<grid, FF_THREADS, FF_SMEM, h->stream>>>(m1, m2, m3, h->P, x, n, y, h->status);
+  MLP_CUDA(cudaGetLastError());
   return status_of(h);
 }
 

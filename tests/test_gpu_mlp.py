@@ -198,6 +198,33 @@ def test_prediction_matches_oracle():
         lbm.lbm_mlp_destroy(h)
 
 
+def test_fused_forward_over_many_tiles():
+    """lbm_mlp_predict runs the fused forward kernel: persistent CTAs with two 128-row tile
+    pipelines each. 303 tiles (the last one 77 rows) give every CTA several tiles and its
+    two groups different counts; sampled rows (the first and last tiles whole, 1500 random)
+    against the oracle in its bfloat16 mode, element-wise as above."""
+    import torch
+
+    P = params_for_test(5)
+    n = 128 * 302 + 77
+    raw, _ = features(n, 9)
+    h = lbm.lbm_mlp_create(lbm.mlp_pack(P), 256)
+    try:
+        Pf = lbm.mlp_unpack(lbm.lbm_mlp_get_params(h))
+        y = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+        lbm.lbm_mlp_predict(h, to_gpu(raw), y)
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))  # every row written
+        rng = np.random.default_rng(3)
+        rows = np.unique(np.concatenate([np.arange(128), np.arange(n - 77, n), rng.integers(0, n, 1500)]))
+        x = omlp.normalise(raw[rows].astype(np.float64)).astype(np.float32).astype(np.float64)
+        want, _ = omlp.forward(x, Pf, bf16=True)
+        _, aY = magnitudes(x, np.zeros(len(x)), Pf)
+        assert_elementwise(got[rows], want, aY, "fused forward")
+    finally:
+        lbm.lbm_mlp_destroy(h)
+
+
 def test_adam_steps_match_oracle():
     """Three training steps with the SplitMix64 minibatches of the input module: the
     parameters follow the oracle's Adam (bfloat16 mode) to a small fraction of lr."""
