@@ -20,6 +20,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 namespace {
 
@@ -55,7 +56,23 @@ int slab_tiling(const lbm_params* p, const lbm_slab* s, lbm::StepTiling* t, char
     return LBM_EINVAL;
   }
   int dev = 0, nsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    snprintf(err, 512, "no CUDA device");
+    return LBM_ECUDA;
+  }
+  // the plan of the last call on this thread is reused while the device and the lattice's
+  // shape are the same (a step is called once per time step; the plan needs an occupancy query)
+  struct PlanKey {
+    int dev, precision, nx, ny, y0, ny_own, wall;
+  };
+  thread_local PlanKey last_key{-1, 0, 0, 0, 0, 0, 0};
+  thread_local lbm::StepTiling last_plan{};
+  const PlanKey key{dev, p->precision, p->nx, p->ny, s->y0, s->ny_own, p->wall};
+  if (std::memcmp(&key, &last_key, sizeof(key)) == 0) {
+    *t = last_plan;
+    return LBM_OK;
+  }
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     snprintf(err, 512, "no CUDA device");
     return LBM_ECUDA;
   }
@@ -69,6 +86,8 @@ int slab_tiling(const lbm_params* p, const lbm_slab* s, lbm::StepTiling* t, char
   t->ylo = wall_lo ? kHalo : 0;
   t->yhi = wall_hi ? kHalo + s->ny_own - 1 : rows - 1;
   t->n_total = double(p->nx) * double(p->ny);
+  last_plan = *t;
+  last_key = key;
   return LBM_OK;
 }
 
