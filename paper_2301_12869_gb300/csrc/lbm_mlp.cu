@@ -278,9 +278,10 @@ __global__ void __launch_bounds__(GT, 1)
 // ------------------------------------------------------------------ fused forward pass
 // The whole network for 128-row tiles in one persistent kernel (inference: lbm_mlp_predict
 // and the warm start). The weights stay in shared memory for the CTA's lifetime (TMA, the
-// GEMM's 128-byte-swizzled K-major layout). The CTA runs two independent tile pipelines,
-// warps 0-3 and 4-7, each with its own activation buffer, TMEM accumulator (128 columns),
-// mbarrier and named barriers, so one group's MMAs overlap the other's epilogue. Per tile
+// GEMM's 128-byte-swizzled K-major layout), the biases and w4 beside them. The CTA runs
+// four independent tile pipelines (groups of 4 warps), each with its own activation
+// buffer, TMEM accumulator (128 of the SM's 512 columns), mbarrier and named barrier, so
+// the groups' MMAs overlap each other's epilogues. Per tile
 // the group's 128 threads (one row each) write their normalised bfloat16 inputs into the
 // A-operand buffer, one thread issues the layer's MMAs, and every thread reads its row
 // back (tcgen05.ld), adds the bias, applies SiLU and writes the bfloat16 activations
@@ -289,14 +290,16 @@ __global__ void __launch_bounds__(GT, 1)
 // third layer the output layer is a dot product with w4 in registers. Rounding points as
 // in the GEMM path: bfloat16 inputs, weights and H1, H2; FP32 accumulation, biases, H3
 // and output.
-constexpr int FF_THREADS = 256;                      // two groups of 4 warps
+constexpr int FF_GROUPS = 4;                         // tile pipelines per CTA
+constexpr int FF_THREADS = 128 * FF_GROUPS;           // one group = 4 warps = 128 rows
 constexpr int FF_BOX = BK * 128 * 2;                 // one 64-element x 128-row swizzled box: 16 KB
 constexpr int FF_W1 = 0;                             // W1 (K = 16, zero-filled to the box)
 constexpr int FF_W2 = FF_W1 + FF_BOX;                // W2: two K boxes
 constexpr int FF_W3 = FF_W2 + 2 * FF_BOX;            // W3: two K boxes
 constexpr int FF_H = FF_W3 + 2 * FF_BOX;             // per group: activations / inputs, two K boxes
-constexpr int FF_BAR = FF_H + 4 * FF_BOX;            // mbarriers, TMEM slot, error flag
-constexpr int FF_SMEM = FF_BAR + 64 + 1024;          // + alignment slack: 145 KB
+constexpr int FF_VEC = FF_H + 2 * FF_BOX * FF_GROUPS; // b1, b2, b3, w4 (FP32), b4
+constexpr int FF_BAR = FF_VEC + (4 * 128 + 4) * 4;   // mbarriers, TMEM slot
+constexpr int FF_SMEM = FF_BAR + 64 + 1024;          // + alignment slack: 211 KB
 
 // 16-byte piece (8 bfloat16 values, k = 8 j .. 8 j + 7) of row r of a K-major operand held in
 // 128-byte-swizzled boxes of 64 K values
@@ -312,6 +315,8 @@ __device__ __forceinline__ void ff_store8(uint8_t* base, int r, int j, const flo
                "r"(w[2]), "r"(w[3])
                : "memory");
 }
+
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // barrier among the 128 threads of group g (named barrier 1 + g) returning the AND of v
 __device__ __forceinline__ bool group_and(bool v, int g) {
@@ -335,19 +340,21 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* wbar = reinterpret_cast<uint64_t*>(smem + FF_BAR);
   uint64_t* mbars = wbar + 1;  // one per group
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbars + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbars + FF_GROUPS);
+  float* vec = reinterpret_cast<float*>(smem + FF_VEC);  // b1 [0, 128), b2, b3, w4, b4 [512]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int g = warp >> 2, r = tid & 127;  // group, and this thread's row within the tile
   const long long ntiles = (n + 127) / 128;
 
   if (tid == 0) {
     lbm::mbar_init(wbar, 1);
-    lbm::mbar_init(&mbars[0], 1);
-    lbm::mbar_init(&mbars[1], 1);
+    for (int i = 0; i < FF_GROUPS; ++i) lbm::mbar_init(&mbars[i], 1);
     lbm::fence_mbar_init();
   }
+  for (int i = tid; i < 4 * 128 + 1; i += FF_THREADS)
+    vec[i] = P[i < 128 ? OFF_B1 + i : (i < 256 ? OFF_B2 + i - 128 : (i < 384 ? OFF_B3 + i - 256 : (i < 512 ? OFF_W4 + i - 384 : OFF_B4)))];
   if (warp == 0) {
-    lbm::tmem_alloc(tmem_slot, 256);
+    lbm::tmem_alloc(tmem_slot, 128 * FF_GROUPS);
     lbm::tmem_relinquish();
   }
   lbm::tc_fence_before();
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
     lbm::tc_fence_after();
     return group_and(done, g);
   };
-  for (long long t = 2LL * blockIdx.x + g; ok && t < ntiles; t += 2LL * gridDim.x) {
+  for (long long t = FF_GROUPS * (long long)blockIdx.x + g; ok && t < ntiles; t += FF_GROUPS * (long long)gridDim.x) {
     const long long m = t * 128 + r;  // this thread's row
     {  // normalised inputs, bfloat16, K = 16 (5 used)
       float a[8], b[8];
@@ -399,7 +406,7 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
       ff_store8(sH, r, 0, a);
       ff_store8(sH, r, 1, b);
     }
-    float out = __ldg(P + OFF_B4);
+    float out = vec[512];
 #pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
       const uint8_t* sB = smem + (layer == 0 ? FF_W1 : (layer == 1 ? FF_W2 : FF_W3));
@@ -407,13 +414,13 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
         ok = false;
         break;
       }
-      const float* bias = P + (layer == 0 ? OFF_B1 : (layer == 1 ? OFF_B2 : OFF_B3));
+      const float* bias = vec + 128 * layer;
 #pragma unroll 1
       for (int cc = 0; cc < 4; ++cc) {  // columns 32 cc .. 32 cc + 31 of this row
         float v[32];
         lbm::tmem_ld32(tmem + uint32_t(32 * cc), v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = silu_f(v[i] + __ldg(bias + 32 * cc + i));
+        for (int i = 0; i < 32; ++i) v[i] = silu_fast(v[i] + bias[32 * cc + i]);
         if (layer < 2) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -424,7 +431,7 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
           }
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) out = fmaf(v[i], __ldg(P + OFF_W4 + 32 * cc + i), out);
+          for (int i = 0; i < 32; ++i) out = fmaf(v[i], vec[384 + 32 * cc + i], out);
         }
       }
       // every read of the accumulator is complete before the group's next MMAs overwrite it
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
   }
   lbm::tc_fence_before();
   __syncthreads();
-  if (warp == 0) lbm::tmem_dealloc(*tmem_slot, 256);
+  if (warp == 0) lbm::tmem_dealloc(*tmem_slot, 128 * FF_GROUPS);
 }
 
 // ------------------------------------------------------------------ other kernels
@@ -974,7 +981,7 @@ int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y) {
   if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
   if (!device_pointer(x) || !device_pointer(y)) return fail(LBM_EINVAL, "x and y must be device pointers");
   if (n == 0) return LBM_OK;
-  // the fused forward kernel: one persistent CTA per SM at most, two 128-row tiles in flight each
+  // the fused forward kernel: one persistent CTA per SM at most, four 128-row tiles in flight each
   CUtensorMap m1, m2, m3;
   if (!make_map(&m1, h->W1, W, KIN, KIN) || !make_map(&m2, h->W2, W, W, W) || !make_map(&m3, h->W3, W, W, W))
     return fail(LBM_ECUDA, "tensor maps of the weights");
@@ -982,7 +989,7 @@ int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y) {
   MLP_CUDA(cudaGetDevice(&dev));
   MLP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const long long ntiles = (n + 127) / 128;
-  const int grid = int(std::min<long long>(nsm, (ntiles + 1) / 2));
+  const int grid = int(std::min<long long>(nsm, (ntiles + FF_GROUPS - 1) / FF_GROUPS));
   mlp_forward_kernel<<<grid, FF_THREADS, FF_SMEM, h->stream>>>(m1, m2, m3, h->P, x, n, y, h->status);
   MLP_CUDA(cudaGetLastError());
   return status_of(h);
