@@ -996,7 +996,7 @@ def run_warmstart(args):
     lbm.lbm_batch_moments(b, rho=rho_dev)
     lbm.lbm_batch_destroy(b)
     rows = sum(c["ny"] for c in cols_tr)
-    x_all = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    x_all = torch.empty((rows, lbm.MLP_INPUTS), dtype=torch.float32, device="cuda")
     t_all = torch.empty(rows, dtype=torch.float32, device="cuda")
     lbm.lbm_mlp_features(cols_tr, 4, A, B, R, x_all, t=t_all, rho=rho_dev)
     good = (res <= 1e-7) & (status == 0)

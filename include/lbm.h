@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 3
+#define LBM_ABI_VERSION 4
 
 /* ---- status codes */
 enum {
@@ -305,22 +305,23 @@ int lbm_batch_destroy(lbm_batch* b);
 
 /* ---- learned warm start for the liquid columns (no counterpart in the paper)
  *
- * A 5 -> 128 -> 128 -> 128 -> 1 network with SiLU activations predicts the steady density
+ * A 6 -> 128 -> 128 -> 128 -> 1 network with SiLU activations predicts the steady density
  * profile rho(z)/rho_c of a column from its descriptors (T/T_c, log10|g|, gravity form,
- * <rho>/rho_c, z/H) with z = y + 1/2 and H = ny. Its only use is to initialise columns;
+ * <rho>/rho_c, z/H, log2 H) with z = y + 1/2 and H = ny (the height places an interface of a
+ * few lattice units' width, which z/H alone cannot). Its only use is to initialise columns;
  * the lattice Boltzmann run to the residual target alone decides the result.
  * Arithmetic: bfloat16 inputs, weights and activations as tensor-core operands (tcgen05,
  * FP32 accumulation in tensor memory), FP32 biases, output layer, loss and Adam; inputs
- * normalised as x_n = (x - c)/s with c = (0.825, -5, 1.5, 1.4, 0.5), s = (0.125, 1, 0.5,
- * 1.1, 0.5). Loss: mean squared error of rho/rho_c.
+ * normalised as x_n = (x - c)/s with c = (0.825, -5, 1.5, 1.4, 0.5, 8), s = (0.125, 1, 0.5,
+ * 1.1, 0.5, 2). Loss: mean squared error of rho/rho_c.
  *
  * Parameters: LBM_MLP_NPARAMS FP32 values, packed in this order:
- *   W1 [128][16] (input j < 5 used; the rest must be 0), b1 [128], W2 [128][128] ([out][in]),
+ *   W1 [128][16] (input j < 6 used; the rest must be 0), b1 [128], W2 [128][128] ([out][in]),
  *   b2 [128], W3 [128][128], b3 [128], w4 [128], b4 [1].
- * Feature rows: 5 FP32 values (T/T_c, log10|g|, form, <rho>/rho_c, z/H), raw (the network
+ * Feature rows: 6 FP32 values (T/T_c, log10|g|, form, <rho>/rho_c, z/H, log2 H), raw (the network
  * normalises them). All feature/target/output arrays of these calls are DEVICE pointers. */
 #define LBM_MLP_WIDTH 128
-#define LBM_MLP_INPUTS 5
+#define LBM_MLP_INPUTS 6
 #define LBM_MLP_IN_PAD 16
 #define LBM_MLP_NPARAMS (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 128 + 1)
 
@@ -348,7 +349,7 @@ int lbm_mlp_train(lbm_mlp* h, const float* x, const float* t, long long n, int b
 /* y[i] = network(x[i]) (predicted rho/rho_c) for n rows (device arrays); synchronises. */
 int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y);
 /* Feature rows of columns: row (c, y) of the concatenation over columns (sum of ny_c rows)
- * gets (T_c/T_crit, log10|g_c|, form_c, <rho>_c/rho_crit, (y + 1/2)/ny_c), with the critical
+ * gets (T_c/T_crit, log10|g_c|, form_c, <rho>_c/rho_crit, (y + 1/2)/ny_c, log2 ny_c), with the critical
  * point of a, b, R. <rho>_c comes from rho when rho != NULL - the columns' density fields,
  * DEVICE, concatenated [col][y][x] with nx per column as lbm_batch_moments writes them -
  * else from mean_rho (host, one value per column). With rho and t != NULL, t receives the

@@ -1,13 +1,13 @@
 """Learned warm start: the density-profile MLP, FP64 oracle (test infrastructure only).
 
 The network is not part of the paper: it predicts the steady density profile of a
-liquid column (the set-up of Sec. IV) from five column descriptors, and its output
+liquid column (the set-up of Sec. IV) from six column descriptors, and its output
 only initialises the lattice Boltzmann run, which alone decides the result.
 
 Definition (plain FP64, in this order):
-    x  = (T/T_c, log10|g|, form, <rho>/rho_c, z/H) mapped by the fixed affine
-         normalisation FEATURE_CENTER / FEATURE_SCALE
-    Z1 = x W1^T + b1,  H1 = silu(Z1)          (W1: 128 x 5)
+    x  = (T/T_c, log10|g|, form, <rho>/rho_c, z/H, log2 H) mapped by the fixed
+         affine normalisation FEATURE_CENTER / FEATURE_SCALE
+    Z1 = x W1^T + b1,  H1 = silu(Z1)          (W1: 128 x 6)
     Z2 = H1 W2^T + b2, H2 = silu(Z2)          (W2: 128 x 128)
     Z3 = H2 W3^T + b3, H3 = silu(Z3)          (W3: 128 x 128)
     y  = H3 w4 + b4                           (predicted rho / rho_c)
@@ -30,11 +30,11 @@ from __future__ import annotations
 import numpy as np
 
 WIDTH = 128
-N_IN = 5
+N_IN = 6
 # x_norm = (x - center) / scale: T/T_c in [0.70, 0.95], log10|g| in [-6, -4], form in
-# {1, 2}, <rho>/rho_c in ~[0.3, 2.5], z/H in (0, 1)
-FEATURE_CENTER = np.array([0.825, -5.0, 1.5, 1.4, 0.5])
-FEATURE_SCALE = np.array([0.125, 1.0, 0.5, 1.1, 0.5])
+# {1, 2}, <rho>/rho_c in ~[0.3, 2.5], z/H in (0, 1), log2 H in [6, 10]
+FEATURE_CENTER = np.array([0.825, -5.0, 1.5, 1.4, 0.5, 8.0])
+FEATURE_SCALE = np.array([0.125, 1.0, 0.5, 1.1, 0.5, 2.0])
 
 
 def to_bf16(a):
@@ -60,7 +60,7 @@ def dsilu(z):
 
 
 def normalise(raw):
-    """raw: (n, 5) column descriptors -> network inputs."""
+    """raw: (n, 6) column descriptors -> network inputs."""
     return (np.asarray(raw, dtype=np.float64) - FEATURE_CENTER) / FEATURE_SCALE
 
 
@@ -79,7 +79,7 @@ def init_params(u):
 
 
 def forward(x, P, bf16=False):
-    """Returns y and the cache of the forward pass (x: normalised inputs, (n, 5))."""
+    """Returns y and the cache of the forward pass (x: normalised inputs, (n, 6))."""
     r = to_bf16 if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     X = r(x)
     Z1 = X @ r(P["W1"]).T + P["b1"]

@@ -1,6 +1,6 @@
-// Learned warm start for the liquid-column runs: a 5 -> 128 -> 128 -> 128 -> 1 SiLU
+// Learned warm start for the liquid-column runs: a 6 -> 128 -> 128 -> 128 -> 1 SiLU
 // network that predicts the steady density profile rho(z)/rho_c of a column from
-// (T/T_c, log10|g|, gravity form, <rho>/rho_c, z/H). It has no counterpart in the paper;
+// (T/T_c, log10|g|, gravity form, <rho>/rho_c, z/H, log2 H). It has no counterpart in the paper;
 // it only initialises lattice Boltzmann runs (Sec. IV set-up), which decide the result.
 //
 // Arithmetic: bfloat16 inputs, weights and activations as matrix operands, FP32
@@ -62,8 +62,8 @@ constexpr int NPARAM = OFF_B4 + 1;
 static_assert(NPARAM == LBM_MLP_NPARAMS, "parameter layout");
 
 // feature normalisation x_norm = (x - c) / s
-__constant__ float kCenter[LBM_MLP_INPUTS] = {0.825f, -5.0f, 1.5f, 1.4f, 0.5f};
-__constant__ float kScale[LBM_MLP_INPUTS] = {0.125f, 1.0f, 0.5f, 1.1f, 0.5f};
+__constant__ float kCenter[LBM_MLP_INPUTS] = {0.825f, -5.0f, 1.5f, 1.4f, 0.5f, 8.0f};
+__constant__ float kScale[LBM_MLP_INPUTS] = {0.125f, 1.0f, 0.5f, 1.1f, 0.5f, 2.0f};
 
 // ------------------------------------------------------------------ GEMM
 constexpr int BM = 128, BN = 128, BK = 64, GT = 128;
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(FF_THREADS, 1)
   };
   for (long long t = FF_GROUPS * (long long)blockIdx.x + g; ok && t < ntiles; t += FF_GROUPS * (long long)gridDim.x) {
     const long long m = t * 128 + r;  // this thread's row
-    {  // normalised inputs, bfloat16, K = 16 (5 used)
+    {  // normalised inputs, bfloat16, K = 16 (6 used)
       float a[8], b[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) a[j] = b[j] = 0.0f;
@@ -565,9 +565,10 @@ struct ColFeat {
   long long row_off;   // first row of this column in the concatenated row list
   long long node_off;  // first node of this column in the concatenated [col][y][x] fields
   float t, lg, form, mean;  // T/T_c, log10|g|, form, <rho>/rho_c (NaN: from rho)
+  float lh;                 // log2 H
 };
 
-// raw features (T/T_c, log10|g|, form, <rho>/rho_c, z/H) of every row of every column;
+// raw features (T/T_c, log10|g|, form, <rho>/rho_c, z/H, log2 H) of every row of every column;
 // with rho != NULL also the targets rho(y, x = 0)/rho_c and <rho> from rho itself
 __global__ void features_kernel(const ColFeat* __restrict__ cols, int ncols, int nx, const double* __restrict__ rho,
                                 double rho_c, float* __restrict__ feat, float* __restrict__ tgt) {
@@ -594,6 +595,7 @@ __global__ void features_kernel(const ColFeat* __restrict__ cols, int ncols, int
     f[2] = cf.form;
     f[3] = mean;
     f[4] = (float(y) + 0.5f) / float(cf.ny);
+    f[5] = cf.lh;
     if (rho && tgt) tgt[cf.row_off + y] = float(rho[cf.node_off + (long long)y * nx] / rho_c);
   }
 }
@@ -837,6 +839,7 @@ int column_table(const lbm_column* cols, int ncols, int nx, double a, double b, 
     f.lg = float(gmag > 0 ? std::log10(gmag) : -12.0);
     f.form = float(in.gravity_form);
     f.mean = mean_rho ? float(mean_rho[c] / rc) : NAN;
+    f.lh = float(std::log2(double(in.ny)));
     r += in.ny;
     q += (long long)in.ny * nx;
   }

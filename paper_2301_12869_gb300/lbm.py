@@ -48,7 +48,7 @@ EXPORTS = (
     "lbm_mlp_destroy", "lbm_slab_partials", "lbm_slab_init", "lbm_slab_mass", "lbm_slab_step",
 )
 
-MLP_WIDTH, MLP_INPUTS, MLP_IN_PAD = 128, 5, 16
+MLP_WIDTH, MLP_INPUTS, MLP_IN_PAD = 128, 6, 16
 #: packed parameter layout of the warm-start network: (name, shape) in order
 MLP_LAYOUT = (("W1", (128, 16)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (128, 128)),
               ("b3", (128,)), ("w4", (128,)), ("b4", (1,)))
@@ -631,7 +631,7 @@ def lbm_mlp_get_params(h):
 
 
 def lbm_mlp_gradients(h, x, t):
-    """x: CUDA float32 tensor (n, 5); t: (n,). Returns (loss, packed gradient array)."""
+    """x: CUDA float32 tensor (n, 6); t: (n,). Returns (loss, packed gradient array)."""
     g = np.empty(MLP_NPARAMS, dtype=np.float32)
     loss = ctypes.c_double()
     _check(load().lbm_mlp_gradients(h, _dev(x), _dev(t), int(t.numel()), g.ctypes.data, ctypes.byref(loss)))

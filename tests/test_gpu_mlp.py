@@ -112,7 +112,7 @@ def params_for_test(seed=1):
 def features(n, seed):
     rng = np.random.default_rng(seed)
     raw = np.column_stack([rng.uniform(0.7, 0.95, n), rng.uniform(-6, -4, n), rng.integers(1, 3, n),
-                           rng.uniform(0.3, 2.5, n), rng.random(n)])
+                           rng.uniform(0.3, 2.5, n), rng.random(n), rng.integers(6, 11, n)])
     t = 1.3 - 1.0 * np.tanh(8.0 * (raw[:, 4] - 0.5)) + 0.2 * (raw[:, 0] - 0.8)
     return raw.astype(np.float32), t.astype(np.float32)
 
@@ -275,11 +275,12 @@ def test_features_and_warm_start_profile():
     mean = np.array([0.12, 0.15, 0.2])
     nx = 4
     rows = sum(c["ny"] for c in cols)
-    x = torch.empty((rows, 5), dtype=torch.float32, device="cuda")
+    x = torch.empty((rows, lbm.MLP_INPUTS), dtype=torch.float32, device="cuda")
     lbm.lbm_mlp_features(cols, nx, a, b, R, x, mean_rho=mean)
     want = np.concatenate([np.column_stack([np.full(c["ny"], c["T"] / T_c), np.full(c["ny"], np.log10(abs(c["gy"]))),
                                             np.full(c["ny"], c["form"]), np.full(c["ny"], m / rho_c),
-                                            (np.arange(c["ny"]) + 0.5) / c["ny"]]) for c, m in zip(cols, mean)])
+                                            (np.arange(c["ny"]) + 0.5) / c["ny"], np.full(c["ny"], np.log2(c["ny"]))])
+                           for c, m in zip(cols, mean)])
     np.testing.assert_allclose(x.cpu().numpy(), want, rtol=1e-6)
     h = lbm.lbm_mlp_create(lbm.mlp_pack(params_for_test(5)), 128)
     try:
@@ -331,7 +332,7 @@ def test_warm_start_gain_on_held_out_columns():
     rho_dev = torch.empty(rho.size, dtype=torch.float64, device="cuda")
     lbm.lbm_batch_moments(bt, rho=rho_dev)
     lbm.lbm_batch_destroy(bt)
-    x = torch.empty((64 * len(cols), 5), dtype=torch.float32, device="cuda")
+    x = torch.empty((64 * len(cols), lbm.MLP_INPUTS), dtype=torch.float32, device="cuda")
     t = torch.empty(64 * len(cols), dtype=torch.float32, device="cuda")
     lbm.lbm_mlp_features(cols, 4, a, b, R, x, t=t, rho=rho_dev)
     keep = torch.from_numpy(np.repeat((res <= 1e-7) & (status == 0), 64)).cuda()

@@ -109,7 +109,8 @@ def test_training_by_the_oracle_fits_a_smooth_profile():
     two orders of magnitude (the network can represent the target family)."""
     rng = np.random.default_rng(9)
     n = 256
-    raw = np.column_stack([np.full(n, 0.8), np.full(n, -5.0), np.ones(n), np.full(n, 1.4), rng.random(n)])
+    raw = np.column_stack([np.full(n, 0.8), np.full(n, -5.0), np.ones(n), np.full(n, 1.4), rng.random(n),
+                           np.full(n, 7.0)])
     t = 1.3 - 1.1 * np.tanh(10.0 * (raw[:, 4] - 0.5))
     x = mlp.normalise(raw)
     P = small_params(10, scale=0.0)
