@@ -166,7 +166,7 @@ def test_gradients_match_oracle(n):
         x = omlp.normalise(raw.astype(np.float64)).astype(np.float32).astype(np.float64)
         loss, g = lbm.lbm_mlp_gradients(h, to_gpu(raw), to_gpu(t))
         G = lbm.mlp_unpack(g)
-        assert np.all(g[:128 * 16].reshape(128, 16)[:, 5:] == 0)  # padded inputs get no gradient
+        assert np.all(g[:128 * 16].reshape(128, 16)[:, lbm.MLP_INPUTS:] == 0)  # padded inputs get no gradient
         l16, g16 = omlp.loss_and_grads(x, t.astype(np.float64), Pf, bf16=True)
         l64, g64 = omlp.loss_and_grads(x, t.astype(np.float64), Pf)
         S, _ = magnitudes(x, t.astype(np.float64), Pf)
