@@ -10,11 +10,13 @@ fused kernel). Metric: MLUPS (million lattice-node updates per second).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
-With N > 1 (torchrun, one rank per GPU) the domain is cut into N slabs of rows,
-one per GPU (strong scaling): every step each rank runs the fused step on its rows,
-sums the domain's mass with the others (NCCL all-reduce, for <rho> of Eq.
-Gravity_2) and swaps two ghost rows with each neighbour (NCCL send / receive);
-``--partition replicas`` runs N independent copies instead. The time-to-steady
+With N > 1 (torchrun, one rank per GPU) the column is cut into N slabs of rows,
+one per GPU - by default a 1024 x 4096 slab per GPU of a 1024 x 4096 N column (weak
+scaling; ``--slab-scaling strong`` cuts the 1024 x 4096 column itself): every step
+each rank runs the fused step on its rows, sums the column's mass with the others
+(NCCL all-reduce, for <rho> of Eq. Gravity_2) and swaps two ghost rows with each
+neighbour (NCCL send / receive); ``--partition replicas`` runs N independent copies
+instead. The time-to-steady
 block splits its columns over the ranks with no exchange. The JSON line reports
 the aggregate over ranks with the max-over-ranks time. ``--impl reference``
 times the FP64 CPU oracle on the host cores on a bounded slice of the same
@@ -469,19 +471,26 @@ def precision_report(lbm, rho0, Tc, steps=PRECISION_STEPS, every=100):
 
 # ---------------------------------------------------------------- the domain as slabs (N GPUs)
 def run_slabs(args, torch, lbm, inputs, world, rank, local, rho0, Tc):
-    """The 1024 x 4096 domain cut into `world` slabs of rows, one per GPU (strong scaling:
-    the domain stays the same as N grows). Per step each rank runs the fused step on its
-    rows (lbm_slab_step), then sums the domain's mass over ranks (NCCL all-reduce of one
-    double, for <rho> of Eq. Gravity_2) and swaps 2 ghost rows x 9 planes with each
-    neighbour (NCCL send / receive). Returns (local ms, local node updates, restores,
-    per-step bytes exchanged, end-to-end dict or None)."""
+    """One liquid column cut into `world` slabs of rows, one per GPU. Weak scaling (the
+    default): every rank holds a 1024 x 4096 slab of a 1024 x 4096 N column, liquid in its
+    lower half; strong scaling (--slab-scaling strong): the 1024 x 4096 column itself is
+    cut. Per step each rank runs the fused step on its rows (lbm_slab_step), then sums the
+    column's mass over ranks (NCCL all-reduce of one double, for <rho> of Eq. Gravity_2)
+    and swaps 2 ghost rows x 9 planes with each neighbour (NCCL send / receive). Returns
+    (local ms, local node updates, restores, per-step bytes exchanged, end-to-end dict or
+    None, status, the rank's slab, the column's rows)."""
     import numpy as np
 
     from paper_2301_12869_gb300 import partition
 
+    weak = args.slab_scaling == "weak"
+    ny_total = NY * world if weak else NY
+    if weak and world > 1:
+        rv, rl, _ = lbm.lbm_coexistence(A, B, R, TR * Tc)
+        rho0 = inputs.column_rho0(NX, ny_total, rl, rv, LIQUID_ROWS * world, noise_amp=NOISE, seed=SEED)
     rho_ref = float(rho0.mean()) if args.precision == "fp32" else 0.0
-    p = lbm.make_params(NX, NY, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY), rho_ref=rho_ref)
-    plan = partition.SlabPlan(NY, world)
+    p = lbm.make_params(NX, ny_total, TR * Tc, args.precision, a=A, b=B, R=R, form=2, g=(0.0, GY), rho_ref=rho_ref)
+    plan = partition.SlabPlan(ny_total, world)
     sl = plan[rank]
     if world > 1:
         import torch.distributed as dist
@@ -527,16 +536,17 @@ def run_slabs(args, torch, lbm, inputs, world, rank, local, rho0, Tc):
         t0 = time.perf_counter()
         lat = partition.SlabLattice(p, sl, pinned.cuda(non_blocking=True), comm)
         lat.step(args.steps)
-        mass = float(lat.mass[lat.cur].item()) + rho_ref * NX * NY
+        mass = float(lat.mass[lat.cur].item()) + rho_ref * NX * ny_total
         t1 = time.perf_counter()
         ms_e, units_e = aggregate((t1 - t0) * 1e3, float(NX * sl.ny_own) * args.steps, torch)
-        e2e = {"value": units_e / (ms_e / 1e3) / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 8 * NX * NY / args.steps,
+        e2e = {"value": units_e / (ms_e / 1e3) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * NX * ny_total / args.steps,
                "d2h_bytes_per_step": 8 * world / args.steps, "mass": mass,
                "what": "each rank: its rows of rho0 from pinned host memory, slab set-up, K steps with the "
                        "exchanges, the domain mass to the host; host clock, max over ranks"}
         del lat
     halo_bytes = 2 * 2 * partition.HALO * 9 * NX * (4 if args.precision == "fp32" else 8)
-    return local_ms, float(NX * sl.ny_own) * args.steps, restores, halo_bytes, e2e, status, sl
+    return local_ms, float(NX * sl.ny_own) * args.steps, restores, halo_bytes, e2e, status, sl, ny_total
 
 
 # ---------------------------------------------------------------- batched columns
@@ -1281,6 +1291,9 @@ def main(argv=None):
     ap.add_argument("--partition", choices=["auto", "slabs", "replicas"], default="auto",
                     help="N > 1: the domain as slabs, one per GPU (auto) or N independent replicas; "
                          "slabs also runs at N = 1 (one slab = the whole domain)")
+    ap.add_argument("--slab-scaling", choices=["weak", "strong"], default="weak",
+                    help="slabs: a 1024 x 4096 slab per GPU of a 1024 x 4096 N column (weak), or the "
+                         "1024 x 4096 column cut into N slabs (strong)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--ref-rows", type=int, default=64, help="rows of the oracle slice for --impl reference")
     ap.add_argument("--workload", choices=["domain", "columns", "thermal", "warmstart", "boiling", "gemm", "small"],
@@ -1373,7 +1386,7 @@ def main(argv=None):
         nvml = NvmlClocks(local).start()
         with ClockSampler(local) as smi:
             t_host0 = time.perf_counter()
-            local_ms, local_units, restores, halo_bytes, e2e, status, sl = run_slabs(
+            local_ms, local_units, restores, halo_bytes, e2e, status, sl, ny_total = run_slabs(
                 args, torch, lbm, inputs, world, rank, local, rho0, Tc)
             t_host1 = time.perf_counter()
         nvml.stop()
@@ -1383,10 +1396,11 @@ def main(argv=None):
         alg_bytes = BYTES_PER_NODE[args.precision] * NX * sl.ny_own
         achieved = alg_bytes / kernel_s / 1e9
         mass = e2e["mass"] if e2e else None
-        info = {"slab_rows_rank0": sl.ny_own, "ghost_rows_per_side": 2, "exchange_bytes_per_step_per_rank": halo_bytes,
+        info = {"column_rows": ny_total, "slab_rows_rank0": sl.ny_own, "ghost_rows_per_side": 2,
+                "exchange_bytes_per_step_per_rank": halo_bytes,
                 "exchanges_per_step": "NCCL all-reduce of the mass (8 B) + send/receive of 2 ghost rows x 9 planes "
                                       "with each neighbour"}
-        scaling, parallelism = "strong", f"y-slabs x{world}"
+        scaling, parallelism = args.slab_scaling, f"y-slabs x{world}"
         launches = 2 * args.steps  # slab step + its partial-sum kernel per step
         kernel_name = "step_kernel_ws on the rank's slab (+ exchanges, per step)"
         torch.cuda.empty_cache()
@@ -1451,7 +1465,10 @@ def main(argv=None):
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": scaling,
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": workload_config(args.precision) | {"launch": info, "parallelism": parallelism},
+        "config": workload_config(args.precision) | {"launch": info, "parallelism": parallelism} | (
+            {"workload": f"liquid column {NX}x{ny_total} D2Q9 as {world} slabs of {NX}x{ny_total // world}, "
+                         f"{args.precision.upper()} populations, FP64 reductions",
+             "ny": ny_total, "liquid_rows": LIQUID_ROWS * ny_total // NY} if use_slabs else {}),
         "roofline": ({
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None if use_slabs else traffic_from_profile(args.precision),

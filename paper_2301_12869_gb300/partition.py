@@ -100,19 +100,30 @@ def own_rows(buf, slab):
     return buf[..., HALO:HALO + slab.ny_own, :]
 
 
-def exchange_halos(buf, slab, comm):
+def exchange_halos(buf, slab, comm, bufs=None):
     """Refresh the ghost rows of a slab buffer (torch tensor [9, rows, nx] holding the
     post-collision populations of the last step) from the neighbours: the lowest HALO own
     rows go to the lower neighbour's upper halo, the highest HALO own rows to the upper
     neighbour's lower halo, and the halos are filled from what the neighbours send.
-    comm.exchange(sends), sends = {peer: contiguous tensor}, returns {peer: tensor} of the
-    same shapes. A slab at a wall leaves that halo untouched (the step applies the wall)."""
-    sends = {}
+    comm.exchange(sends, recvs), sends = {peer: contiguous tensor}, returns {peer: tensor} of
+    the same shapes (into recvs when given). bufs: optional preallocated
+    {("send" | "recv", peer): tensor [9, HALO, nx]}. A slab at a wall leaves that halo
+    untouched (the step applies the wall)."""
+    sends, recvs = {}, None
+    edges = []
     if slab.lower is not None:
-        sends[slab.lower] = buf[:, HALO:2 * HALO, :].contiguous()
+        edges.append((slab.lower, HALO))
     if slab.upper is not None:
-        sends[slab.upper] = buf[:, slab.ny_own:slab.ny_own + HALO, :].contiguous()
-    recv = comm.exchange(sends)
+        edges.append((slab.upper, slab.ny_own))
+    for peer, row in edges:
+        if bufs is None:
+            sends[peer] = buf[:, row:row + HALO, :].contiguous()
+        else:
+            sends[peer] = bufs[("send", peer)]
+            sends[peer].copy_(buf[:, row:row + HALO, :])
+    if bufs is not None:
+        recvs = {peer: bufs[("recv", peer)] for peer, _ in edges}
+    recv = comm.exchange(sends, recvs) if recvs is not None else comm.exchange(sends)
     if slab.lower is not None:
         buf[:, 0:HALO, :] = recv[slab.lower]
     if slab.upper is not None:
@@ -129,11 +140,12 @@ class TorchComm:
     def __init__(self, dist):
         self.dist = dist
 
-    def exchange(self, sends):
+    def exchange(self, sends, recvs=None):
         import torch
 
         dist = self.dist
-        recvs = {peer: torch.empty_like(t) for peer, t in sends.items()}
+        if recvs is None:
+            recvs = {peer: torch.empty_like(t) for peer, t in sends.items()}
         ops = []
         for peer, t in sends.items():
             ops.append(dist.P2POp(dist.isend, t, peer))
@@ -176,9 +188,23 @@ class SlabLattice:
         stream = self._stream()
         lbm.lbm_slab_init(params, self.s, rho0_own.contiguous(), self.f[0], stream)
         lbm.lbm_slab_mass(params, self.s, self.f[0], self.part, self.mass[0], stream)
+        # ghost-row exchange buffers, allocated once
+        self.bufs = {}
+        for peer in (slab.lower, slab.upper):
+            if peer is not None:
+                for kind in ("send", "recv"):
+                    self.bufs[(kind, peer)] = torch.empty((9, HALO, params.nx), dtype=dtype, device="cuda")
         comm.sum_(self.mass[0])
-        exchange_halos(self.f[0], slab, comm)
+        exchange_halos(self.f[0], slab, comm, self.bufs)
         self.steps = 0
+        # the step's library call with its arguments marshalled once (the buffers never move)
+        import ctypes
+
+        lib = lbm.load()
+        self._call = lib.lbm_slab_step
+        self._pp, self._sp = ctypes.byref(params), ctypes.byref(self.s)
+        self._ptr = {"f": [t.data_ptr() for t in self.f], "m": [t.data_ptr() for t in self.mass],
+                     "part": self.part.data_ptr(), "status": self.status.data_ptr()}
 
     def _stream(self):
         return self._torch.cuda.current_stream().cuda_stream
@@ -190,13 +216,16 @@ class SlabLattice:
 
     def step(self, n=1):
         lbm, stream = self._lbm, self._stream()
+        pf, pm = self._ptr["f"], self._ptr["m"]
         for _ in range(n):
-            fi, fo = self.f[self.cur], self.f[1 - self.cur]
-            lbm.lbm_slab_step(self.p, self.s, fi, fo, self.mass[self.cur], self.part, self.mass[1 - self.cur],
-                              self.status, stream)
+            c = self.cur
+            rc = self._call(self._pp, self._sp, pf[c], pf[1 - c], pm[c], self._ptr["part"], pm[1 - c],
+                            self._ptr["status"], stream)
+            if rc != lbm.LBM_OK:
+                lbm._check(rc)
             self.cur ^= 1
             self.comm.sum_(self.mass[self.cur])
-            exchange_halos(self.f[self.cur], self.slab, self.comm)
+            exchange_halos(self.f[self.cur], self.slab, self.comm, self.bufs)
             self.steps += 1
 
     def snapshot(self):
@@ -220,7 +249,7 @@ class SlabLattice:
 class SingleComm:
     """The comm of a single rank (one slab = the whole domain): nothing to exchange."""
 
-    def exchange(self, sends):
+    def exchange(self, sends, recvs=None):
         if sends:
             raise ValueError("a single rank has no neighbours")
         return {}

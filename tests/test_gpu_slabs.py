@@ -44,12 +44,16 @@ class ThreadComm:
         comm = self
 
         class View:
-            def exchange(self, sends):
+            def exchange(self, sends, recvs=None):
                 for peer, t in sends.items():
                     comm.box[(rank, peer)] = t.clone()
                 comm.barrier.wait()
                 out = {peer: comm.box[(peer, rank)] for peer in sends}
                 comm.barrier.wait()
+                if recvs is not None:
+                    for peer in out:
+                        recvs[peer].copy_(out[peer])
+                    return recvs
                 return out
 
             def sum_(self, t):
