@@ -178,10 +178,11 @@ class NvmlClocks:
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
                0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, torch_device):
+    def __init__(self, torch_device, period_s=0.0002):
         import ctypes
         import threading
 
+        self.period = period_s
         self.samples, self.max_mhz, self.err = [], None, None
         self._stop = threading.Event()
         self._thread = None
@@ -220,7 +221,7 @@ class NvmlClocks:
             if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
                 r = rsn.value if self._reasons(self.h, ctypes.byref(rsn)) == 0 else 0
                 self.samples.append((time.perf_counter(), clk.value, r))
-            time.sleep(0.0002)
+            time.sleep(self.period)
 
     def start(self):
         import threading
@@ -244,7 +245,7 @@ class NvmlClocks:
                     "source": "nvml" if self.lib is not None else f"none ({self.err})"}
         reasons = sorted({name for _, _, r in sel for bit, name in self.REASONS.items() if r & bit})
         return {"sm_mhz": statistics.median(c for _, c, _ in sel), "sm_max_mhz": self.max_mhz, "reasons": reasons,
-                "samples": len(sel), "source": "nvml, ~0.2 ms period"}
+                "samples": len(sel), "source": f"nvml, ~{1e3 * self.period:g} ms period"}
 
 
 # ---------------------------------------------------------------- CPU oracle timing
@@ -1382,8 +1383,9 @@ def main(argv=None):
     use_slabs = args.partition == "slabs" or (args.partition == "auto" and world > 1)
     peaks, peak_kind = measured_peaks()
     if use_slabs:
-        # ---- the domain cut into slabs, one per GPU (strong scaling), NCCL exchanges per step
-        nvml = NvmlClocks(local).start()
+        # ---- the column cut into slabs, one per GPU, NCCL exchanges per step; the slab loop
+        # runs Python per step, so the sampler polls slowly (it competes for the interpreter)
+        nvml = NvmlClocks(local, period_s=0.005).start()
         with ClockSampler(local) as smi:
             t_host0 = time.perf_counter()
             local_ms, local_units, restores, halo_bytes, e2e, status, sl, ny_total = run_slabs(
