@@ -407,17 +407,20 @@ int lbm_slab_partials(const lbm_params* p, const lbm_slab* s, int* count);
 /* Own rows of f = the rest equilibrium of rho0 (ny_own x nx doubles [y][x], device); ghost
  * rows untouched. */
 int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, void* f, void* stream);
-/* mass[0] = sum of the stored deviations over the own rows of f (device; part: scratch of
- * lbm_slab_partials doubles). Summed over all slabs this is sum(rho - rho_ref) of the domain. */
-int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, double* mass, void* stream);
+/* mass[0] = sum of the stored deviations over the own rows of f (device; part: device scratch of
+ * npart >= lbm_slab_partials doubles, else LBM_EINVAL). Summed over all slabs this is
+ * sum(rho - rho_ref) of the domain. */
+int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, double* mass,
+                  void* stream);
 /* One time step of the own rows, f_out = step(f_in) (distinct buffers; f_in's ghost rows must
  * hold the neighbours' rows of the same state). mass_in: device double = the domain-wide sum
  * of lbm_slab_mass / mass_out over all slabs for f_in (read for Eq. Gravity_2 only, may be
- * NULL otherwise). Writes part (lbm_slab_partials doubles) and mass_out[0] = this slab's mass
- * of f_out. status: device int the kernel ORs LBM status bits into (1: non-physical, 2: a
- * bounded wait timed out); the caller zeroes it and reads it after the stream completes. */
+ * NULL otherwise). Writes part (device, npart >= lbm_slab_partials doubles, else LBM_EINVAL)
+ * and mass_out[0] = this slab's mass of f_out. status: device int the kernel ORs LBM status
+ * bits into (1: non-physical, 2: a bounded wait timed out); the caller zeroes it and reads it
+ * after the stream completes. */
 int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* mass_in,
-                  double* part, double* mass_out, int* status, void* stream);
+                  double* part, int npart, double* mass_out, int* status, void* stream);
 
 /* ---- one step without device allocation (this entry point has no counterpart in the paper)
  *

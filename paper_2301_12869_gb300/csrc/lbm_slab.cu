@@ -32,6 +32,26 @@ int fail(int code, const char* msg) {
   return code;
 }
 
+// The step kernels' shared-memory limit, once per device and precision. It must be set
+// before a plan is made: the occupancy query that sizes the grid depends on it.
+int prepare_once(int dev, int precision, char* err) {
+  static std::atomic<bool> prepared[kMaxDevices][2];
+  if (dev < 0 || dev >= kMaxDevices) {
+    snprintf(err, 512, "device index beyond the %d this entry point supports", kMaxDevices);
+    return LBM_EINVAL;
+  }
+  std::atomic<bool>& ready = prepared[dev][precision == LBM_FP32 ? 1 : 0];
+  if (!ready.load()) {
+    const cudaError_t e = lbm::step_prepare(precision);
+    if (e != cudaSuccess) {
+      snprintf(err, 512, "kernel attributes: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+    ready.store(true);
+  }
+  return LBM_OK;
+}
+
 // The step's tiling for a slab: strips over the own rows only, buffer rows, wall rows
 // where the slab touches the domain's ends, the whole domain's node count for <rho>.
 int slab_tiling(const lbm_params* p, const lbm_slab* s, lbm::StepTiling* t, char* err) {
@@ -76,6 +96,7 @@ int slab_tiling(const lbm_params* p, const lbm_slab* s, lbm::StepTiling* t, char
     snprintf(err, 512, "no CUDA device");
     return LBM_ECUDA;
   }
+  if ((rc = prepare_once(dev, p->precision, err))) return rc;
   lbm_params q = *p;
   q.ny = s->ny_own;  // strips over the own rows
   if ((rc = lbm::plan_step_tiling(q, nsm, t, err))) return rc;
@@ -164,7 +185,8 @@ int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, vo
   return LBM_OK;
 }
 
-int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, double* mass, void* stream) {
+int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, double* mass,
+                  void* stream) {
   char err[512];
   lbm::StepTiling t;
   const int rc = slab_tiling(p, s, &t, err);
@@ -172,6 +194,10 @@ int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double*
   if (!f || !part || !mass) return fail(LBM_EINVAL, "f, part and mass must be device arrays");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int P = std::max(t.nbands * t.nstrips, 1);
+  if (npart < P) {
+    snprintf(err, sizeof(err), "part holds %d values, the slab needs %d (lbm_slab_partials)", npart, P);
+    return fail(LBM_EINVAL, err);
+  }
   if (p->precision == LBM_FP32)
     slab_partials_kernel<float><<<P, 256, 0, st>>>(static_cast<const float*>(f), p->nx, t.ny, s->ny_own, part);
   else
@@ -183,7 +209,7 @@ int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double*
 }
 
 int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* mass_in,
-                  double* part, double* mass_out, int* status, void* stream) {
+                  double* part, int npart, double* mass_out, int* status, void* stream) {
   char err[512];
   lbm::StepTiling t;
   const int rc = slab_tiling(p, s, &t, err);
@@ -191,15 +217,10 @@ int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void
   const bool form2 = p->gravity_form == LBM_GRAVITY_RHO_MINUS_MEAN_G;
   if (!f_in || !f_out || f_in == f_out || !part || !mass_out || !status || (form2 && !mass_in))
     return fail(LBM_EINVAL, "f_in, f_out (distinct), part, mass_out, status (and mass_in for Eq. Gravity_2) must be set");
-  // the step kernels' shared-memory limit, once per device and precision
-  static std::atomic<bool> prepared[kMaxDevices][2];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev >= kMaxDevices) return fail(LBM_ECUDA, "no usable CUDA device");
-  std::atomic<bool>& ready = prepared[dev][p->precision == LBM_FP32 ? 1 : 0];
-  if (!ready.load()) {
-    const cudaError_t e = lbm::step_prepare(p->precision);
-    if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
-    ready.store(true);
+  if (npart < t.nbands * t.nstrips) {
+    snprintf(err, sizeof(err), "part holds %d values, the step writes %d (lbm_slab_partials)", npart,
+             t.nbands * t.nstrips);
+    return fail(LBM_EINVAL, err);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   lbm::StepIO io{};

@@ -150,8 +150,8 @@ def load(path: str = LIB_PATH):
         "lbm_mlp_destroy": (i32, [vp]),
         "lbm_slab_partials": (i32, [P(lbm_params), P(lbm_slab), P(i32)]),
         "lbm_slab_init": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp]),
-        "lbm_slab_mass": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, vp]),
-        "lbm_slab_step": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, vp, vp, vp, vp]),
+        "lbm_slab_mass": (i32, [P(lbm_params), P(lbm_slab), vp, vp, i32, vp, vp]),
+        "lbm_slab_step": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -359,13 +359,13 @@ def lbm_slab_init(p, s, rho0, f, stream=None):
 
 def lbm_slab_mass(p, s, f, part, mass, stream=None):
     _check(load().lbm_slab_mass(ctypes.byref(p), ctypes.byref(s), _slab_ptr(f, "f"), _slab_ptr(part, "part"),
-                                _slab_ptr(mass, "mass"), stream))
+                                int(part.numel()), _slab_ptr(mass, "mass"), stream))
 
 
 def lbm_slab_step(p, s, f_in, f_out, mass_in, part, mass_out, status, stream=None):
     _check(load().lbm_slab_step(ctypes.byref(p), ctypes.byref(s), _slab_ptr(f_in, "f_in"), _slab_ptr(f_out, "f_out"),
-                                _slab_ptr(mass_in, "mass_in"), _slab_ptr(part, "part"), _slab_ptr(mass_out, "mass_out"),
-                                _slab_ptr(status, "status"), stream))
+                                _slab_ptr(mass_in, "mass_in"), _slab_ptr(part, "part"), int(part.numel()),
+                                _slab_ptr(mass_out, "mass_out"), _slab_ptr(status, "status"), stream))
 
 
 def lbm_batch_init(p, columns, rho0, stream=None):

@@ -204,7 +204,7 @@ class SlabLattice:
         self._call = lib.lbm_slab_step
         self._pp, self._sp = ctypes.byref(params), ctypes.byref(self.s)
         self._ptr = {"f": [t.data_ptr() for t in self.f], "m": [t.data_ptr() for t in self.mass],
-                     "part": self.part.data_ptr(), "status": self.status.data_ptr()}
+                     "part": self.part.data_ptr(), "npart": int(self.part.numel()), "status": self.status.data_ptr()}
 
     def _stream(self):
         return self._torch.cuda.current_stream().cuda_stream
@@ -219,8 +219,8 @@ class SlabLattice:
         pf, pm = self._ptr["f"], self._ptr["m"]
         for _ in range(n):
             c = self.cur
-            rc = self._call(self._pp, self._sp, pf[c], pf[1 - c], pm[c], self._ptr["part"], pm[1 - c],
-                            self._ptr["status"], stream)
+            rc = self._call(self._pp, self._sp, pf[c], pf[1 - c], pm[c], self._ptr["part"], self._ptr["npart"],
+                            pm[1 - c], self._ptr["status"], stream)
             if rc != lbm.LBM_OK:
                 lbm._check(rc)
             self.cur ^= 1

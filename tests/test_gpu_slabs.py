@@ -143,3 +143,19 @@ def test_slab_arguments_are_checked():
         lbm.lbm_slab_step(p, s, f, f, m, part, m, st)
     with pytest.raises(ValueError, match="CUDA"):
         lbm.lbm_slab_step(p, s, f.cpu(), f, m, part, m, st)
+    with pytest.raises(lbm.LbmError, match="part holds"):  # fewer partial slots than CTAs
+        lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), m, part[:0], m, st)
+
+
+@pytest.mark.parametrize("precision, nx, ny", [("fp32", 1024, 4096), ("fp64", 1024, 4096), ("fp32", 64, 40)])
+def test_whole_domain_slab_plans_like_a_handle(precision, nx, ny):
+    """One slab over the whole domain, asked first in a fresh plan: as many CTAs (= partial
+    sums) as the handle's grid for the same lattice - the plan is made after the step
+    kernels' shared-memory limit is set (their occupancy depends on it)."""
+    p = lbm.make_params(nx, ny, 0.02, precision, a=A)
+    n = lbm.lbm_slab_partials(p, lbm.make_slab(0, ny))
+    h = lbm.lbm_init(p, np.full((ny, nx), 0.1))
+    try:
+        assert n == lbm.lbm_launch_info(h)["grid"]
+    finally:
+        lbm.lbm_destroy(h)
