@@ -144,7 +144,7 @@ def test_slab_arguments_are_checked():
     with pytest.raises(ValueError, match="CUDA"):
         lbm.lbm_slab_step(p, s, f.cpu(), f, m, part, m, st)
     with pytest.raises(lbm.LbmError, match="part holds"):  # fewer partial slots than CTAs
-        lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), m, part[:0], m, st)
+        lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), m, part[:1], m, st)
 
 
 @pytest.mark.parametrize("precision, nx, ny", [("fp32", 1024, 4096), ("fp64", 1024, 4096), ("fp32", 64, 40)])
