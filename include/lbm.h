@@ -389,8 +389,8 @@ int lbm_mlp_destroy(lbm_mlp* h);
  * Shan-Chen force (Eq. ShanChenForce) on the slab's edge row needs psi of that row, which
  * pulls from the next one. Walls (p->wall) act where the slab meets row 0 or row p->ny - 1;
  * elsewhere the caller refreshes the ghost rows after every step with its neighbours' edge
- * rows (2 rows x 9 planes each way) and sums the slabs' mass for <rho> of Eq. Gravity_2 over
- * the whole domain (both by its own communication, e.g. NCCL). p->rho_ref must be the same
+ * rows (2 rows x 9 planes each way) and adds the slabs' mass partials element-wise for <rho>
+ * of Eq. Gravity_2 over the whole domain (both by its own communication, e.g. NCCL). p->rho_ref must be the same
  * on every slab (NaN means 0). These calls allocate nothing, are asynchronous on `stream`
  * (a cudaStream_t, NULL = default) and take only device pointers. Isothermal only. A slab
  * with a neighbour needs ny_own >= LBM_SLAB_HALO. Errors: LBM_EINVAL, LBM_ECUDA. */
@@ -407,20 +407,20 @@ int lbm_slab_partials(const lbm_params* p, const lbm_slab* s, int* count);
 /* Own rows of f = the rest equilibrium of rho0 (ny_own x nx doubles [y][x], device); ghost
  * rows untouched. */
 int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, void* f, void* stream);
-/* mass[0] = sum of the stored deviations over the own rows of f (device; part: device scratch of
- * npart >= lbm_slab_partials doubles, else LBM_EINVAL). Summed over all slabs this is
- * sum(rho - rho_ref) of the domain. */
-int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, double* mass,
-                  void* stream);
+/* The FP64 mass partials of the own rows of f (device): part[0 .. lbm_slab_partials) (npart >=
+ * that, else LBM_EINVAL). Their sum, over all slabs, is sum(rho - rho_ref) of the domain. */
+int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, void* stream);
 /* One time step of the own rows, f_out = step(f_in) (distinct buffers; f_in's ghost rows must
- * hold the neighbours' rows of the same state). mass_in: device double = the domain-wide sum
- * of lbm_slab_mass / mass_out over all slabs for f_in (read for Eq. Gravity_2 only, may be
- * NULL otherwise). Writes part (device, npart >= lbm_slab_partials doubles, else LBM_EINVAL)
- * and mass_out[0] = this slab's mass of f_out. status: device int the kernel ORs LBM status
- * bits into (1: non-physical, 2: a bounded wait timed out); the caller zeroes it and reads it
- * after the stream completes. */
-int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* mass_in,
-                  double* part, int npart, double* mass_out, int* status, void* stream);
+ * hold the neighbours' rows of the same state). part_in: device, npart_in doubles whose sum is
+ * the domain-wide sum(rho - rho_ref) of f_in - the slabs' partials (lbm_slab_mass, or the
+ * previous step's part_out) added element-wise over all slabs, zero-padded to a common length;
+ * read for Eq. Gravity_2 only (may be NULL otherwise) and summed in a fixed order. Writes
+ * part_out (device, distinct from part_in, npart_out >= lbm_slab_partials, else LBM_EINVAL;
+ * entries beyond lbm_slab_partials untouched): this slab's partials of f_out. status: device
+ * int the kernel ORs LBM status bits into (1: non-physical, 2: a bounded wait timed out); the
+ * caller zeroes it and reads it after the stream completes. */
+int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* part_in,
+                  int npart_in, double* part_out, int npart_out, int* status, void* stream);
 
 /* ---- one step without device allocation (this entry point has no counterpart in the paper)
  *

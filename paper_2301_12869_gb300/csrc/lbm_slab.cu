@@ -7,9 +7,10 @@
 // streaming (Eq. LBE) reads the ghost row next to the slab, and the Shan-Chen stencil
 // (Eq. ShanChenForce) needs psi of that ghost row, which in turn pulls from the outer one;
 // walls apply only where the slab meets the domain's bottom or top. Between steps the
-// caller refreshes the ghost rows from the neighbouring slabs and sums the slabs' mass
-// (the <rho> of Eq. Gravity_2 is a mean over the whole domain); these calls allocate
-// nothing and move no data between GPUs themselves.
+// caller refreshes the ghost rows from the neighbouring slabs and adds the slabs' FP64
+// mass partials element-wise across ranks (the <rho> of Eq. Gravity_2 is a mean over the
+// whole domain; the next step's kernel finishes the sum in a fixed order); these calls
+// allocate nothing and move no data between GPUs themselves.
 #include "lbm.h"
 #include "lbm_internal.h"
 #include "lbm_physics.cuh"
@@ -185,13 +186,12 @@ int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, vo
   return LBM_OK;
 }
 
-int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, double* mass,
-                  void* stream) {
+int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, void* stream) {
   char err[512];
   lbm::StepTiling t;
   const int rc = slab_tiling(p, s, &t, err);
   if (rc) return fail(rc, err);
-  if (!f || !part || !mass) return fail(LBM_EINVAL, "f, part and mass must be device arrays");
+  if (!f || !part) return fail(LBM_EINVAL, "f and part must be device arrays");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int P = std::max(t.nbands * t.nstrips, 1);
   if (npart < P) {
@@ -202,23 +202,24 @@ int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double*
     slab_partials_kernel<float><<<P, 256, 0, st>>>(static_cast<const float*>(f), p->nx, t.ny, s->ny_own, part);
   else
     slab_partials_kernel<double><<<P, 256, 0, st>>>(static_cast<const double*>(f), p->nx, t.ny, s->ny_own, part);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = lbm::launch_sum_partials(part, P, mass, st);
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
 
-int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* mass_in,
-                  double* part, int npart, double* mass_out, int* status, void* stream) {
+int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* part_in,
+                  int npart_in, double* part_out, int npart_out, int* status, void* stream) {
   char err[512];
   lbm::StepTiling t;
   const int rc = slab_tiling(p, s, &t, err);
   if (rc) return fail(rc, err);
   const bool form2 = p->gravity_form == LBM_GRAVITY_RHO_MINUS_MEAN_G;
-  if (!f_in || !f_out || f_in == f_out || !part || !mass_out || !status || (form2 && !mass_in))
-    return fail(LBM_EINVAL, "f_in, f_out (distinct), part, mass_out, status (and mass_in for Eq. Gravity_2) must be set");
-  if (npart < t.nbands * t.nstrips) {
-    snprintf(err, sizeof(err), "part holds %d values, the step writes %d (lbm_slab_partials)", npart,
+  if (!f_in || !f_out || f_in == f_out || !part_out || !status || (form2 && (!part_in || npart_in < 1)))
+    return fail(LBM_EINVAL,
+                "f_in, f_out (distinct), part_out, status (and part_in for Eq. Gravity_2) must be set");
+  if (part_in == part_out) return fail(LBM_EINVAL, "part_in and part_out must be distinct");
+  if (npart_out < t.nbands * t.nstrips) {
+    snprintf(err, sizeof(err), "part_out holds %d values, the step writes %d (lbm_slab_partials)", npart_out,
              t.nbands * t.nstrips);
     return fail(LBM_EINVAL, err);
   }
@@ -226,12 +227,12 @@ int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void
   lbm::StepIO io{};
   io.fin = f_in;
   io.fout = f_out;
-  io.part_in = mass_in;
-  io.npart_in = form2 ? 1 : 0;
-  io.part_out = part;
+  io.part_in = part_in;
+  io.npart_in = form2 ? npart_in : 0;
+  io.part_out = part_out;
   io.status = status;
-  cudaError_t e = lbm::launch_step(p->precision, lbm::MODE_STEP, t, lbm::phys_from_params(*p, slab_rho_ref(p)), io, st);
-  if (e == cudaSuccess) e = lbm::launch_sum_partials(part, t.nbands * t.nstrips, mass_out, st);
+  const cudaError_t e =
+      lbm::launch_step(p->precision, lbm::MODE_STEP, t, lbm::phys_from_params(*p, slab_rho_ref(p)), io, st);
   if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
   return LBM_OK;
 }

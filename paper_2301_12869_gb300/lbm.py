@@ -150,8 +150,8 @@ def load(path: str = LIB_PATH):
         "lbm_mlp_destroy": (i32, [vp]),
         "lbm_slab_partials": (i32, [P(lbm_params), P(lbm_slab), P(i32)]),
         "lbm_slab_init": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp]),
-        "lbm_slab_mass": (i32, [P(lbm_params), P(lbm_slab), vp, vp, i32, vp, vp]),
-        "lbm_slab_step": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, vp, i32, vp, vp, vp]),
+        "lbm_slab_mass": (i32, [P(lbm_params), P(lbm_slab), vp, vp, i32, vp]),
+        "lbm_slab_step": (i32, [P(lbm_params), P(lbm_slab), vp, vp, vp, i32, vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -357,15 +357,18 @@ def lbm_slab_init(p, s, rho0, f, stream=None):
     _check(load().lbm_slab_init(ctypes.byref(p), ctypes.byref(s), _slab_ptr(rho0, "rho0"), _slab_ptr(f, "f"), stream))
 
 
-def lbm_slab_mass(p, s, f, part, mass, stream=None):
+def lbm_slab_mass(p, s, f, part, stream=None):
+    """The FP64 mass partials of the slab's own rows into part (device, >= lbm_slab_partials)."""
     _check(load().lbm_slab_mass(ctypes.byref(p), ctypes.byref(s), _slab_ptr(f, "f"), _slab_ptr(part, "part"),
-                                int(part.numel()), _slab_ptr(mass, "mass"), stream))
+                                int(part.numel()), stream))
 
 
-def lbm_slab_step(p, s, f_in, f_out, mass_in, part, mass_out, status, stream=None):
+def lbm_slab_step(p, s, f_in, f_out, part_in, part_out, status, stream=None):
+    """One step of the slab; part_in: the domain's partials of f_in (summed over slabs)."""
     _check(load().lbm_slab_step(ctypes.byref(p), ctypes.byref(s), _slab_ptr(f_in, "f_in"), _slab_ptr(f_out, "f_out"),
-                                _slab_ptr(mass_in, "mass_in"), _slab_ptr(part, "part"), int(part.numel()),
-                                _slab_ptr(mass_out, "mass_out"), _slab_ptr(status, "status"), stream))
+                                _slab_ptr(part_in, "part_in"), 0 if part_in is None else int(part_in.numel()),
+                                _slab_ptr(part_out, "part_out"), int(part_out.numel()), _slab_ptr(status, "status"),
+                                stream))
 
 
 def lbm_batch_init(p, columns, rho0, stream=None):

@@ -156,16 +156,23 @@ class TorchComm:
         return recvs
 
     def sum_(self, t):
-        """In-place sum of a tensor over all ranks."""
+        """In-place element-wise sum of a tensor over all ranks."""
         self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return t
+
+    def max_(self, t):
+        """In-place element-wise max of a tensor over all ranks."""
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
         return t
 
 
 class SlabLattice:
     """One rank's slab of a domain on the current GPU. Buffers are torch CUDA tensors, every
     step is the library's slab step (lbm_slab_step) on torch's current stream, and `comm`
-    carries the two exchanges a step needs: the domain's mass (a sum over ranks, for
-    Eq. Gravity_2) and the ghost rows (``exchange_halos``).
+    carries the two exchanges a step needs: the domain's mass (the slabs' FP64 partials,
+    added element-wise over ranks, for Eq. Gravity_2) and the ghost rows
+    (``exchange_halos``). The partials vectors have the largest rank's length (a max over
+    ranks at set-up), zero beyond a rank's own count.
 
     params: lbm_params of the whole domain (p.ny = all rows; p.rho_ref the same on every
     rank); slab: this rank's ``Slab``; rho0_own: its rows of the initial density, a torch
@@ -182,19 +189,21 @@ class SlabLattice:
         dtype = torch.float32 if params.precision == lbm.LBM_FP32 else torch.float64
         self.f = [torch.zeros((9, slab.rows, params.nx), dtype=dtype, device="cuda") for _ in range(2)]
         self.cur = 0
-        self.part = torch.empty(lbm.lbm_slab_partials(params, self.s), dtype=torch.float64, device="cuda")
-        self.mass = [torch.zeros(1, dtype=torch.float64, device="cuda") for _ in range(2)]
+        count = torch.tensor([float(lbm.lbm_slab_partials(params, self.s))], dtype=torch.float64, device="cuda")
+        comm.max_(count)
+        npart = int(count.item())
+        self.part = [torch.zeros(npart, dtype=torch.float64, device="cuda") for _ in range(2)]
         self.status = torch.zeros(1, dtype=torch.int32, device="cuda")
         stream = self._stream()
         lbm.lbm_slab_init(params, self.s, rho0_own.contiguous(), self.f[0], stream)
-        lbm.lbm_slab_mass(params, self.s, self.f[0], self.part, self.mass[0], stream)
+        lbm.lbm_slab_mass(params, self.s, self.f[0], self.part[0], stream)
         # ghost-row exchange buffers, allocated once
         self.bufs = {}
         for peer in (slab.lower, slab.upper):
             if peer is not None:
                 for kind in ("send", "recv"):
                     self.bufs[(kind, peer)] = torch.empty((9, HALO, params.nx), dtype=dtype, device="cuda")
-        comm.sum_(self.mass[0])
+        comm.sum_(self.part[0])
         exchange_halos(self.f[0], slab, comm, self.bufs)
         self.steps = 0
         # the step's library call with its arguments marshalled once (the buffers never move)
@@ -203,8 +212,8 @@ class SlabLattice:
         lib = lbm.load()
         self._call = lib.lbm_slab_step
         self._pp, self._sp = ctypes.byref(params), ctypes.byref(self.s)
-        self._ptr = {"f": [t.data_ptr() for t in self.f], "m": [t.data_ptr() for t in self.mass],
-                     "part": self.part.data_ptr(), "npart": int(self.part.numel()), "status": self.status.data_ptr()}
+        self._ptr = {"f": [t.data_ptr() for t in self.f], "part": [t.data_ptr() for t in self.part], "npart": npart,
+                     "status": self.status.data_ptr()}
 
     def _stream(self):
         return self._torch.cuda.current_stream().cuda_stream
@@ -216,25 +225,30 @@ class SlabLattice:
 
     def step(self, n=1):
         lbm, stream = self._lbm, self._stream()
-        pf, pm = self._ptr["f"], self._ptr["m"]
+        pf, pp, npart = self._ptr["f"], self._ptr["part"], self._ptr["npart"]
         for _ in range(n):
             c = self.cur
-            rc = self._call(self._pp, self._sp, pf[c], pf[1 - c], pm[c], self._ptr["part"], self._ptr["npart"],
-                            pm[1 - c], self._ptr["status"], stream)
+            rc = self._call(self._pp, self._sp, pf[c], pf[1 - c], pp[c], npart, pp[1 - c], npart, self._ptr["status"],
+                            stream)
             if rc != lbm.LBM_OK:
                 lbm._check(rc)
             self.cur ^= 1
-            self.comm.sum_(self.mass[self.cur])
+            self.comm.sum_(self.part[self.cur])
             exchange_halos(self.f[self.cur], self.slab, self.comm, self.bufs)
             self.steps += 1
 
+    @property
+    def mass(self):
+        """sum(rho - rho_ref) over the whole domain of the current state (host float)."""
+        return float(self.part[self.cur].sum().item())
+
     def snapshot(self):
-        return self.state.clone(), self.mass[self.cur].clone()
+        return self.state.clone(), self.part[self.cur].clone()
 
     def restore(self, snap):
         f, m = snap
         self.state.copy_(f)
-        self.mass[self.cur].copy_(m)
+        self.part[self.cur].copy_(m)
 
     def status_code(self):
         """LBM_OK, or LBM_ENONPHYS / LBM_ETIMEOUT from the status bits of this rank's steps."""
@@ -255,4 +269,7 @@ class SingleComm:
         return {}
 
     def sum_(self, t):
+        return t
+
+    def max_(self, t):
         return t

@@ -142,4 +142,4 @@ def test_slab_calls_reach_the_library_without_a_gpu():
         lbm.lbm_slab_partials(p, lbm.make_slab(8, 4))
     f = torch.zeros((9, 9, 16), dtype=torch.float64)
     with pytest.raises(ValueError, match="CUDA"):
-        lbm.lbm_slab_step(p, s, f, f, None, f, f, f)
+        lbm.lbm_slab_step(p, s, f, f, None, f, f)

@@ -41,6 +41,8 @@ class ThreadComm:
         self.barrier = threading.Barrier(world, timeout=120)
 
     def rank_view(self, rank):
+        import torch
+
         comm = self
 
         class View:
@@ -57,11 +59,17 @@ class ThreadComm:
                 return out
 
             def sum_(self, t):
-                comm.box[("sum", rank)] = t.clone()
+                return self._reduce(t, lambda a, b: a + b)
+
+            def max_(self, t):
+                return self._reduce(t, torch.maximum)
+
+            def _reduce(self, t, op):
+                comm.box[("red", rank)] = t.clone()
                 comm.barrier.wait()
-                total = comm.box[("sum", 0)].clone()
+                total = comm.box[("red", 0)].clone()
                 for r in range(1, comm.world):
-                    total += comm.box[("sum", r)]
+                    total = op(total, comm.box[("red", r)])
                 comm.barrier.wait()
                 t.copy_(total)
                 return t
@@ -137,14 +145,16 @@ def test_slab_arguments_are_checked():
     s = lbm.make_slab(0, 5)
     f = torch.zeros((9, 9, 16), dtype=torch.float64, device="cuda")
     part = torch.zeros(lbm.lbm_slab_partials(p, s), dtype=torch.float64, device="cuda")
-    m = torch.zeros(1, dtype=torch.float64, device="cuda")
+    part2 = torch.zeros_like(part)
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     with pytest.raises(lbm.LbmError, match="distinct"):
-        lbm.lbm_slab_step(p, s, f, f, m, part, m, st)
+        lbm.lbm_slab_step(p, s, f, f, part, part2, st)
+    with pytest.raises(lbm.LbmError, match="distinct"):
+        lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), part, part, st)
     with pytest.raises(ValueError, match="CUDA"):
-        lbm.lbm_slab_step(p, s, f.cpu(), f, m, part, m, st)
-    with pytest.raises(lbm.LbmError, match="part holds"):  # fewer partial slots than CTAs
-        lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), m, part[:1], m, st)
+        lbm.lbm_slab_step(p, s, f.cpu(), f, part, part2, st)
+    with pytest.raises(lbm.LbmError, match="part_out holds"):  # fewer partial slots than CTAs
+        lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), part, part2[:1], st)
 
 
 @pytest.mark.parametrize("precision, nx, ny", [("fp32", 1024, 4096), ("fp64", 1024, 4096), ("fp32", 64, 40)])
