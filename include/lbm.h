@@ -408,7 +408,8 @@ int lbm_slab_partials(const lbm_params* p, const lbm_slab* s, int* count);
  * rows untouched. */
 int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, void* f, void* stream);
 /* The FP64 mass partials of the own rows of f (device): part[0 .. lbm_slab_partials) (npart >=
- * that, else LBM_EINVAL). Their sum, over all slabs, is sum(rho - rho_ref) of the domain. */
+ * that, else LBM_EINVAL; the rest of part set to zero). Their sum, over all slabs, is
+ * sum(rho - rho_ref) of the domain. */
 int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double* part, int npart, void* stream);
 /* One time step of the own rows, f_out = step(f_in) (distinct buffers; f_in's ghost rows must
  * hold the neighbours' rows of the same state). part_in: device, npart_in doubles whose sum is
@@ -416,7 +417,7 @@ int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double*
  * previous step's part_out) added element-wise over all slabs, zero-padded to a common length;
  * read for Eq. Gravity_2 only (may be NULL otherwise) and summed in a fixed order. Writes
  * part_out (device, distinct from part_in, npart_out >= lbm_slab_partials, else LBM_EINVAL;
- * entries beyond lbm_slab_partials untouched): this slab's partials of f_out. status: device
+ * entries beyond lbm_slab_partials set to zero): this slab's partials of f_out. status: device
  * int the kernel ORs LBM status bits into (1: non-physical, 2: a bounded wait timed out); the
  * caller zeroes it and reads it after the stream completes. */
 int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void* f_out, const double* part_in,

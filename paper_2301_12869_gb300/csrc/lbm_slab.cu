@@ -202,7 +202,9 @@ int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double*
     slab_partials_kernel<float><<<P, 256, 0, st>>>(static_cast<const float*>(f), p->nx, t.ny, s->ny_own, part);
   else
     slab_partials_kernel<double><<<P, 256, 0, st>>>(static_cast<const double*>(f), p->nx, t.ny, s->ny_own, part);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  // the entries past this slab's count are zero: an element-wise sum over ranks adds them
+  if (e == cudaSuccess && npart > P) e = cudaMemsetAsync(part + P, 0, sizeof(double) * size_t(npart - P), st);
   if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -231,8 +233,12 @@ int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void
   io.npart_in = form2 ? npart_in : 0;
   io.part_out = part_out;
   io.status = status;
-  const cudaError_t e =
+  cudaError_t e =
       lbm::launch_step(p->precision, lbm::MODE_STEP, t, lbm::phys_from_params(*p, slab_rho_ref(p)), io, st);
+  // the entries past this slab's count are zero (the buffer may hold the last sum over ranks)
+  const int P = t.nbands * t.nstrips;
+  if (e == cudaSuccess && npart_out > P)
+    e = cudaMemsetAsync(part_out + P, 0, sizeof(double) * size_t(npart_out - P), st);
   if (e != cudaSuccess) return fail(LBM_ECUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
