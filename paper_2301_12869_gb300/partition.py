@@ -239,8 +239,9 @@ class SlabLattice:
 
     @property
     def mass(self):
-        """sum(rho - rho_ref) over the whole domain of the current state (host float)."""
-        return float(self.part[self.cur].sum().item())
+        """sum(rho - rho_ref) over the whole domain of the current state (host float; the
+        partials are copied back and added on the host in index order)."""
+        return float(np.sum(self.part[self.cur].cpu().numpy()))
 
     def snapshot(self):
         return self.state.clone(), self.part[self.cur].clone()
