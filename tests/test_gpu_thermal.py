@@ -112,6 +112,34 @@ def test_fp64_steps_match_oracle(nx, ny, form, taus):
         lbm.lbm_destroy(h)
 
 
+@pytest.mark.parametrize("nx, ny, form, wall", [
+    (5, 17, 2, lbm.LBM_WALL_BOUNCE_BACK),   # 5 columns wrapped over a warp; a one-row second strip
+    (29, 33, 2, lbm.LBM_WALL_ZOU_HE),       # one column past a warp's 28 owned; <rho> in the wall closure
+    (40, 3, 1, lbm.LBM_WALL_BOUNCE_BACK),   # three rows: both wall ghosts within one short walk
+    (64, 4, 2, lbm.LBM_WALL_ZOU_HE),        # two fluid rows between the wall nodes
+    (30, 48, 1, lbm.LBM_WALL_ZOU_HE),       # three full strips, Zou-He with rho g
+])
+def test_fp64_energy_walk_edges_match_oracle(nx, ny, form, wall):
+    """The Heun strip walk at its edges, with rho and u of the moments pass: lattices
+    narrower than a warp (x wraps within it), one column past a warp's owned columns, a
+    few rows (both wall ghosts inside one walk), strips ending one row past a boundary,
+    and Zou-He walls with (rho - <rho>) g in the wall closure."""
+    p = thermal_params(nx, ny, "fp64", form=form, g=(2e-6, -5e-5), wall=wall)
+    op, th = oracle_of(p)
+    op.wall = "zou-he" if wall == lbm.LBM_WALL_ZOU_HE else "bounce-back"
+    h, f, T = start(p, column(nx, ny, liquid=max(1, ny // 2)))
+    try:
+        for n in range(6):
+            f, T = oth.thermal_step(f, T, op, th)
+            lbm.lbm_step(h, 1)
+            fg, Tg = read(h, p)
+            assert np.max(np.abs(fg - f)) <= 1e-14, n
+            assert np.max(np.abs(Tg - T)) <= 1e-14, n
+        assert lbm.lbm_status(h) == lbm.LBM_OK
+    finally:
+        lbm.lbm_destroy(h)
+
+
 def test_fp64_300_steps_match_oracle():
     nx, ny = 8, 48
     p = thermal_params(nx, ny, "fp64", g=(0.0, -5e-5))
