@@ -1400,10 +1400,10 @@ def main(argv=None):
         mass = e2e["mass"] if e2e else None
         info = {"column_rows": ny_total, "slab_rows_rank0": sl.ny_own, "ghost_rows_per_side": 2,
                 "exchange_bytes_per_step_per_rank": halo_bytes,
-                "exchanges_per_step": "NCCL all-reduce of the mass (8 B) + send/receive of 2 ghost rows x 9 planes "
-                                      "with each neighbour"}
+                "exchanges_per_step": "NCCL all-reduce of the FP64 mass partials (one per CTA of the largest "
+                                      "slab's grid) + send/receive of 2 ghost rows x 9 planes with each neighbour"}
         scaling, parallelism = args.slab_scaling, f"y-slabs x{world}"
-        launches = 2 * args.steps  # slab step + its partial-sum kernel per step
+        launches = args.steps  # one slab step kernel per step (the exchanges are NCCL's and torch's copies)
         kernel_name = "step_kernel_ws on the rank's slab (+ exchanges, per step)"
         torch.cuda.empty_cache()
     else:

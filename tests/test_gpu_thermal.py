@@ -113,15 +113,15 @@ def test_fp64_steps_match_oracle(nx, ny, form, taus):
 
 
 @pytest.mark.parametrize("nx, ny, form, wall", [
-    (5, 17, 2, lbm.LBM_WALL_BOUNCE_BACK),   # 5 columns wrapped over a warp; a one-row second strip
-    (29, 33, 2, lbm.LBM_WALL_ZOU_HE),       # one column past a warp's 28 owned; <rho> in the wall closure
+    (6, 17, 2, lbm.LBM_WALL_BOUNCE_BACK),   # 6 columns wrapped over a warp; a one-row second strip
+    (30, 33, 2, lbm.LBM_WALL_ZOU_HE),       # two columns past a warp's 28 owned; <rho> in the wall closure
     (40, 3, 1, lbm.LBM_WALL_BOUNCE_BACK),   # three rows: both wall ghosts within one short walk
     (64, 4, 2, lbm.LBM_WALL_ZOU_HE),        # two fluid rows between the wall nodes
-    (30, 48, 1, lbm.LBM_WALL_ZOU_HE),       # three full strips, Zou-He with rho g
+    (58, 48, 1, lbm.LBM_WALL_ZOU_HE),       # three full strips over two warps and two columns, rho g
 ])
 def test_fp64_energy_walk_edges_match_oracle(nx, ny, form, wall):
     """The Heun strip walk at its edges, with rho and u of the moments pass: lattices
-    narrower than a warp (x wraps within it), one column past a warp's owned columns, a
+    narrower than a warp (x wraps within it), a column block just past a warp's, a
     few rows (both wall ghosts inside one walk), strips ending one row past a boundary,
     and Zou-He walls with (rho - <rho>) g in the wall closure."""
     p = thermal_params(nx, ny, "fp64", form=form, g=(2e-6, -5e-5), wall=wall)
