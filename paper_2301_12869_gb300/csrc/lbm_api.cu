@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -169,8 +170,8 @@ int plan_tiling(const lbm_params& p, int nsm, lbm::StepTiling* t, char* err, int
     set_err(err, "internal: band width %d not a multiple of %d", t->band_w, H);
     return LBM_EINVAL;
   }
-  int per_sm = lbm::step_max_ctas_per_sm(p.precision, variant, t->threads, t->smem_bytes);
-  if (per_sm < 1) per_sm = 1;
+  int per_sm = 1;
+  if (int rc = lbm::step_ctas_per_sm(p.precision, variant, t->threads, t->smem_bytes, &per_sm, err)) return rc;
   // one wave: every CTA resident at once, so neighbouring strips stream their shared
   // halo rows at the same time
   const long target = long(nsm) * per_sm;
@@ -348,6 +349,50 @@ int run_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
 
 // ---- wrappers for the other translation units (lbm_internal.h)
 namespace lbm {
+namespace {
+constexpr int kMaxDevices = 64;
+constexpr int kMaxVariants = 16;
+}  // namespace
+
+int prepare_step_kernels(int dev, int precision, char* err) {
+  static std::atomic<bool> ready[kMaxDevices][2];
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_err(err, "device index %d beyond the %d this library supports", dev, kMaxDevices);
+    return LBM_EINVAL;
+  }
+  std::atomic<bool>& r = ready[dev][precision == LBM_FP32 ? 1 : 0];
+  if (!r.load(std::memory_order_acquire)) {  // two threads may both set it: the same values
+    const cudaError_t e = step_prepare(precision);
+    if (e != cudaSuccess) {
+      set_err(err, "kernel attributes: %s", cudaGetErrorString(e));
+      return LBM_ECUDA;
+    }
+    r.store(true, std::memory_order_release);
+  }
+  return LBM_OK;
+}
+
+int step_ctas_per_sm(int precision, int variant, int threads, int smem_bytes, int* per_sm, char* err) {
+  // cache entries hold the count + 1 (0: not asked yet); the threads and shared memory of a
+  // variant are fixed, so (device, precision, variant) is the key
+  static std::atomic<int> cache[kMaxDevices][2][kMaxVariants];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_err(err, "no CUDA device");
+    return LBM_ECUDA;
+  }
+  if (int rc = prepare_step_kernels(dev, precision, err)) return rc;  // the query depends on the limit
+  std::atomic<int>* slot = variant >= 0 && variant < kMaxVariants ? &cache[dev][precision == LBM_FP32 ? 1 : 0][variant]
+                                                                   : nullptr;
+  int n = slot ? slot->load(std::memory_order_acquire) - 1 : -1;
+  if (n < 0) {
+    n = std::max(1, step_max_ctas_per_sm(precision, variant, threads, smem_bytes));
+    if (slot) slot->store(n + 1, std::memory_order_release);
+  }
+  *per_sm = n;
+  return LBM_OK;
+}
+
 int validate_params(const lbm_params* p, char* err) { return validate(p, err); }
 StepPhys phys_from_params(const lbm_params& p, double rho_ref) { return phys_of(p, rho_ref); }
 int plan_step_tiling(const lbm_params& p, int nsm, StepTiling* t, char* err) { return plan_tiling(p, nsm, t, err); }
@@ -384,12 +429,7 @@ int lbm_workspace_bytes(const lbm_params* p, uint64_t* bytes) {
     return LBM_ECUDA;
   }
   // the grid plan depends on the occupancy the kernels reach with their shared-memory
-  // limit set, as in lbm_init
-  const cudaError_t e = lbm::step_prepare(p->precision);
-  if (e != cudaSuccess) {
-    set_err(g_err, "kernel attributes: %s", cudaGetErrorString(e));
-    return LBM_ECUDA;
-  }
+  // limit set, as in lbm_init (plan_tiling sets it first)
   lbm::StepTiling t;
   if ((rc = plan_tiling(*p, nsm, &t, g_err))) return rc;
   const int cap = max_partials(*p, nsm, g_err);
@@ -421,9 +461,9 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
     set_err(h->err, "no CUDA device");
     return fail(LBM_ECUDA);
   }
-  cudaError_t e = lbm::step_prepare(p->precision);
-  if (e != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return fail(LBM_ECUDA); }
+  if ((rc = lbm::prepare_step_kernels(h->dev, p->precision, h->err))) return fail(rc);
   if ((rc = plan_tiling(*p, h->nsm, &h->tiling, h->err))) return fail(rc);
+  cudaError_t e = cudaSuccess;
   h->P = h->tiling.nbands * h->tiling.nstrips;
   h->Pcap = max_partials(*p, h->nsm, h->err);
   if (h->Pcap < 0) return fail(LBM_EINVAL);

@@ -116,6 +116,12 @@ struct TraceRange {
 // ---- host helpers of lbm_api.cu shared with other entry points (same behaviour as lbm_init's)
 int validate_params(const lbm_params* p, char* err);  // err: 512 bytes
 StepPhys phys_from_params(const lbm_params& p, double rho_ref);
+// step_prepare once per device and precision (thread-safe; a failure is not remembered):
+// every grid plan needs it first, since the occupancy query depends on the limit it sets
+int prepare_step_kernels(int dev, int precision, char* err);
+// resident step CTAs per SM of a tile variant on the current device (at least 1), asked
+// once per device, precision and variant after prepare_step_kernels
+int step_ctas_per_sm(int precision, int variant, int threads, int smem_bytes, int* per_sm, char* err);
 int plan_step_tiling(const lbm_params& p, int nsm, StepTiling* t, char* err);  // default variant
 void set_last_error(const char* msg);  // text returned by lbm_last_error(NULL)
 

@@ -18,7 +18,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,31 +25,10 @@
 namespace {
 
 constexpr int kHalo = LBM_SLAB_HALO;
-constexpr int kMaxDevices = 64;
 
 int fail(int code, const char* msg) {
   lbm::set_last_error(msg);
   return code;
-}
-
-// The step kernels' shared-memory limit, once per device and precision. It must be set
-// before a plan is made: the occupancy query that sizes the grid depends on it.
-int prepare_once(int dev, int precision, char* err) {
-  static std::atomic<bool> prepared[kMaxDevices][2];
-  if (dev < 0 || dev >= kMaxDevices) {
-    snprintf(err, 512, "device index beyond the %d this entry point supports", kMaxDevices);
-    return LBM_EINVAL;
-  }
-  std::atomic<bool>& ready = prepared[dev][precision == LBM_FP32 ? 1 : 0];
-  if (!ready.load()) {
-    const cudaError_t e = lbm::step_prepare(precision);
-    if (e != cudaSuccess) {
-      snprintf(err, 512, "kernel attributes: %s", cudaGetErrorString(e));
-      return LBM_ECUDA;
-    }
-    ready.store(true);
-  }
-  return LBM_OK;
 }
 
 // The step's tiling for a slab: strips over the own rows only, buffer rows, wall rows
@@ -97,7 +75,7 @@ int slab_tiling(const lbm_params* p, const lbm_slab* s, lbm::StepTiling* t, char
     snprintf(err, 512, "no CUDA device");
     return LBM_ECUDA;
   }
-  if ((rc = prepare_once(dev, p->precision, err))) return rc;
+  if ((rc = lbm::prepare_step_kernels(dev, p->precision, err))) return rc;
   lbm_params q = *p;
   q.ny = s->ny_own;  // strips over the own rows
   if ((rc = lbm::plan_step_tiling(q, nsm, t, err))) return rc;
