@@ -849,10 +849,10 @@ def time_to_steady(args, lbm, inputs, world, rank, torch):
 # ---------------------------------------------------------------- thermal variant
 TH_NX, TH_NY, TH_LIQUID = 512, 2048, 1024
 TH_TBOT, TH_TTOP, TH_GY = 0.95, 0.80, -5e-5
-# per node and step, as launched: fused step 72 B populations + 4 B T; moments pass 36 B
-# populations + 4 B T read, 12 B rho/u written; Heun kernel 4 B T + 12 B rho/u read, 4 B T
-# written (FP32 storage, rho and u handed over as floats; FP64 storage doubles every term)
-TH_BYTES_PER_NODE = {"fp32": 76 + 52 + 20, "fp64": 152 + 104 + 40}
+# per node and step, as launched: fused step 72 B populations + 4 B T read, 12 B rho/u
+# written; Heun kernel 4 B T + 12 B rho/u read, 4 B T written (FP32 storage, rho and u
+# handed over as floats; FP64 storage doubles every term)
+TH_BYTES_PER_NODE = {"fp32": 88 + 20, "fp64": 176 + 40}
 # The heated column goes non-physical: its 1024 vapour rows weigh more than the vapour's
 # saturation pressure can carry at g_y = -5e-5 (scale height of the vapour ~100 rows), so
 # the vapour falls freely and the top empties (max |u| = |g| t) within ~5000 steps. Timed
@@ -905,8 +905,9 @@ def crossing_heights(lbm, h, Tc):
 
 
 def run_thermal(args, torch, lbm, inputs):
-    """Throughput of the thermal step (fused LBM step with T(x) in psi, moments pass, two
-    Heun stages of the energy equation) on the 512 x 2048 heated-from-below column; with
+    """Throughput of the thermal step (fused LBM step with T(x) in psi that also stores
+    rho, u; one launch for the two Heun stages of the energy equation) on the 512 x 2048
+    heated-from-below column; with
     --thermal-track, config 4 in full (FP32 and FP64, --thermal-steps steps) with the
     liquid/vapour crossing heights every --thermal-every steps."""
     import numpy as np
@@ -954,9 +955,9 @@ def run_thermal(args, torch, lbm, inputs):
                    "l2": "state 151 MB (FP32) > 129 MB L2"},
         "roofline": {"bound": "hbm", "achieved": bytes_step / step_s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": bytes_step / step_s / 1e9 / peaks["hbm_gbs"], "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "whole thermal step (fused step, moments, Heun: 3 launches)",
+                     "kernel": "whole thermal step (fused step storing rho, u; Heun: 2 launches)",
                      "bytes_per_node": TH_BYTES_PER_NODE[args.precision]},
-        "gpu_launches": 3 * args.steps + restores * (9 + 1 + 1), "restores": restores,
+        "gpu_launches": 2 * args.steps + restores * (9 + 1 + 1), "restores": restores,
         "physical_window": f"populations and T restored from the post-warm-up snapshot every {TH_WINDOW} steps",
         "clocks": clocks.summary(), "status": status,
     }

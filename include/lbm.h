@@ -131,9 +131,9 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
  * one launch of the fused kernel: stream (and, with Zou-He walls, rebuild the wall nodes'
  * incoming populations), rho, psi, <rho>, F_int, F_g, u, MRT + Li forcing, store. Device-side faults (non-physical state, timeouts) are recorded in a
  * sticky status returned by the next synchronising call.
- * Thermal variant: psi uses R T(x) of the current temperature field; then a moments
- * launch gives rho and u of the new populations (as the next step evaluates them) and one
- * launch advances T by Heun's second-order Runge-Kutta (dt = 1) on Eq. Energy_Equation,
+ * Thermal variant: psi uses R T(x) of the current temperature field T^n, and the step
+ * also stores its rho^n and u^n; then one launch advances T^n by Heun's second-order
+ * Runge-Kutta (dt = 1) on Eq. Energy_Equation with those rho^n, u^n held fixed,
  * with isotropic D2Q9-weighted central differences and the wall temperatures T_bot, T_top
  * (ghost rows T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top; with Zou-He walls
  * the wall rows 0 and ny-1 hold T_bot and T_top). */

@@ -15,9 +15,10 @@ printing them; each is listed in the design notes):
   lap phi = (2/cs^2) sum_i w_i (phi(x + c_i) - phi(x));
 * Heun's second-order Runge-Kutta with the lattice time step dt = 1, rho and u
   held fixed during the step;
-* the energy update of a time step uses rho and u of the populations after that
-  step's collision, evaluated as the next step would (streamed, with the force of
-  the current temperature);
+* the energy update of a time step advances T^n with rho^n and u^n, the density and
+  the half-force velocity that step itself forms from the streamed populations (with
+  the force of T^n): every field of the right-hand side at the time level of T^n, an
+  explicit step of the coupled system;
 * walls: T = T_bot on the wall below row 0 and T_top above row ny-1 (half a link
   beyond the last rows, as for the populations), by ghost rows
   T(-1) = 2 T_bot - T(0), T(ny) = 2 T_top - T(ny-1); velocity ghosts vanish at the
@@ -116,10 +117,10 @@ def energy_step(T, rho, ux, uy, p, th):
 
 def thermal_step(fstar, T, p, th):
     """One time step of the thermal variant: the LBM step with the local temperature in
-    Eq. EOS, then the energy update with rho, u of the new populations."""
+    Eq. EOS, and the energy update of T with the rho and u of that step (time level n)."""
     pT = dataclasses.replace(p, T=T)
+    mac = lbm.macroscopic(fstar, pT)
     f_new = lbm.step(fstar, pT)
-    mac = lbm.macroscopic(f_new, pT)
     return f_new, energy_step(T, mac.rho, mac.u[0], mac.u[1], p, th)
 
 

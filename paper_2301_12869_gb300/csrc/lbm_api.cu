@@ -315,22 +315,6 @@ int refresh_partials(lbm_handle* h) {
   return LBM_OK;
 }
 
-// rho, u of the state as floats into the moment scratch (FP32 thermal handles, whose tile
-// is the barrier-free one): the energy step reads them without FP64 conversions
-int run_moments32(lbm_handle* h) {
-  lbm::StepIO io{};
-  io.Tfield = h->Tf;
-  io.fin = h->f[h->cur];
-  io.part_in = h->parts[h->pcur];
-  io.npart_in = h->npart;
-  io.status = h->status;
-  io.rho32 = reinterpret_cast<float*>(h->rho_now);
-  io.ux32 = reinterpret_cast<float*>(h->ux);
-  io.uy32 = reinterpret_cast<float*>(h->uy);
-  LBM_CUDA(h, lbm::launch_step(h->p.precision, lbm::MODE_MOMENTS, h->tiling, h->phys, io, h->stream));
-  return LBM_OK;
-}
-
 int run_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
   lbm::StepIO io{};
   io.Tfield = h->Tf;
@@ -548,6 +532,17 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   lbm::StepIO io{};
   io.status = h->status;
   const lbm_params& p = h->p;
+  if (p.thermal) {  // the step's rho, u for the energy equation: floats for FP32 handles
+    if (p.precision == LBM_FP32) {
+      io.rho32 = reinterpret_cast<float*>(h->rho_now);
+      io.ux32 = reinterpret_cast<float*>(h->ux);
+      io.uy32 = reinterpret_cast<float*>(h->uy);
+    } else {
+      io.rho_out = h->rho_now;
+      io.ux_out = h->ux;
+      io.uy_out = h->uy;
+    }
+  }
   for (int64_t t = 0; t < nsteps; ++t) {
     io.Tfield = h->Tf;
     io.fin = h->f[h->cur];
@@ -561,9 +556,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     h->npart = h->P;
     ++h->steps;
     if (p.thermal) {
-      // rho, u of the new populations with the force of T^n, then T^n -> T^(n+1)
-      int rc = p.precision == LBM_FP32 ? run_moments32(h) : run_moments(h, h->rho_now, h->ux, h->uy);
-      if (rc) return rc;
+      // T^n -> T^(n+1) with the rho^n, u^n this step formed (force of T^n)
       LBM_CUDA(h, lbm::launch_energy_step(p.precision, p.nx, p.ny, p.wall == LBM_WALL_ZOU_HE ? 1 : 0, p.R, p.b, p.c_v,
                                           p.kappa, p.T_bot, p.T_top, h->rho_now, h->ux, h->uy, h->Tf, h->Tnext,
                                           h->stream));

@@ -53,11 +53,11 @@ struct StepIO {
   int npart_in;
   double* part_out;        // one FP64 partial per CTA of sum_i g_i of fout (MODE_STEP)
   int* status;             // sticky device status word
-  double* rho_out;         // MODE_MOMENTS outputs, [y][x] doubles (may be NULL)
-  double* ux_out;
+  double* rho_out;         // MODE_MOMENTS outputs, [y][x] doubles (may be NULL); thermal FP64
+  double* ux_out;          // MODE_STEP: this step's rho, u for the energy equation (required)
   double* uy_out;
-  float* rho32;            // MODE_MOMENTS with FP32 storage, barrier-free tile: rho, u as floats
-  float* ux32;             // (may be NULL), [y][x]
+  float* rho32;            // thermal FP32 MODE_STEP (barrier-free tile): this step's rho, u as
+  float* ux32;             // floats, [y][x] (required there, unused elsewhere)
   float* uy32;
   const void* Tfield;      // thermal variant: real[ny][nx] temperature (NULL: uniform T)
 };

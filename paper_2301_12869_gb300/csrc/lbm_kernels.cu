@@ -128,8 +128,9 @@ __device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (
 // Template parameters: storage type T, value type V (T, or f2 for pairs of FP32 nodes),
 // mode, all-unit relaxation, band width BW (nodes along x per CTA), nodes per thread NPT
 // (threads = BW / NPT; a thread owns NPT / width(V) values), CTAs per SM the launch
-// bounds aim for; TH: thermal variant, psi uses R T(x) of the field io.Tfield (else R T);
-// ZH: Zou-He wet-node walls on rows 0 and ny - 1 (else halfway bounce-back).
+// bounds aim for; TH: thermal variant, psi uses R T(x) of the field io.Tfield (else R T),
+// and a step also stores each node's rho, u for the energy equation; ZH: Zou-He wet-node
+// walls on rows 0 and ny - 1 (else halfway bounce-back).
 // CTA b: x band (b % nbands) of width tl.band_w (<= BW), strip (b / nbands) of
 // tl.strip_h rows. Even strips walk their rows upward, odd strips downward, so two
 // neighbouring strips reach their common halo rows at the same time (L2 reuse).
@@ -282,6 +283,13 @@ __global__ void __launch_bounds__(BW / NPT, MINB) step_kernel(const StepTiling t
 #pragma unroll
         for (int i = 0; i < 9; ++i) *reinterpret_cast<V*>(dst + i * plane) = o[i];
         acc.add9(o);
+        if constexpr (TH) {  // this step's rho, u for the energy equation (Eq. Energy_Equation)
+          static_assert(VW == 1, "thermal instantiations are one node per value");
+          const size_t idx = size_t(y) * nx + xa + (j - 1);
+          io.rho_out[idx] = double(rho);
+          io.ux_out[idx] = double(ux);
+          io.uy_out[idx] = double(uy);
+        }
       } else {
         const size_t idx = size_t(y) * nx + xa + (j - 1);
         if constexpr (VW == 1) {
@@ -583,14 +591,17 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
 #pragma unroll
         for (int i = 0; i < 9; ++i) *reinterpret_cast<V*>(fout + node + i * plane) = o[i];
         acc.add(sum9(o));  // the node pair's stored values, summed in FP32 first
+        if constexpr (TH) {
+          // this step's rho, u for the energy equation (Eq. Energy_Equation) as floats: one
+          // aligned pair per lane, no FP64 conversion (slow on GB300)
+          *reinterpret_cast<V*>(io.rho32 + node) = rho;
+          *reinterpret_cast<V*>(io.ux32 + node) = ux;
+          *reinterpret_cast<V*>(io.uy32 + node) = uy;
+        }
       } else {
         if (io.rho_out) { io.rho_out[node] = lo(rho); io.rho_out[node + 1] = hi(rho); }
         if (io.ux_out) { io.ux_out[node] = lo(ux); io.ux_out[node + 1] = hi(ux); }
         if (io.uy_out) { io.uy_out[node] = lo(uy); io.uy_out[node + 1] = hi(uy); }
-        // FP32 outputs: one aligned pair per lane, no FP64 conversion (slow on GB300)
-        if (io.rho32) *reinterpret_cast<V*>(io.rho32 + node) = rho;
-        if (io.ux32) *reinterpret_cast<V*>(io.ux32 + node) = ux;
-        if (io.uy32) *reinterpret_cast<V*>(io.uy32 + node) = uy;
       }
     };
 

@@ -7,14 +7,15 @@
 // lap phi = 6 sum_i w_i (phi(x + c_i) - phi(x))), Heun's second-order Runge-Kutta with
 // dt = 1, and Dirichlet walls half a link beyond the first and last rows (ghost rows
 // T(-1) = 2 T_bot - T(0), u(-1) = -u(0), likewise at the top) - or, with Zou-He wet-node
-// walls, T held at T_bot and T_top on the wall rows 0 and ny - 1 themselves. rho and u come
-// from the moments pass that follows each LBM step.
+// walls, T held at T_bot and T_top on the wall rows 0 and ny - 1 themselves. rho and u are
+// those of the same time level as T: the fused LBM step stores them as it collides (the
+// streamed populations, the force of T^n).
 //
 // One launch does the whole Heun step (heun_strip_kernel below): each warp walks a strip
 // of rows with the stencil's rows held in registers, computing k1 and T* = T + k1 one row
 // ahead of k2, so both Heun stages run in one pass without shared memory or CTA
 // barriers. rho and u come in the field's own precision (FP32 handles get them as floats
-// from the moments pass: FP64 conversions are slow on GB300).
+// from the step: FP64 conversions are slow on GB300).
 #include "lbm_internal.h"
 #include "lbm_physics.cuh"
 #include "lbm_ptx.cuh"
@@ -79,7 +80,7 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kStripWarps) heun_strip_kernel(const EnergyArgs<T> a, const T* __restrict__ rho,
                                                                       const T* __restrict__ ux, const T* __restrict__ uy,
                                                                       const T* __restrict__ Tin, T* __restrict__ Tout) {
-  griddep_wait();  // launched as a dependent of the moments pass: rho, u are complete
+  griddep_wait();  // launched as a dependent of the step: rho, u are complete
   griddep_launch_dependents();
   const int nx = a.nx, ny = a.ny, lane = threadIdx.x;
   const int x0 = blockIdx.x * kOwn;

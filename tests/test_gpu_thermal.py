@@ -1,8 +1,8 @@
 """GPU parity of the thermal variant (Sec. III, Eq. Energy_Equation) against the FP64 oracle.
 
 The handle is created with thermal = 1: psi uses R T(x) of the temperature field, and
-after every LBM step the field is advanced by Heun's RK2 on the energy equation. The
-oracle is oracle.thermal.thermal_step. Tolerances:
+after every LBM step the field is advanced by Heun's RK2 on the energy equation with that
+step's rho and u. The oracle is oracle.thermal.thermal_step. Tolerances:
 * FP64: per-step checks |df|, |dT| <= 1e-14 as for the isothermal path. Two FP64
   oracles that differ only in the summation order of the finite-difference stencils
   drift apart by 2e-16 (f) and 2e-17 (T) over 1000 steps on this kind of column, so the
@@ -120,7 +120,7 @@ def test_fp64_steps_match_oracle(nx, ny, form, taus):
     (58, 48, 1, lbm.LBM_WALL_ZOU_HE),       # three full strips over two warps and two columns, rho g
 ])
 def test_fp64_energy_walk_edges_match_oracle(nx, ny, form, wall):
-    """The Heun strip walk at its edges, with rho and u of the moments pass: lattices
+    """The Heun strip walk at its edges, with rho and u stored by the step: lattices
     narrower than a warp (x wraps within it), a column block just past a warp's, a
     few rows (both wall ghosts inside one walk), strips ending one row past a boundary,
     and Zou-He walls with (rho - <rho>) g in the wall closure."""
@@ -280,8 +280,8 @@ def test_thermal_handle_keeps_a_thermal_tile(precision):
 
 def test_full_size_thermal_column_sampled():
     """The 512 x 2048 FP32 heated column of the thermal workload (bench.py's set-up, default
-    tile: the launch configuration it times): one thermal step - fused LBM step, moments
-    pass, Heun step - after 20, checked on sampled columns against the oracle run on a
+    tile: the launch configuration it times): one thermal step - fused LBM step storing
+    rho and u, Heun step - after 20, checked on sampled columns against the oracle run on a
     24-column strip around each column (full height, so the walls are exact; one thermal step
     reaches 6 columns, the strip's periodic seams are 12 away)."""
     import dataclasses
