@@ -315,6 +315,21 @@ int refresh_partials(lbm_handle* h) {
   return LBM_OK;
 }
 
+// A thermal step stores its rho, u for the energy equation in the handle's moment
+// scratch (floats for FP32 handles); isothermal steps store none.
+void set_thermal_outputs(lbm_handle* h, lbm::StepIO& io) {
+  if (!h->p.thermal) return;
+  if (h->p.precision == LBM_FP32) {
+    io.rho32 = reinterpret_cast<float*>(h->rho_now);
+    io.ux32 = reinterpret_cast<float*>(h->ux);
+    io.uy32 = reinterpret_cast<float*>(h->uy);
+  } else {
+    io.rho_out = h->rho_now;
+    io.ux_out = h->ux;
+    io.uy_out = h->uy;
+  }
+}
+
 int run_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
   lbm::StepIO io{};
   io.Tfield = h->Tf;
@@ -532,17 +547,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
   lbm::StepIO io{};
   io.status = h->status;
   const lbm_params& p = h->p;
-  if (p.thermal) {  // the step's rho, u for the energy equation: floats for FP32 handles
-    if (p.precision == LBM_FP32) {
-      io.rho32 = reinterpret_cast<float*>(h->rho_now);
-      io.ux32 = reinterpret_cast<float*>(h->ux);
-      io.uy32 = reinterpret_cast<float*>(h->uy);
-    } else {
-      io.rho_out = h->rho_now;
-      io.ux_out = h->ux;
-      io.uy_out = h->uy;
-    }
-  }
+  set_thermal_outputs(h, io);
   for (int64_t t = 0; t < nsteps; ++t) {
     io.Tfield = h->Tf;
     io.fin = h->f[h->cur];
@@ -782,6 +787,7 @@ int lbm_autotune(lbm_handle* h, int steps, int* variant, double* ms) {
   io.part_out = h->parts[1 - h->pcur];
   io.status = h->status;
   io.Tfield = h->Tf;
+  set_thermal_outputs(h, io);
   for (int v = 0; v < lbm::step_num_variants(h->p.precision) && rc == LBM_OK; ++v) {
     lbm::StepTiling t;
     if (plan_tiling(h->p, h->nsm, &t, h->err, v)) continue;

@@ -1015,6 +1015,10 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
   const dim3 grid(t.nbands * t.nstrips), block(t.threads);
   const bool unit = unit_relaxation(ph);
   const bool th = io.Tfield != nullptr, zh = ph.wall == LBM_WALL_ZOU_HE;
+  // a thermal step stores its rho, u: refuse a launch without somewhere to put them
+  if (th && mode == MODE_STEP &&
+      !(precision == 1 ? (io.rho32 && io.ux32 && io.uy32) : (io.rho_out && io.ux_out && io.uy_out)))
+    return cudaErrorInvalidValue;
   if (precision == 1) {
     const VariantF& v = kVariantsF[t.variant];
     if (th || zh) {

@@ -92,3 +92,27 @@ def test_zou_he_walls_hold_the_wall_temperatures():
     rng = np.random.default_rng(2)
     T2 = thermal.energy_step(T, rho, 1e-3 * rng.random((14, 6)), 1e-3 * rng.random((14, 6)), p, th)
     assert np.all(T2[0] == th.T_bot) and np.all(T2[-1] == th.T_top)
+
+
+def test_first_step_advances_T_with_the_fields_of_its_own_time_level():
+    """Coupling order (the paper gives none): T^n advances with rho^n and u^n. From rest at
+    uniform density and temperature those are rho0 and, by Eq. Momentum with no momentum,
+    u = F / (2 rho0) = g / 2 at every node (F = rho0 g; uniform psi exerts no Shan-Chen
+    force) - so the first step's T must be the Heun update with exactly these hand-built
+    fields, and not the one with the velocity after the step."""
+    nx, ny = 6, 10
+    rho0, gy = 0.3, -1e-3
+    p = lbm.Params(nx=nx, ny=ny, a=A, b=B, R=R, T=0.9 * T_C, g=(0.0, gy), form=1)
+    th = thermal.Thermal(T_bot=0.9 * T_C, T_top=0.9 * T_C)
+    T = np.full((ny, nx), 0.9 * T_C)
+    fstar = lbm.init_state(np.full((ny, nx), rho0))
+    f1, T1 = thermal.thermal_step(fstar, T, p, th)
+    rho = np.full((ny, nx), rho0)
+    want = thermal.energy_step(T, rho, np.zeros_like(rho), np.full_like(rho, 0.5 * gy), p, th)
+    np.testing.assert_allclose(T1, want, rtol=0, atol=1e-15)
+    # not vacuous: the wall ghosts u(-1) = -u(0) make div u and so the update non-zero there,
+    # and the velocity after the step (about 3 g / 2 in the bulk) gives another update
+    assert np.max(np.abs(T1 - T)) > 1e-7
+    mac1 = lbm.macroscopic(f1, p)
+    other = thermal.energy_step(T, mac1.rho, mac1.u[0], mac1.u[1], p, th)
+    assert np.max(np.abs(other - T1)) > 1e-7
