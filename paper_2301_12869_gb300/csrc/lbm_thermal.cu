@@ -29,7 +29,7 @@ template <typename T>
 struct EnergyArgs {
   int nx, ny;
   int wall_nodes;  // 1: rows 0 and ny - 1 are wall nodes at fixed temperature (Zou-He walls)
-  T R, b4, c_v, kappa, twoTbot, twoTtop, inv_cv;
+  T b4, kP, kZ, twoTbot, twoTtop;  // b/4, (2/3) kappa/c_v, R/c_v, 2 T_bot, 2 T_top
 };
 
 // the walk's value type: one FP64 column per lane, or a pair of neighbouring FP32 columns
@@ -53,11 +53,21 @@ __device__ __forceinline__ f2 recip(f2 x) { return make_f2(rcp_approx(lo(x)), rc
 // columns lie 2 .. 32 W - 3 from the warp's left edge own them (W = 1: lanes 2 .. 29; W =
 // 2: lanes 1 .. 30), the two columns at each edge are halo. x neighbours come from the
 // adjacent columns - the lane's other column or a shuffle from the next lane - and y
-// neighbours from a window of rows in registers: walking up, input row q (T, u, v and the
-// two rho coefficients) is loaded, k1 and T* = T + k1 are formed for row q - 1, and k2 and
-// T_new = T + (k1 + k2)/2 for row q - 2. k1 is valid one column in from the edges, so the
-// owned columns have T* on both sides. Each input value is loaded once per warp (plus
-// the halo columns and 2 + 2 halo rows of the strip).
+// neighbours from a window of rows in registers: walking up, input row q (T, u, v, rho) is
+// taken in, k1 and T* = T + k1 are formed for row q - 1, and k2 and T_new = T + (k1 + k2)/2
+// for row q - 2. k1 is valid one column in from the edges, so the owned columns have T* on
+// both sides.
+//
+// For fixed rho and u the right-hand side of Eq. Energy_Equation is linear in T, so at a
+// node it is a 9-point stencil L(phi) = sum_i a_i phi(x + c_i) whose weights follow from
+// the D2Q9-weighted differences (c_s^2 = 1/3, P = (2/3) kappa/(rho c_v), U = u/3, V = v/3):
+//   axis neighbours   a = P - U c_x - V c_y
+//   diagonal ones     a = (P - U c_x - V c_y)/4
+//   centre            a = -5 P - (R Z(eta)/c_v) div u
+// with div u = (1/3)[du(y) + v(y+1) - v(y-1)] + (1/12)[du(y+1) + du(y-1) + sv(y+1) - sv(y-1)],
+// du = u(x+1) - u(x-1), sv = v(x+1) + v(x-1) of each row. Both Heun stages apply the same
+// weights (k1 = L(T), k2 = L(T*)): they are formed once, at the first stage, and kept one
+// row for the second. The row loop is unrolled in full, so the windows rotate by renaming.
 template <typename V>
 __host__ __device__ constexpr int own_columns() {
   return 32 * VecTraits<V>::width - 4;
@@ -80,26 +90,52 @@ template <typename V>
 __device__ __forceinline__ Nb<V> affine(V a, V s, const Nb<V>& v) {  // a + s v, pointwise
   return {a + s * v.c, a + s * v.l, a + s * v.r};
 }
+// v(x + 1) - v(x - 1) and v(x + 1) + v(x - 1) at the lane's column(s)
+__device__ __forceinline__ double xdiff(double v) {
+  return __shfl_down_sync(0xffffffffu, v, 1) - __shfl_up_sync(0xffffffffu, v, 1);
+}
+__device__ __forceinline__ double xsum(double v) {
+  return __shfl_down_sync(0xffffffffu, v, 1) + __shfl_up_sync(0xffffffffu, v, 1);
+}
+__device__ __forceinline__ f2 xdiff(f2 v) {
+  const float a = lo(v), b = hi(v);
+  const float left = __shfl_up_sync(0xffffffffu, b, 1), right = __shfl_down_sync(0xffffffffu, a, 1);
+  return make_f2(b - left, right - a);
+}
+__device__ __forceinline__ f2 xsum(f2 v) {
+  const float a = lo(v), b = hi(v);
+  const float left = __shfl_up_sync(0xffffffffu, b, 1), right = __shfl_down_sync(0xffffffffu, a, 1);
+  return make_f2(left + b, a + right);
+}
 
-// Right-hand side of Eq. Energy_Equation at the lane's node(s) of row r from T on rows
-// r-1 (ts), r (tc), r+1 (tn), u, v on the same rows and the node's coefficients: the
-// D2Q9-weighted differences with w = 1/9 (axes) and 1/36 (diagonals).
 template <typename V>
-__device__ __forceinline__ V rate_nb(const Nb<V>& ts, const Nb<V>& tc, const Nb<V>& tn, const Nb<V>& us,
-                                     const Nb<V>& uc, const Nb<V>& un, const Nb<V>& vs, const Nb<V>& vc,
-                                     const Nb<V>& vn, V ck, V cz) {
-  const V w1 = cst<V>(1.0 / 9.0), w2 = cst<V>(1.0 / 36.0), three = cst<V>(3.0);
-  const V gx = w1 * (tc.r - tc.l) + w2 * ((tn.r - tn.l) + (ts.r - ts.l));
-  const V gy = w1 * (tn.c - ts.c) + w2 * ((tn.r + tn.l) - (ts.r + ts.l));
-  const V lap = w1 * ((tc.r + tc.l) + (tn.c + ts.c)) + w2 * ((tn.r + tn.l) + (ts.r + ts.l)) - cst<V>(5.0 / 9.0) * tc.c;
-  const V div = w1 * ((uc.r - uc.l) + (vn.c - vs.c)) + w2 * (((un.r - un.l) + (us.r - us.l)) + ((vn.r + vn.l) - (vs.r + vs.l)));
-  return (ck * (cst<V>(6.0) * lap) - (uc.c * (three * gx) + vc.c * (three * gy))) - tc.c * cz * (three * div);
+struct Weights {  // the stencil weights of one node row: centre, E, W, N, S, NE, NW, SE, SW
+  V c, e, w, n, s, ne, nw, se, sw;
+};
+template <typename V>
+__device__ __forceinline__ Weights<V> weights(V P, V U, V Vv, V ac) {
+  const V quarter = cst<V>(0.25);
+  const V q = quarter * P, p = quarter * (U + Vv), m = quarter * (U - Vv);
+  return {ac, P - U, P + U, P - Vv, P + Vv, q - p, q + m, q - m, q + p};
+}
+// L(phi) at the lane's node(s) from phi on the rows below (s), at (c) and above (n)
+template <typename V>
+__device__ __forceinline__ V apply(const Weights<V>& a, const Nb<V>& s, const Nb<V>& c, const Nb<V>& n) {
+  V r0 = a.c * c.c, r1 = a.n * n.c;
+  r0 = fmadd(a.e, c.r, r0);
+  r1 = fmadd(a.s, s.c, r1);
+  r0 = fmadd(a.w, c.l, r0);
+  r1 = fmadd(a.ne, n.r, r1);
+  r0 = fmadd(a.nw, n.l, r0);
+  r1 = fmadd(a.se, s.r, r1);
+  r0 = fmadd(a.sw, s.l, r0);
+  return r0 + r1;
 }
 
 template <typename T, typename V, int ROWS, int WARPS, int AHEAD>
-__global__ void __launch_bounds__(32 * WARPS) heun_strip_kernel(const EnergyArgs<T> a, const T* __restrict__ rho,
-                                                                const T* __restrict__ ux, const T* __restrict__ uy,
-                                                                const T* __restrict__ Tin, T* __restrict__ Tout) {
+__global__ void __launch_bounds__(32 * WARPS, 2) heun_strip_kernel(const EnergyArgs<T> a, const T* __restrict__ rho,
+                                                                   const T* __restrict__ ux, const T* __restrict__ uy,
+                                                                   const T* __restrict__ Tin, T* __restrict__ Tout) {
   griddep_wait();  // launched as a dependent of the step: rho, u are complete
   griddep_launch_dependents();
   constexpr int W = VecTraits<V>::width;
@@ -120,21 +156,14 @@ __global__ void __launch_bounds__(32 * WARPS) heun_strip_kernel(const EnergyArgs
   const int yb = min(ya + ROWS, ny);
   const bool walls = a.wall_nodes != 0;
   const V zero = cst<V>(0.0), half = cst<V>(0.5), one = cst<V>(1.0), mone = cst<V>(-1.0);
+  const V third = cst<V>(1.0 / 3.0), twelfth = cst<V>(1.0 / 12.0);
   const V twoTbot = splat<V>(a.twoTbot), twoTtop = splat<V>(a.twoTtop);
-  const V kappa = splat<V>(a.kappa), c_v = splat<V>(a.c_v), R = splat<V>(a.R), b4 = splat<V>(a.b4);
-  const V inv_cv = splat<V>(a.inv_cv);
+  const V kP = splat<V>(a.kP), kZ = splat<V>(a.kZ), b4 = splat<V>(a.b4);
   auto load = [&](const T* p, size_t n) { return *reinterpret_cast<const V*>(p + n); };
-  // windows (row index relative to the input row q of the current iteration)
-  Nb<V> t0{}, t1{}, t2{};            // T rows q-2, q-1, q
-  Nb<V> u0{}, u1{}, u2{}, u3{};      // u rows q-3 .. q
-  Nb<V> v0{}, v1{}, v2{}, v3{};      // v rows q-3 .. q
-  Nb<V> s0{}, s1{}, s2{};            // T* rows q-3, q-2, q-1
-  V ckA = zero, czA = zero, ckB = zero, czB = zero, ckC = zero, czC = zero;  // coefficients, rows q-2, q-1, q
-  V k1a = zero, k1b = zero;          // k1 of rows q-2 (a) and q-1 (b)
-  // Input rows are loaded AHEAD iterations before they are used (a ring of raw T, u, v,
-  // rho in registers), so the global-load latency overlaps the work of the rows before.
-  // A row outside the strip's range, or beyond the walls, loads nothing.
-  const int q_first = ya - 2, q_last = yb + 1;
+  // Input rows are loaded AHEAD rows before they are used (a ring of raw T, u, v, rho in
+  // registers), so the global-load latency overlaps the work of the rows before. A row
+  // outside the strip's range, or beyond the walls, loads nothing.
+  const int q_last = yb + 1;
   struct Raw {
     V t, u, v, r;
   };
@@ -152,57 +181,70 @@ __global__ void __launch_bounds__(32 * WARPS) heun_strip_kernel(const EnergyArgs
   };
   Raw ring[AHEAD];
 #pragma unroll
-  for (int d = 0; d < AHEAD; ++d) fetch(q_first + d, ring[d]);
-  for (int q = q_first; q <= q_last; ++q) {
-    // ---- input row q: T, u, v with the wall ghosts, and the rho coefficients
-    Raw in = ring[0];
+  for (int d = 0; d < AHEAD; ++d) fetch(ya - 2 + d, ring[d]);
+  // windows (row index relative to the input row q of the current iteration)
+  Nb<V> t0{}, t1{}, t2{};                     // T rows q-2, q-1, q
+  Nb<V> s0{}, s1{}, s2{};                     // T* rows q-3, q-2, q-1
+  V du0 = zero, du1 = zero, du2 = zero;       // du rows q-2, q-1, q
+  V vc0 = zero, vc1 = zero, vc2 = zero;       // v rows q-2, q-1, q
+  V sv0 = zero, sv1 = zero, sv2 = zero;       // sv rows q-2, q-1, q
+  V U1 = zero, U2 = zero, P1 = zero, P2 = zero, Z1 = zero, Z2 = zero;  // rows q-1, q
+  Weights<V> wB{zero, zero, zero, zero, zero, zero, zero, zero, zero};  // weights of row q-2
+  V k1B = zero;                                                         // k1 of row q-2
 #pragma unroll
-    for (int d = 0; d + 1 < AHEAD; ++d) ring[d] = ring[d + 1];
-    fetch(q + AHEAD, ring[AHEAD - 1]);
+  for (int it = 0; it < ROWS + 4; ++it) {
+    const int q = ya - 2 + it;
+    // ---- input row q: T, u, v with the wall ghosts, and the rho-dependent factors
+    const Raw in = ring[it % AHEAD];
+    if (it + AHEAD < ROWS + 4) fetch(q + AHEAD, ring[it % AHEAD]);
     V tq = in.t, uq = in.u, vq = in.v;
-    V ckq = zero, czq = zero;
+    V Pq = zero, Zq = zero;
     const bool real = q >= 0 && q < ny;
     const bool ghost = !walls && (q == -1 || q == ny);
-    if (real || ghost) {
-      if (ghost) {  // T(-1) = 2 T_bot - T(0), u(-1) = -u(0); likewise above the top row
-        tq = (q < 0 ? twoTbot : twoTtop) - tq;
-        uq = zero - uq;
-        vq = zero - vq;
-      } else {
-        const V rh = in.r;
-        const V eta = b4 * rh;
-        const V om = one - eta;
-        ckq = kappa * recip(rh * c_v);
-        czq = R * (one + eta * (one + eta * (one - eta))) * recip(om * om * om) * inv_cv;
-      }
+    if (ghost) {  // T(-1) = 2 T_bot - T(0), u(-1) = -u(0); likewise above the top row
+      tq = (q < 0 ? twoTbot : twoTtop) - tq;
+      uq = zero - uq;
+      vq = zero - vq;
+    } else if (real) {
+      const V rh = in.r;
+      const V eta = b4 * rh;
+      const V om = one - eta;
+      Pq = kP * recip(rh);                                                        // (2/3) kappa/(rho c_v)
+      Zq = kZ * fmadd(eta, fmadd(eta, om, one), one) * recip(om * om * om);       // R Z(eta)/c_v
     }
     t0 = t1; t1 = t2; t2 = nb(tq);
-    u0 = u1; u1 = u2; u2 = u3; u3 = nb(uq);
-    v0 = v1; v1 = v2; v2 = v3; v3 = nb(vq);
-    ckA = ckB; czA = czB; ckB = ckC; czB = czC; ckC = ckq; czC = czq;
-    // ---- k1 and T* of row r1 = q - 1 (rows r1-1, r1, r1+1 are t0, t1, t2)
+    du0 = du1; du1 = du2; du2 = xdiff(uq);
+    vc0 = vc1; vc1 = vc2; vc2 = vq;
+    sv0 = sv1; sv1 = sv2; sv2 = xsum(vq);
+    U1 = U2; U2 = third * uq;
+    P1 = P2; P2 = Pq;
+    Z1 = Z2; Z2 = Zq;
+    // ---- weights, k1 and T* of row r1 = q - 1 (T rows r1-1, r1, r1+1 are t0, t1, t2)
     const int r1 = q - 1;
+    Weights<V> wA{zero, zero, zero, zero, zero, zero, zero, zero, zero};
     V k1 = zero;
-    if (r1 >= 0 && r1 < ny && !(walls && (r1 == 0 || r1 == ny - 1)))
-      k1 = rate_nb(t0, t1, t2, u1, u2, u3, v1, v2, v3, ckB, czB);
+    if (it >= 1 && r1 >= 0 && r1 < ny && !(walls && (r1 == 0 || r1 == ny - 1))) {
+      const V div = fmadd(third, du1 + (vc2 - vc0), twelfth * ((du2 + du0) + (sv2 - sv0)));
+      wA = weights(P1, U1, third * vc1, fmadd(cst<V>(-5.0), P1, zero - Z1 * div));
+      k1 = apply(wA, t0, t1, t2);
+    }
     s0 = s1; s1 = s2;
     s2 = nb(t1.c + k1);
     if (!walls && r1 == 0) s1 = affine(twoTbot, mone, s2);     // T*(-1) = 2 T_bot - T*(0)
     if (!walls && r1 == ny) s2 = affine(twoTtop, mone, s1);    // T*(ny) = 2 T_top - T*(ny-1)
-    k1a = k1b;
-    k1b = k1;
     // ---- k2 and T_new of row r2 = q - 2 (T* rows r2-1 .. r2+1 are s0, s1, s2)
     const int r2 = q - 2;
-    if (r2 >= ya && r2 < yb && own) {
+    if (it >= 2 && r2 >= ya && r2 < yb && own) {
       V tn;
       if (walls && (r2 == 0 || r2 == ny - 1)) {
         tn = half * (r2 == 0 ? twoTbot : twoTtop);  // wall node: T_bot / T_top
       } else {
-        const V k2 = rate_nb(s0, s1, s2, u0, u1, u2, v0, v1, v2, ckA, czA);
-        tn = t0.c + half * (k1a + k2);
+        tn = fmadd(half, k1B + apply(wB, s0, s1, s2), t0.c);
       }
       *reinterpret_cast<V*>(Tout + size_t(r2) * nx + x) = tn;
     }
+    wB = wA;
+    k1B = k1;
   }
 }
 
@@ -224,23 +266,22 @@ unsigned rows_grid(int rows) { return unsigned(rows < 65535 ? rows : 65535); }
 cudaError_t launch_energy_step(int precision, int nx, int ny, int wall_nodes, double R, double b, double c_v,
                                double kappa, double T_bot, double T_top, const void* rho, const void* ux,
                                const void* uy, const void* Tin, void* Tout, cudaStream_t stream) {
+  // 8-row strips: 2304 warps on the 512 x 2048 column, two 8-warp CTAs per SM
+  constexpr int kRows = 8, kWarps = 8, kAhead = 2;
+  const int strips = (ny + kRows - 1) / kRows;
   if (precision == 1) {
-    constexpr int kRows = 16, kWarps = 8, kAhead = 4;
-    const int strips = (ny + kRows - 1) / kRows;
     const dim3 grid((nx + own_columns<f2>() - 1) / own_columns<f2>(), (strips + kWarps - 1) / kWarps),
         block(32, kWarps);
-    const EnergyArgs<float> a{nx, ny, wall_nodes, float(R), float(b / 4.0), float(c_v), float(kappa),
-                              float(2.0 * T_bot), float(2.0 * T_top), float(1.0 / c_v)};
+    const EnergyArgs<float> a{nx, ny, wall_nodes, float(b / 4.0), float(2.0 * kappa / (3.0 * c_v)), float(R / c_v),
+                              float(2.0 * T_bot), float(2.0 * T_top)};
     return launch_dependent(heun_strip_kernel<float, f2, kRows, kWarps, kAhead>, grid, block, 0, stream, a,
                             static_cast<const float*>(rho), static_cast<const float*>(ux),
                             static_cast<const float*>(uy), static_cast<const float*>(Tin),
                             static_cast<float*>(Tout));
   }
-  constexpr int kRows = 16, kWarps = 8, kAhead = 4;
-  const int strips = (ny + kRows - 1) / kRows;
   const dim3 grid((nx + own_columns<double>() - 1) / own_columns<double>(), (strips + kWarps - 1) / kWarps),
       block(32, kWarps);
-  const EnergyArgs<double> a{nx, ny, wall_nodes, R, b / 4.0, c_v, kappa, 2.0 * T_bot, 2.0 * T_top, 1.0 / c_v};
+  const EnergyArgs<double> a{nx, ny, wall_nodes, b / 4.0, 2.0 * kappa / (3.0 * c_v), R / c_v, 2.0 * T_bot, 2.0 * T_top};
   return launch_dependent(heun_strip_kernel<double, double, kRows, kWarps, kAhead>, grid, block, 0, stream, a,
                           static_cast<const double*>(rho), static_cast<const double*>(ux),
                           static_cast<const double*>(uy), static_cast<const double*>(Tin),
