@@ -392,7 +392,8 @@ int lbm_mlp_destroy(lbm_mlp* h);
  * rows (2 rows x 9 planes each way) and adds the slabs' mass partials element-wise for <rho>
  * of Eq. Gravity_2 over the whole domain (both by its own communication, e.g. NCCL). p->rho_ref must be the same
  * on every slab (NaN means 0). These calls allocate nothing, are asynchronous on `stream`
- * (a cudaStream_t, NULL = default) and take only device pointers. Isothermal only. A slab
+ * (a cudaStream_t, NULL = default) and take only device pointers; slab buffers start on a
+ * 16-byte boundary (the step's bulk copies; else LBM_EINVAL). Isothermal only. A slab
  * with a neighbour needs ny_own >= LBM_SLAB_HALO. Errors: LBM_EINVAL, LBM_ECUDA. */
 #define LBM_SLAB_HALO 2
 typedef struct lbm_slab {
@@ -434,9 +435,10 @@ int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void
  * f_in, f_out: distinct DEVICE arrays (of the current device, or managed memory) of
  *   9*nx*ny reals (float for LBM_FP32, double for LBM_FP64), layout [i][y][x] in the order
  *   of Eq. VelocitySet, holding the deviations f_i - w_i rho_ref with rho_ref = p->rho_ref
- *   (NaN means 0). Caller-owned; read / written. A pointer that is not device memory is
- *   rejected (LBM_EINVAL); the element type and count cannot be checked here and are the
- *   caller's to get right (the Python binding checks them).
+ *   (NaN means 0), each starting on a 16-byte boundary. Caller-owned; read / written. A
+ *   pointer that is not device memory, or not 16-byte aligned, is rejected (LBM_EINVAL);
+ *   the element type and count cannot be checked here and are the caller's to get right
+ *   (the Python binding checks them).
  * p: as for lbm_init, isothermal (thermal = 0), any wall; p->workspace is ignored. stream: a cudaStream_t (NULL = default).
  * Scratch: the FP64 partial mass sums that give <rho> (Eq. Gravity_2) and a status word
  *   live in a file-scope __device__ array of 65 792 bytes inside liblbm, held by every

@@ -526,14 +526,15 @@ int lbm_init(const lbm_params* p, const double* rho0, int rho0_where, void* stre
   h->rho_mid = midpoint_level(h->p);
 
   e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = lbm::launch_init(p->precision, rho_dev, h->f[0], p->nx, p->ny, rho_ref, h->stream);
+  if (e == cudaSuccess)
+    e = lbm::launch_init(p->precision, rho_dev, h->f[0], p->nx, p->ny, rho_ref, h->parts[0], h->P, h->stream);
   if (e == cudaSuccess && p->thermal)
     e = lbm::launch_linear_T(p->precision, p->nx, p->ny, p->T_bot, p->T_top, p->wall == LBM_WALL_ZOU_HE ? 1 : 0, h->Tf,
                              h->stream);
   if (e != cudaSuccess) { cuda_fail(h, e, "init kernel"); return fail(LBM_ECUDA); }
   h->cur = 0;
   h->pcur = 0;
-  if ((rc = refresh_partials(h))) return fail(rc);
+  h->npart = h->P;  // the init kernel wrote the partials of the initial state
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) { cuda_fail(h, e, "lbm_init"); return fail(LBM_ECUDA); }
   *out = h;

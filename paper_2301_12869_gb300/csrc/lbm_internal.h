@@ -74,8 +74,9 @@ cudaError_t step_prepare(int precision);  // sets the dynamic shared memory limi
 cudaError_t launch_step(int precision, int mode, const StepTiling& t, const StepPhys& ph,
                         const StepIO& io, cudaStream_t stream);
 
-cudaError_t launch_init(int precision, const double* rho0, void* f, int nx, int ny, double rho_ref,
-                        cudaStream_t stream);
+// initial state and the FP64 partial sums of its stored values into part[0..npart)
+cudaError_t launch_init(int precision, const double* rho0, void* f, int nx, int ny, double rho_ref, double* part,
+                        int npart, cudaStream_t stream);
 cudaError_t launch_partials(int precision, const void* f, int nx, int ny, double* part, int npart,
                             cudaStream_t stream);
 // out[0] = sum of part[0..npart) in a fixed order

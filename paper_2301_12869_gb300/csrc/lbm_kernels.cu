@@ -697,33 +697,48 @@ __global__ void __launch_bounds__((NWC + 1) * 32, MINB)
   }
 }
 
-// ---- initial state g_i = f_i^eq(rho0, 0) - w_i rho_ref = w_i (rho0 - rho_ref)
+// ---- vector access for the whole-lattice passes: a lane takes 4 FP32 nodes (16-byte loads
+// and stores of each plane; n = nx ny is a multiple of 4 for FP32, whose rows are 16-byte
+// multiples) or 2 FP64 nodes, as node pairs of the accumulator's value type
 template <typename T>
-__global__ void init_kernel(const double* __restrict__ rho0, T* __restrict__ f, int nx, int ny, double rho_ref) {
-  const size_t n = size_t(nx) * ny;
-  for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < n; q += size_t(gridDim.x) * blockDim.x) {
-    const double d = rho0[q] - rho_ref;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i * n + q] = T(w_of(i) * d);
+struct Quad;
+template <>
+struct Quad<float> {
+  static constexpr int nodes = 4;
+  using V = f2;
+  __device__ static void load(const float* p, V (&v)[2]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = make_f2(q.x, q.y);
+    v[1] = make_f2(q.z, q.w);
   }
-}
+  // store d rounded to FP32 and return the stored values as pairs
+  __device__ static void store(float* p, const double (&d)[4], V (&v)[2]) {
+    const float4 q = make_float4(float(d[0]), float(d[1]), float(d[2]), float(d[3]));
+    *reinterpret_cast<float4*>(p) = q;
+    v[0] = make_f2(q.x, q.y);
+    v[1] = make_f2(q.z, q.w);
+  }
+};
+template <>
+struct Quad<double> {
+  static constexpr int nodes = 2;
+  using V = double;
+  __device__ static void load(const double* p, V (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+  }
+  __device__ static void store(double* p, const double (&d)[2], V (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(d[0], d[1]);
+    v[0] = d[0];
+    v[1] = d[1];
+  }
+};
 
-// ---- FP64 partial sums of sum_i g_i: block b covers nodes [b*chunk, (b+1)*chunk).
-// FP32 storage: every value into the per-thread two-sum pair (GB300's FP64 pipe is slow);
-// FP64 storage: plain FP64 sums.
-template <typename T>
-__global__ void partials_kernel(const T* __restrict__ f, int nx, int ny, double* __restrict__ part) {
+// a block's FP64 total of its threads' accumulators, written to part[blockIdx.x]
+template <typename V>
+__device__ __forceinline__ void block_partial(const Acc<V>& acc, double* part) {
   __shared__ double red[32];
-  const size_t n = size_t(nx) * ny;
-  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const size_t q0 = blockIdx.x * chunk, q1 = min(n, q0 + chunk);
-  Acc<T> acc;
-  for (size_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-    T g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = f[i * n + q];
-    acc.add9(g);
-  }
   const double s = warp_sum(acc.value());
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -732,6 +747,63 @@ __global__ void partials_kernel(const T* __restrict__ f, int nx, int ny, double*
     const double t = warp_sum(threadIdx.x < nw ? red[threadIdx.x] : 0.0);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
   }
+}
+
+// ---- initial state g_i = f_i^eq(rho0, 0) - w_i rho_ref = w_i (rho0 - rho_ref), and the FP64
+// partial sums of the stored values (every value into the two-sum pairs, as partials_kernel
+// adds them): block b covers vector groups [b*chunk, (b+1)*chunk) and writes part[b]
+template <typename T>
+__global__ void init_kernel(const double* __restrict__ rho0, T* __restrict__ f, int nx, int ny, double rho_ref,
+                            double* __restrict__ part) {
+  using Q = Quad<T>;
+  using V = typename Q::V;
+  constexpr int NQ = Q::nodes;
+  const size_t n = size_t(nx) * ny, groups = n / NQ;
+  const size_t chunk = (groups + gridDim.x - 1) / gridDim.x;
+  const size_t k0 = blockIdx.x * chunk, k1 = min(groups, k0 + chunk);
+  Acc<V> acc;
+  for (size_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    double d[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) d[j] = rho0[k * NQ + j] - rho_ref;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      double v[NQ];
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) v[j] = w_of(i) * d[j];
+      V g[2];
+      Q::store(f + i * n + k * NQ, v, g);
+      acc.add(g[0], i % 3);
+      acc.add(g[1], i % 3);
+    }
+  }
+  block_partial(acc, part);
+}
+
+// ---- FP64 partial sums of sum_i g_i: block b covers vector groups [b*chunk, (b+1)*chunk).
+// FP32 storage: every value into the per-thread two-sum pairs (GB300's FP64 pipe is slow),
+// four nodes a thread per plane; FP64 storage: plain FP64 sums, two nodes a thread.
+template <typename T>
+__global__ void partials_kernel(const T* __restrict__ f, int nx, int ny, double* __restrict__ part) {
+  using Q = Quad<T>;
+  using V = typename Q::V;
+  constexpr int NQ = Q::nodes;
+  const size_t n = size_t(nx) * ny, groups = n / NQ;
+  const size_t chunk = (groups + gridDim.x - 1) / gridDim.x;
+  const size_t k0 = blockIdx.x * chunk, k1 = min(groups, k0 + chunk);
+  Acc<V> acc;
+#pragma unroll 2
+  for (size_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    V g[9][2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Q::load(f + i * n + k * NQ, g[i]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      acc.add(g[i][0], i % 3);
+      acc.add(g[i][1], i % 3);
+    }
+  }
+  block_partial(acc, part);
 }
 
 __global__ void sum_partials_kernel(const double* part, int npart, double* out) {
@@ -1045,13 +1117,12 @@ cudaError_t launch_step(int precision, int mode, const StepTiling& t, const Step
   }
 }
 
-cudaError_t launch_init(int precision, const double* rho0, void* f, int nx, int ny, double rho_ref,
-                        cudaStream_t stream) {
-  const size_t n = size_t(nx) * ny;
+cudaError_t launch_init(int precision, const double* rho0, void* f, int nx, int ny, double rho_ref, double* part,
+                        int npart, cudaStream_t stream) {
   if (precision == 1)
-    init_kernel<float><<<grid_for(n, 256), 256, 0, stream>>>(rho0, static_cast<float*>(f), nx, ny, rho_ref);
+    init_kernel<float><<<npart, 256, 0, stream>>>(rho0, static_cast<float*>(f), nx, ny, rho_ref, part);
   else
-    init_kernel<double><<<grid_for(n, 256), 256, 0, stream>>>(rho0, static_cast<double*>(f), nx, ny, rho_ref);
+    init_kernel<double><<<npart, 256, 0, stream>>>(rho0, static_cast<double*>(f), nx, ny, rho_ref, part);
   return cudaGetLastError();
 }
 

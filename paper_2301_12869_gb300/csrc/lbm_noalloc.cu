@@ -13,6 +13,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -87,6 +89,9 @@ extern "C" int lbm_step_noalloc(const lbm_params* p, const void* f_in, void* f_o
 
   if (!is_device_pointer(f_in, dev) || !is_device_pointer(f_out, dev))
     return fail(LBM_EINVAL, "f_in and f_out must be device memory of the current device");
+  // the step's bulk copies and vector loads start on 16-byte boundaries of the planes
+  if ((reinterpret_cast<uintptr_t>(f_in) | reinterpret_cast<uintptr_t>(f_out)) & 15u)
+    return fail(LBM_EINVAL, "f_in and f_out must be 16-byte aligned");
 
   // once per device, with that device current: the scratch array's device address and the
   // kernels' shared-memory limit (both precisions)

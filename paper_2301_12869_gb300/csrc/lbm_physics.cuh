@@ -80,7 +80,7 @@ struct Acc;
 template <>
 struct Acc<double> {
   double s = 0.0;
-  __device__ void add(double x) { s += x; }
+  __device__ void add(double x, int = 0) { s += x; }
   __device__ void add9(const double (&v)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) s += v[i];

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 
 namespace {
@@ -131,6 +132,9 @@ __global__ void slab_partials_kernel(const T* __restrict__ f, int nx, int rows, 
 
 int grid_for(size_t n) { return int(std::max<size_t>(1, std::min<size_t>(4096, (n + 255) / 256))); }
 
+// the step's bulk copies start on 16-byte boundaries of the planes
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
 }  // namespace
 
 extern "C" {
@@ -151,6 +155,7 @@ int lbm_slab_init(const lbm_params* p, const lbm_slab* s, const double* rho0, vo
   const int rc = slab_tiling(p, s, &t, err);
   if (rc) return fail(rc, err);
   if (!rho0 || !f) return fail(LBM_EINVAL, "rho0 and f must be device arrays");
+  if (misaligned(f)) return fail(LBM_EINVAL, "f must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t n = size_t(p->nx) * s->ny_own;
   if (p->precision == LBM_FP32)
@@ -170,6 +175,7 @@ int lbm_slab_mass(const lbm_params* p, const lbm_slab* s, const void* f, double*
   const int rc = slab_tiling(p, s, &t, err);
   if (rc) return fail(rc, err);
   if (!f || !part) return fail(LBM_EINVAL, "f and part must be device arrays");
+  if (misaligned(f)) return fail(LBM_EINVAL, "f must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int P = std::max(t.nbands * t.nstrips, 1);
   if (npart < P) {
@@ -198,6 +204,7 @@ int lbm_slab_step(const lbm_params* p, const lbm_slab* s, const void* f_in, void
     return fail(LBM_EINVAL,
                 "f_in, f_out (distinct), part_out, status (and part_in for Eq. Gravity_2) must be set");
   if (part_in == part_out) return fail(LBM_EINVAL, "part_in and part_out must be distinct");
+  if (misaligned(f_in) || misaligned(f_out)) return fail(LBM_EINVAL, "f_in and f_out must be 16-byte aligned");
   if (npart_out < t.nbands * t.nstrips) {
     snprintf(err, sizeof(err), "part_out holds %d values, the step writes %d (lbm_slab_partials)", npart_out,
              t.nbands * t.nstrips);

@@ -155,6 +155,9 @@ def test_slab_arguments_are_checked():
         lbm.lbm_slab_step(p, s, f.cpu(), f, part, part2, st)
     with pytest.raises(lbm.LbmError, match="part_out holds"):  # fewer partial slots than CTAs
         lbm.lbm_slab_step(p, s, f, torch.zeros_like(f), part, part2[:1], st)
+    off = torch.zeros(f.numel() + 1, dtype=torch.float64, device="cuda")[1:]  # 8 bytes past a boundary
+    with pytest.raises(lbm.LbmError, match="16-byte"):  # refused on the host: nothing is launched
+        lbm.lbm_slab_step(p, s, off, torch.zeros_like(f), part, part2, st)
 
 
 @pytest.mark.parametrize("precision, nx, ny", [("fp32", 1024, 4096), ("fp64", 1024, 4096), ("fp32", 64, 40)])

@@ -116,6 +116,12 @@ def test_noalloc_rejects_bad_arguments():
                                      ctypes.c_void_p(torch.empty_like(buf).data_ptr()), None)
     assert rc == lbm.LBM_EINVAL
     assert b"device memory" in lbm.load().lbm_last_error(None)
+    # a device address off the 16-byte boundary the step's bulk copies need (nothing launched)
+    out = torch.empty_like(buf)
+    rc = lbm.load().lbm_step_noalloc(ctypes.byref(p), ctypes.c_void_p(buf.data_ptr() + 4),
+                                     ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == lbm.LBM_EINVAL
+    assert b"16-byte" in lbm.load().lbm_last_error(None)
     p.nx = 6
     with pytest.raises(lbm.LbmError, match="multiple of 4"):
         lbm.lbm_step_noalloc(p, buf[:, :, :6].contiguous(), torch.empty_like(buf[:, :, :6]).contiguous())
