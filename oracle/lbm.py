@@ -383,6 +383,36 @@ def init_state(rho0):
     return equilibrium(rho0, z, z)
 
 
+def rest_state(rho, p, mean_rho=None):
+    """Stored (post-collision) populations of a lattice at rest with the density field rho:
+    an initialisation, no counterpart in the paper (which gives only the density profile of
+    its initial state). The forces of Eqs. ShanChenForce and Gravity_1 / Gravity_2 follow
+    from rho; the populations before the collision have the moments of the rest equilibrium
+    f_eq(rho, 0) (Eq. EquilibriumDistribution) except the momentum, which is -F/2, so that
+    the velocity of Eq. Momentum vanishes; then one collision (Eqs. OperatorMRT, LiFS). Its
+    momentum is +F/2 (a collision adds F), and with every tau = 1 the state is
+    m* = m_eq(rho, 0) + S~(u = 0, F)/2, which a steady state of the method satisfies."""
+    rho = np.asarray(rho, dtype=np.float64)
+    if mean_rho is None:
+        mean_rho = float(np.mean(rho))
+    psi, _ = interaction_potential(rho, p)
+    Sx, Sy = shan_chen_sum(psi)
+    Fint = (-p.G * psi * Sx, -p.G * psi * Sy)
+    Fg = gravity(rho, mean_rho, p)
+    F = (Fint[0] + Fg[0], Fint[1] + Fg[1])
+    z = np.zeros_like(rho)
+    m = M @ equilibrium(rho, z, z).reshape(9, -1)
+    m[3] = -0.5 * F[0].ravel()  # j_x (moment order of Eq. MatrixMRT)
+    m[5] = -0.5 * F[1].ravel()  # j_y
+    f_pre = (MINV @ m).reshape((9,) + rho.shape)
+    ux, uy = velocity(f_pre, rho, F[0], F[1])  # zero up to rounding
+    ratio = sigma_ratio(Fint[0], Fint[1], psi, Sx, Sy, p.G)
+    ratio[0] = 0.0
+    ratio[-1] = 0.0
+    S = li_source(ux, uy, F[0], F[1], ratio, p)
+    return collide(f_pre, equilibrium(rho, ux, uy), S, p)
+
+
 # ---------------------------------------------------------------- diagnostics
 def mass(fstar):
     """Total mass sum_x sum_i f*_i (equal to sum_x rho after streaming)."""
