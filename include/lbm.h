@@ -296,6 +296,19 @@ int lbm_batch_moments(lbm_batch* b, double* rho, double* ux, double* uy, int whe
  * column), host or device. Synchronises. */
 int lbm_batch_get_state(lbm_batch* b, double* f, int where);
 
+/* Replace every column's populations by the rest state of its stored density field
+ * rho = sum_i f_i (an initialisation with no counterpart in the paper, which gives only the
+ * initial density profile): the forces F = F_int + F_g of Eqs. ShanChenForce and Gravity_1 /
+ * Gravity_2 from rho (<rho> the column's mean), pre-collision populations with the moments
+ * of the rest equilibrium f_eq(rho, 0) except the momentum -F/2, so that the velocity of
+ * Eq. Momentum is zero, and one collision (Eqs. OperatorMRT, LiFS). The density is kept; the
+ * momentum becomes +F/2. With every tau = 1 this is m* = m_eq(rho, 0) + S~(0, F)/2, which a
+ * steady column satisfies up to its small residual velocity, so a start whose density is
+ * close to the steady one starts close to the steady populations (f_eq(rho, 0), the state
+ * lbm_batch_init sets, lacks the forcing terms). Call it after lbm_batch_init (or between
+ * runs). A non-physical density sets the column's status. Synchronises. */
+int lbm_batch_rest_state(lbm_batch* b);
+
 /* A new batch with src's columns and current state in another precision (e.g. an FP32 run
  * continued in FP64 below the FP32 rounding floor); step counts carry over. */
 int lbm_batch_convert(const lbm_batch* src, int precision, lbm_batch** out);
@@ -356,9 +369,13 @@ int lbm_mlp_predict(lbm_mlp* h, const float* x, long long n, float* y);
  * targets rho(y, x = 0)/rho_crit. x, t: DEVICE. Synchronises `stream`. */
 int lbm_mlp_features(const lbm_column* cols, int ncols, int nx, double a, double b, double R, const double* rho,
                      const double* mean_rho, float* x, float* t, void* stream);
-/* Initial densities for lbm_batch_init: for each column the predicted profile times
- * rho_crit (floored at 1e-3), scaled so that its mean equals mean_rho[c] (host), the same
- * on every x; written to rho0 (DEVICE, concatenated [col][y][x]). Synchronises. */
+/* Initial densities for lbm_batch_init: for each column the predicted profile p(y) times
+ * rho_crit (floored at 1e-3), moved along y so that its mean equals mean_rho[c] (host): row y
+ * takes p at y - s (linear between rows, the end values beyond them) with the shift s in
+ * [-ny, ny] found by bisection, then a factor within rounding of 1 makes the mean exact
+ * (a mean outside [p(ny - 1), p(0)] keeps s = 0 and scales the profile instead). Moving
+ * rather than scaling keeps the predicted bulk densities. The same on every x; written to
+ * rho0 (DEVICE, concatenated [col][y][x]). Synchronises. */
 int lbm_mlp_warm_start(lbm_mlp* h, const lbm_column* cols, int ncols, int nx, double a, double b, double R,
                        const double* mean_rho, double* rho0);
 /* The network's tensor-core matrix product on its own: C[M x N] = A[M x K] B[N x K]^T with A,

@@ -472,6 +472,84 @@ __global__ void __launch_bounds__(NT) batch_kernel(const BatchArgs a) {
   }
 }
 
+// The rest state of every column's stored density field rho = sum_i f*_i (lbm_batch_rest_state):
+// the forces of Eqs. ShanChenForce and Gravity_1 / Gravity_2 from rho, pre-collision
+// populations with the moments of the rest equilibrium f_eq(rho, 0) except the momentum -F/2
+// (so that the velocity of Eq. Momentum vanishes), and one collision (collide_node, Eqs.
+// OperatorMRT, LiFS); written in place. psi of the column is staged in shared memory first.
+// One CTA of 256 threads per column at a time.
+template <typename T, bool UNIT>
+__global__ void __launch_bounds__(256) batch_rest_kernel(const BatchArgs a) {
+  constexpr int NT = 256, NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ double red[NW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* psi_s = reinterpret_cast<T*>(sm_raw);
+  for (int c = blockIdx.x; c < a.ncols; c += gridDim.x) {
+    const BatchCol col = a.cols[c];
+    const int nx = a.nx, ny = col.ny, N = nx * ny;
+    const lbm::PhysT<T> k = column_phys<T>(a, col);
+    T* cur = static_cast<T*>(a.fA) + 9 * col.node_off;
+    int flag = 0;
+    lbm::Acc<T> acc;  // FP64 mass of the stored state, for <rho> of Eq. Gravity_2
+    for (int n = tid; n < N; n += NT) {
+      T g[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = cur[i * N + n];
+      acc.add9(g);
+      psi_s[n] = lbm::psi_of<T>(k.rho_ref + lbm::sum9(g), k, flag);
+    }
+    const double v = lbm::warp_sum(acc.value());
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double msum = 0.0;
+    for (int w = 0; w < NW; ++w) msum += red[w];
+    const T dmean = lbm::from_double<T>(msum / double(N));
+    for (int n = tid; n < N; n += NT) {
+      const int x = n % nx, y = n / nx;
+      const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+      T g[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = cur[i * N + n];
+      const T dr = lbm::sum9(g);
+      T Sx = lbm::cst<T>(0.0), Sy = lbm::cst<T>(0.0);
+      if (y > 0 && y < ny - 1) {  // as in batch_kernel: w(1) = 1/3, w(2) = 1/12, zero on the wall rows
+        const T* pc = psi_s + y * nx;
+        const T* pn = pc + nx;
+        const T* ps = pc - nx;
+        const T E = pc[xr], Wt = pc[xl], Nn = pn[x], Ss = ps[x];
+        const T NE = pn[xr], NW2 = pn[xl], SE = ps[xr], SWt = ps[xl];
+        Sx = lbm::fmadd(lbm::cst<T>(1.0 / 3.0), E - Wt, lbm::cst<T>(1.0 / 12.0) * ((NE - NW2) + (SE - SWt)));
+        Sy = lbm::fmadd(lbm::cst<T>(1.0 / 3.0), Nn - Ss, lbm::cst<T>(1.0 / 12.0) * ((NE + NW2) - (SE + SWt)));
+      }
+      // F = F_int + F_g as collide_node forms it
+      const T base = (k.form == 2) ? (dr - dmean) : (k.rho_ref + dr);
+      const T nGpsi = k.negG * psi_s[n];
+      const T Fx = lbm::fmadd(nGpsi, Sx, base * k.gx);
+      const T Fy = lbm::fmadd(nGpsi, Sy, base * k.gy);
+      // deviations with the moments (dr, e = -2 dr, eps = dr, j = -F/2, q = 0, p_xx = p_xy = 0):
+      // w_i dr plus the momentum part j/6 along each link (M^-1 with q = 0)
+      const T ax = lbm::cst<T>(-1.0 / 12.0) * Fx, ay = lbm::cst<T>(-1.0 / 12.0) * Fy;  // j/6
+      const T r9 = lbm::cst<T>(1.0 / 9.0) * dr, r36 = lbm::cst<T>(1.0 / 36.0) * dr;
+      T pre[9];
+      pre[0] = lbm::cst<T>(4.0 / 9.0) * dr;
+      pre[1] = r9 + ax;
+      pre[3] = r9 - ax;
+      pre[2] = r9 + ay;
+      pre[4] = r9 - ay;
+      pre[5] = r36 + (ax + ay);
+      pre[7] = r36 - (ax + ay);
+      pre[6] = r36 + (ay - ax);
+      pre[8] = r36 - (ay - ax);
+      T o[9], rho, ux, uy;
+      lbm::collide_node<T, UNIT>(pre, psi_s[n], Sx, Sy, dmean, k, o, rho, ux, uy, flag);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) cur[i * N + n] = o[i];
+    }
+    if (__syncthreads_or(flag) && tid == 0) a.status[c] |= lbm::STATUS_NONPHYS;
+  }
+}
+
 // g_i = w_i (rho0 - rho_ref) for every column
 template <typename T>
 __global__ void batch_init_kernel(const BatchCol* cols, int ncols, int nx, const double* rho0, T* f) {
@@ -972,6 +1050,27 @@ int lbm_batch_moments(lbm_batch* b, double* rho, double* ux, double* uy, int whe
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   for (double* t : tmp)
     if (t) cudaFree(t);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_batch_rest_state(lbm_batch* b) {
+  if (!b) return bfail(LBM_EINVAL, "batch is NULL");
+  const BatchArgs a = make_args(b);
+  const size_t smem = size_t(b->nx) * size_t(b->max_ny) * b->s;  // psi of the tallest column
+  const int grid = std::min(b->ncols, 4096);
+  const bool unit = unit_tau(b->p);
+  void* fn;
+  if (b->p.precision == LBM_FP32)
+    fn = unit ? (void*)&batch_rest_kernel<float, true> : (void*)&batch_rest_kernel<float, false>;
+  else if (b->p.precision == LBM_DOUBLE_FLOAT)
+    fn = unit ? (void*)&batch_rest_kernel<lbm::dd, true> : (void*)&batch_rest_kernel<lbm::dd, false>;
+  else
+    fn = unit ? (void*)&batch_rest_kernel<double, true> : (void*)&batch_rest_kernel<double, false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  void* kargs[] = {const_cast<BatchArgs*>(&a)};
+  if (e == cudaSuccess) e = cudaLaunchKernel(fn, dim3(grid), dim3(256), kargs, smem, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(LBM_ECUDA, cudaGetErrorString(e));
   return LBM_OK;
 }

@@ -600,31 +600,63 @@ __global__ void features_kernel(const ColFeat* __restrict__ cols, int ncols, int
   }
 }
 
-// warm start: rho0 of column c = the predicted profile (times rho_c, floored at rho_min),
-// scaled so that its mean is the column's <rho>, the same on every x
+// FP64 sum over the block (every thread gets it); red: 32 doubles of shared memory
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // red may still be read from the previous call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += red[w];
+  return tot;
+}
+
+// warm start: rho0 of column c = the predicted profile p(y) (times rho_c, floored at rho_min)
+// moved along y by the shift s that gives the column's mass, the same on every x. The moved
+// profile at row y is p at y - s, linear between rows and constant beyond the ends, so its
+// mass M(s) runs from ny p(ny - 1) (s = -ny: the top value everywhere) to ny p(0) (s = ny);
+// s follows by bisection on [-ny, ny] (60 halvings). Matching the mass by moving the
+// profile keeps the predicted bulk densities: scaling it instead would change them by the
+// relative mass error, a pressure error in the nearly incompressible liquid that excites
+// the column's slowest mode. A mass outside that range (no bracket) keeps s = 0. A last
+// factor M_target / M(s), within rounding of 1, makes the mass exact.
 __global__ void warm_profile_kernel(const ColFeat* __restrict__ cols, int ncols, int nx, const float* __restrict__ yhat,
                                     const double* __restrict__ mean_rho, double rho_c, double rho_min,
                                     double* __restrict__ rho0) {
   const int c = blockIdx.x;
   if (c >= ncols) return;
   const ColFeat cf = cols[c];
-  __shared__ double part[32];
-  __shared__ double scale;
-  double s = 0.0;
-  for (int y = threadIdx.x; y < cf.ny; y += blockDim.x) s += fmax(double(yhat[cf.row_off + y]) * rho_c, rho_min);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) tot += part[w];
-    scale = mean_rho[c] * double(cf.ny) / tot;
+  __shared__ double red[32];
+  const int ny = cf.ny;
+  auto prof = [&](int y) { return fmax(double(yhat[cf.row_off + y]) * rho_c, rho_min); };
+  auto moved = [&](int y, double sh) {
+    const double z = double(y) - sh;
+    if (!(z > 0.0)) return prof(0);
+    if (z >= double(ny - 1)) return prof(ny - 1);
+    const int k = int(z);
+    const double t = z - double(k);
+    const double p0 = prof(k);
+    return p0 + t * (prof(k + 1) - p0);
+  };
+  auto mass = [&](double sh) {
+    double v = 0.0;
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) v += moved(y, sh);
+    return block_sum(v, red);
+  };
+  const double target = mean_rho[c] * double(ny);
+  double lo = -double(ny), hi = double(ny), sh = 0.0;
+  if (mass(lo) <= target && target <= mass(hi)) {
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mass(mid) < target) lo = mid; else hi = mid;
+    }
+    sh = 0.5 * (lo + hi);
   }
-  __syncthreads();
-  for (long long q = threadIdx.x; q < (long long)cf.ny * nx; q += blockDim.x) {
+  const double scale = target / mass(sh);
+  for (long long q = threadIdx.x; q < (long long)ny * nx; q += blockDim.x) {
     const int y = int(q / nx);
-    rho0[cf.node_off + q] = fmax(double(yhat[cf.row_off + y]) * rho_c, rho_min) * scale;
+    rho0[cf.node_off + q] = moved(y, sh) * scale;
   }
 }
 

@@ -40,7 +40,7 @@ EXPORTS = (
     "lbm_get_state", "lbm_set_state", "lbm_set_params", "lbm_status", "lbm_destroy", "lbm_last_error",
     "lbm_critical_point", "lbm_coexistence", "lbm_launch_info", "lbm_step_noalloc",
     "lbm_autotune", "lbm_tile_variants", "lbm_set_tiling", "lbm_set_temperature", "lbm_get_temperature",
-    "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state",
+    "lbm_batch_init", "lbm_batch_run", "lbm_batch_run_stall", "lbm_batch_set_acceleration", "lbm_batch_results", "lbm_batch_moments", "lbm_batch_get_state", "lbm_batch_rest_state",
     "lbm_batch_convert", "lbm_batch_destroy", "lbm_batch_column_seconds",
     "lbm_batch_set_threads", "lbm_batch_autotune", "lbm_wait_bound_selftest",
     "lbm_mlp_create", "lbm_mlp_set_params", "lbm_mlp_get_params", "lbm_mlp_gradients", "lbm_mlp_train",
@@ -134,6 +134,7 @@ def load(path: str = LIB_PATH):
         "lbm_batch_results": (i32, [vp, vp, vp, vp]),
         "lbm_batch_moments": (i32, [vp, vp, vp, vp, i32]),
         "lbm_batch_get_state": (i32, [vp, vp, i32]),
+        "lbm_batch_rest_state": (i32, [vp]),
         "lbm_batch_convert": (i32, [vp, i32, P(vp)]),
         "lbm_batch_destroy": (i32, [vp]),
         "lbm_batch_column_seconds": (i32, [vp, vp]),
@@ -474,6 +475,11 @@ def lbm_batch_moments(b, rho=None, ux=None, uy=None):
     wheres = {w for _, w in map(_ptr, (rho, ux, uy)) if w is not None}
     where = wheres.pop() if wheres else LBM_HOST
     _check(load().lbm_batch_moments(b, _ptr(rho)[0], _ptr(ux)[0], _ptr(uy)[0], where))
+
+
+def lbm_batch_rest_state(b):
+    """Every column's populations become the rest state of its stored density field."""
+    _check(load().lbm_batch_rest_state(b))
 
 
 def lbm_batch_get_state(b, f):

@@ -478,3 +478,67 @@ def test_full_size_column_set_sampled(precision, tol):
     for c in [0, 1, 511, 1023] + list(rng.integers(0, len(cols), 4)):
         want = olbm.run(g0s[c], oracle_column(cols[c], p), 30)
         assert np.max(np.abs(g1s[c] - want)) <= tol, (c, cols[c])
+
+
+@pytest.mark.parametrize("precision, tol, taus", [
+    ("fp64", 1e-14, {}),
+    ("fp64", 1e-14, dict(tau_e=0.8, tau_varsigma=1.1, tau_q=1.2, tau_nu=0.7)),
+    ("fp32", 2e-6, {}),
+    ("dd", 1e-12, {}),
+])
+def test_rest_state_matches_oracle(precision, tol, taus):
+    """lbm_batch_rest_state on every column of a mixed batch (heights 3 .. 1024, both gravity
+    forms, own T and g) against the oracle's rest_state of the column's stored density."""
+    heights = (8, 24, 64, 256, 1024, 3)
+    cols, rhos = make_columns(12, seed=41, heights=heights)
+    p = batch_params(precision, **taus)
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        total = sum(9 * NX * c["ny"] for c in cols)
+        f0 = np.empty(total)
+        lbm.lbm_batch_get_state(b, f0)
+        lbm.lbm_batch_rest_state(b)
+        f1 = np.empty(total)
+        lbm.lbm_batch_get_state(b, f1)
+        _, _, status = lbm.lbm_batch_results(b, len(cols))
+        assert np.all(status == 0)
+        for col, g0, g1 in zip(cols, split_state(f0, cols), split_state(f1, cols)):
+            want = olbm.rest_state(g0.sum(axis=0), oracle_column(col, p))
+            assert np.max(np.abs(g1 - want)) <= tol, col
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_rest_state_of_a_steady_density_starts_at_the_steady_state():
+    """Columns run in FP64 to a per-step change of 1e-12, then restarted from their converged
+    density: from the rest state of that density they are back below 1e-10 at the first
+    check (100 steps), while the rest equilibrium f_eq(rho, 0) of the same density
+    (lbm_batch_init alone) takes 900 - 8000 steps - the slow transient every equilibrium
+    start pays comes from the missing forcing terms, not from the density."""
+    import torch
+
+    cols, rhos = make_columns(8, seed=17, heights=(16, 24, 32))
+    p = batch_params("fp64")
+    b = lbm.lbm_batch_init(p, cols, np.concatenate([r.ravel() for r in rhos]))
+    try:
+        lbm.lbm_batch_run(b, 1e-12, 400000, 100)
+        _, res, status = lbm.lbm_batch_results(b, len(cols))
+        assert np.all(res <= 1e-12) and np.all(status == 0)
+        rho = torch.empty(sum(NX * c["ny"] for c in cols), dtype=torch.float64, device="cuda")
+        lbm.lbm_batch_moments(b, rho=rho)
+    finally:
+        lbm.lbm_batch_destroy(b)
+    steps = {}
+    for rest in (False, True):
+        bb = lbm.lbm_batch_init(p, cols, rho)
+        try:
+            if rest:
+                lbm.lbm_batch_rest_state(bb)
+            lbm.lbm_batch_run(bb, 1e-10, 400000, 100)
+            st, res, status = lbm.lbm_batch_results(bb, len(cols))
+            assert np.all(res <= 1e-10) and np.all(status == 0)
+            steps[rest] = st
+        finally:
+            lbm.lbm_batch_destroy(bb)
+    assert np.all(steps[True] == 100)
+    assert np.all(steps[False] >= 500)

@@ -287,13 +287,30 @@ def test_features_and_warm_start_profile():
         rho0 = torch.empty(nx * rows, dtype=torch.float64, device="cuda")
         lbm.lbm_mlp_warm_start(h, cols, nx, a, b, R, mean, rho0)
         r = rho0.cpu().numpy()
-        off = 0
+        y = torch.empty(rows, dtype=torch.float32, device="cuda")
+        lbm.lbm_mlp_predict(h, x, y)
+        yh = y.cpu().numpy().astype(np.float64)
+        off = roff = 0
         for c, m in zip(cols, mean):
-            blk = r[off:off + nx * c["ny"]].reshape(c["ny"], nx)
-            off += nx * c["ny"]
+            ny = c["ny"]
+            blk = r[off:off + nx * ny].reshape(ny, nx)
+            off += nx * ny
             assert np.all(blk == blk[:, :1])              # the same on every x
             assert blk.mean() == pytest.approx(m, rel=1e-12)  # mass of the column kept exactly
             assert np.all(blk > 0)
+            # the predicted profile moved along y to the column's mass (the stated definition)
+            prof = np.maximum(yh[roff:roff + ny] * rho_c, 1e-3)
+            roff += ny
+            moved = lambda s: np.interp(np.arange(ny) - s, np.arange(ny), prof)  # noqa: E731
+            lo, hi, target = -ny, ny, m * ny
+            shift = 0.0
+            if moved(lo).sum() <= target <= moved(hi).sum():
+                for _ in range(60):
+                    mid = 0.5 * (lo + hi)
+                    lo, hi = (mid, hi) if moved(mid).sum() < target else (lo, mid)
+                shift = 0.5 * (lo + hi)
+            want_col = moved(shift) * target / moved(shift).sum()
+            np.testing.assert_allclose(blk[:, 0], want_col, rtol=1e-9, atol=0)
         # features from the columns' own density fields: <rho> from the field, targets rho/rho_c
         t = torch.empty(rows, dtype=torch.float32, device="cuda")
         lbm.lbm_mlp_features(cols, nx, a, b, R, x, t=t, rho=rho0)
