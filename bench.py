@@ -712,6 +712,9 @@ def run_columns(args):
 
 # ---------------------------------------------------------------- time to steady state (default line)
 STEADY_HEIGHTS = (64, 128, 256, 512, 1024)
+# the warm-start network of that block: trained on 16384 steady columns of another seed with
+# the heights whose columns converge within the step cap
+WARM_TRAIN_COLUMNS, WARM_HEIGHTS, WARM_ITERS = 16384, (64, 128), 12000
 
 
 def column_stats(rho, cols, lbm):
@@ -820,14 +823,59 @@ def time_to_steady(args, lbm, inputs, world, rank, torch):
     rhodd = np.empty(rho.size)
     lbm.lbm_batch_moments(bd, rho=rhodd)
     lbm.lbm_batch_destroy(bd)
+    # FP32 then double-float from the warm start: the network (trained here, on the GPU, on the
+    # steady columns of another seed) gives the profile of the columns of the heights it was
+    # trained on, the tanh profile stays for the others; every column then starts from the
+    # rest state of its profile (lbm_batch_rest_state). Timed: inference, rest state, both
+    # phases; the training is a one-off cost, reported beside it.
+    net, train = train_warm_network(lbm, inputs, torch, WARM_TRAIN_COLUMNS, WARM_HEIGHTS, cap, WARM_ITERS, 8192,
+                                    SEED + 1)
+    lo = np.cumsum([0] + [4 * c["ny"] for c in cols])
+    sel = [i for i, c in enumerate(cols) if c["ny"] in WARM_HEIGHTS]
+    rho_w = torch.from_numpy(rho).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if sel:
+        sub = [cols[i] for i in sel]
+        pred = torch.empty(sum(4 * c["ny"] for c in sub), dtype=torch.float64, device="cuda")
+        lbm.lbm_mlp_warm_start(net, sub, 4, A, B, R, np.array([rho[lo[i]:lo[i + 1]].mean() for i in sel]), pred)
+        po = 0
+        for i, c in zip(sel, sub):
+            rho_w[lo[i]:lo[i + 1]] = pred[po:po + 4 * c["ny"]]
+            po += 4 * c["ny"]
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    lbm.lbm_mlp_destroy(net)
+    bw = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols, rho_w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbm.lbm_batch_rest_state(bw)
+    t_rest = time.perf_counter() - t0
+    tuned["fp32_warm"] = lbm.lbm_batch_autotune(bw, TUNE_STEPS)
+    lbm.lbm_batch_set_acceleration(bw, ACCEL_CHECKS)
+    tw32 = lbm.lbm_batch_run_stall(bw, FP32_TOL, cap, 100, FP32_STALL_CHECKS)
+    bwd = lbm.lbm_batch_convert(bw, lbm.LBM_DOUBLE_FLOAT)
+    lbm.lbm_batch_destroy(bw)
+    tuned["dd_after_fp32_warm"] = lbm.lbm_batch_autotune(bwd, TUNE_STEPS)
+    lbm.lbm_batch_set_acceleration(bwd, ACCEL_CHECKS)
+    twdd = lbm.lbm_batch_run(bwd, 1e-10, cap, 100)
+    stw, resw, sw = lbm.lbm_batch_results(bwd, n, check=False)
+    secw = lbm.lbm_batch_column_seconds(bwd, n)
+    rhow = np.empty(rho.size)
+    lbm.lbm_batch_moments(bwd, rho=rhow)
+    lbm.lbm_batch_destroy(bwd)
     local = dict(idx=share, cols=cols, t64=t64, t32=t32, tdd=tdd, st64=st64, res64=res64, s64=s64, sec64=sec64,
                  st32=st32, s32=s32, stdd=stdd, resdd=resdd, sdd=sdd, secdd=secdd,
+                 tw=t_inf + t_rest + tw32 + twdd, tw32=tw32, stw=stw, resw=resw, sw=sw, secw=secw, train=train,
+                 warm_columns=len(sel), t_inf=t_inf, t_rest=t_rest,
                  stats64=column_stats(rho64, cols, lbm), stats32=column_stats(rho32, cols, lbm),
-                 statsdd=column_stats(rhodd, cols, lbm), tuned=tuned)
+                 statsdd=column_stats(rhodd, cols, lbm), statsw=column_stats(rhow, cols, lbm), tuned=tuned)
     ok64 = (res64 <= 1e-10) & (s64 == 0)
     okdd = (resdd <= 1e-10) & (sdd == 0)
     local["prec32"] = _error_summary(local["stats32"], local["stats64"], rho32, rho64, cols, ok64 & (s32 == 0))
     local["precdd"] = _error_summary(local["statsdd"], local["stats64"], rhodd, rho64, cols, ok64 & okdd)
+    okw = (resw <= 1e-10) & (sw == 0)
+    local["precw"] = _error_summary(local["statsw"], local["stats64"], rhow, rho64, cols, ok64 & okw)
     if world > 1:
         import torch.distributed as dist
 
@@ -845,21 +893,36 @@ def time_to_steady(args, lbm, inputs, world, rank, torch):
     okdd = (cat("resdd") <= 1e-10) & (cat("sdd") == 0)
     both = ok64 & okdd
     sec64, secdd = cat("sec64"), cat("secdd")
+    TW = max(g["tw"] for g in gathered)
+    okw = (cat("resw") <= 1e-10) & (cat("sw") == 0)
+    secw = cat("secw")
+    all3 = ok64 & okw
     out = {
-        "what": "time to residual 1e-10 of batched 4xH columns: plain FP64 vs FP32 then double-float",
+        "what": "time to residual 1e-10 of batched 4xH columns: plain FP64 vs FP32 then double-float, "
+                "without and with the warm start",
         "workload": f"{len(cols_g)} seeded 4xH liquid columns, H in {STEADY_HEIGHTS}, step cap {args.steady_cap} per phase",
         "ranks": world, "partition": "disjoint column sets balanced by nodes, no exchange" if world > 1 else None,
         "check_every": 100, "fp32_tol": FP32_TOL, "fp32_stall_checks": FP32_STALL_CHECKS, "accel_checks": ACCEL_CHECKS,
         "fp64_plain": _path_summary(T64, cat("st64"), cat("res64"), cat("s64"), sec64, cols_g, ok64),
         "fp32_then_double_float": _path_summary(T32DD, cat("stdd"), cat("resdd"), cat("sdd"), secdd, cols_g, okdd)
         | {"fp32_makespan_s": max(g["t32"] for g in gathered)},
+        "fp32_then_double_float_warm_start": _path_summary(TW, cat("stw"), cat("resw"), cat("sw"), secw, cols_g, okw)
+        | {"fp32_makespan_s": max(g["tw32"] for g in gathered), "warm_started_columns": sum(g["warm_columns"] for g in gathered),
+           "start": f"network profile for H in {WARM_HEIGHTS} (tanh for the others), every column from the rest "
+                    "state of its profile", "inference_s": max(g["t_inf"] for g in gathered),
+           "rest_state_s": max(g["t_rest"] for g in gathered), "training (not timed)": gathered[0]["train"]},
         "makespan_speedup": T64 / T32DD,
+        "makespan_speedup_warm_start": T64 / TW,
+        "converged_in_plain_and_warm": int(all3.sum()),
+        "median_column_speedup_warm_start": float(np.median(sec64[all3] / secw[all3])) if all3.any() else None,
+        "steps_ratio_warm_start_vs_plain_fp64": float(np.sum(cat("stw")[all3]) / max(1, np.sum(cat("st64")[all3]))),
         "converged_in_both": int(both.sum()),
         "median_column_seconds_both": {"fp64_plain": float(np.median(sec64[both])) if both.any() else None,
                                        "fp32_then_double_float": float(np.median(secdd[both])) if both.any() else None},
         "median_column_speedup_both": float(np.median(sec64[both] / secdd[both])) if both.any() else None,
         "precision_vs_fp64": {"fp32_end_of_phase": gathered[0]["prec32"] if world == 1 else [g["prec32"] for g in gathered],
-                              "fp32_then_double_float": gathered[0]["precdd"] if world == 1 else [g["precdd"] for g in gathered]},
+                              "fp32_then_double_float": gathered[0]["precdd"] if world == 1 else [g["precdd"] for g in gathered],
+                              "fp32_then_double_float_warm_start": gathered[0]["precw"] if world == 1 else [g["precw"] for g in gathered]},
         "block_threads": tuned_summary(gathered[0]["tuned"]),
     }
     return out
@@ -1004,22 +1067,15 @@ def run_thermal(args, torch, lbm, inputs):
 
 
 # ---------------------------------------------------------------- learned warm start
-def run_warmstart(args):
-    """Config 5: steady columns generated by the batch runner train the warm-start network
-    on the GPU; held-out seeded columns then run to residual 1e-10 from the tanh profile and
-    from the network's (mass-corrected) profile, in FP64 alone and FP32 then FP64."""
+def train_warm_network(lbm, inputs, torch, ncols, heights, cap, iters, batch, seed):
+    """The warm-start network trained on the GPU (the library's tcgen05 kernels) on the
+    steady profiles of `ncols` seeded columns of `heights` (another seed than any evaluated
+    set), each run by the batch runner in FP32 to residual 1e-7 within `cap` steps; the
+    converged columns give the rows. Returns (network handle, summary)."""
     import numpy as np
-    import torch
 
-    from paper_2301_12869_gb300 import inputs, lbm
-
-    heights = tuple(int(h) for h in args.column_heights.split(","))
-    rho_c, Tc, _ = lbm.lbm_critical_point(A, B, R)
-    cap = args.column_max_steps
-    out = {"metric": "time to steady state (residual 1e-10), batched columns, FP32 (+ double-float finish) + warm start vs plain FP64",
-           "unit": "s", "higher_is_better": False, "impl": "gb300", "n_gpus": 1}
-    # ---- training data: steady profiles of the method (FP32 to its rounding floor)
-    cols_tr, rho_tr = column_set(args.train_columns, SEED + 1, heights, lbm, inputs)
+    _, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    cols_tr, rho_tr = column_set(ncols, seed, heights, lbm, inputs)
     b = lbm.lbm_batch_init(lbm.make_params(4, 8, 0.8 * Tc, "fp32", a=A, b=B, R=R), cols_tr, rho_tr)
     t_gen = lbm.lbm_batch_run(b, 1e-7, cap, 100)
     _, res, status = lbm.lbm_batch_results(b, len(cols_tr), check=False)
@@ -1034,18 +1090,36 @@ def run_warmstart(args):
     row_mask = torch.from_numpy(np.repeat(good, [c["ny"] for c in cols_tr])).cuda()
     x, t = x_all[row_mask].contiguous(), t_all[row_mask].contiguous()
     del rho_dev, x_all, t_all
-    # ---- training
-    h = lbm.lbm_mlp_create(lbm.mlp_initial_params(SEED), args.mlp_batch)
+    h = lbm.lbm_mlp_create(lbm.mlp_initial_params(SEED), batch)
     t0 = time.perf_counter()
     losses = []
     for frac, lr in ((0.5, 1e-3), (0.3, 3e-4), (0.2, 1e-4)):
-        losses.append(lbm.lbm_mlp_train(h, x, t, args.mlp_batch, int(frac * args.mlp_iters), lr, SEED + len(losses)))
+        losses.append(lbm.lbm_mlp_train(h, x, t, batch, int(frac * iters), lr, SEED + len(losses)))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     losses = np.concatenate(losses)
-    out["training"] = {"columns": len(cols_tr), "converged_columns": int(good.sum()), "rows": int(x.shape[0]),
-                       "generation_s": t_gen, "train_s": t_train, "iters": int(losses.size), "batch": args.mlp_batch,
-                       "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-200:]))}
+    return h, {"columns": len(cols_tr), "heights": list(heights), "converged_columns": int(good.sum()),
+               "rows": int(x.shape[0]), "generation_s": t_gen, "train_s": t_train, "iters": int(losses.size),
+               "batch": batch, "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-200:]))}
+
+
+def run_warmstart(args):
+    """Config 5: steady columns generated by the batch runner train the warm-start network
+    on the GPU; held-out seeded columns then run to residual 1e-10 from the tanh profile and
+    from the network's (mass-corrected) profile, in FP64 alone and FP32 then FP64."""
+    import numpy as np
+    import torch
+
+    from paper_2301_12869_gb300 import inputs, lbm
+
+    heights = tuple(int(h) for h in args.column_heights.split(","))
+    rho_c, Tc, _ = lbm.lbm_critical_point(A, B, R)
+    cap = args.column_max_steps
+    out = {"metric": "time to steady state (residual 1e-10), batched columns, FP32 (+ double-float finish) + warm start vs plain FP64",
+           "unit": "s", "higher_is_better": False, "impl": "gb300", "n_gpus": 1}
+    # ---- training data (steady profiles of the method, FP32 to its rounding floor) and training
+    h, out["training"] = train_warm_network(lbm, inputs, torch, args.train_columns, heights, cap, args.mlp_iters,
+                                            args.mlp_batch, SEED + 1)
     # ---- held-out columns: tanh start vs warm start
     cols, rho0 = column_set(args.columns, SEED + 2, heights, lbm, inputs)
     sizes = [4 * c["ny"] for c in cols]

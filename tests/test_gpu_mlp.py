@@ -322,10 +322,16 @@ def test_features_and_warm_start_profile():
 
 def test_warm_start_gain_on_held_out_columns():
     """What the trained network gains over the method without it, on held-out columns:
-    trained on the steady profiles of 512 seeded 4 x 64 columns (FP32 runs of the method),
-    its mass-corrected start is closer to the converged profile than the tanh start, and the
-    lattice Boltzmann run from it reaches the tanh start's steady state on most columns (the
-    network only initialises; the FP64 run to 1e-10 decides)."""
+    trained on the steady profiles of 4096 seeded 4 x 64 columns (FP32 runs of the method;
+    8000 Adam steps of 8192 rows - a network trained on a few hundred columns for 1500 steps
+    started the rest-state runs farther from the steady state than the tanh profile),
+    its start is closer to the converged profile than the tanh start; the lattice Boltzmann
+    run from it reaches the tanh start's steady state on most columns (the network only
+    initialises; the FP64 run to 1e-10 decides); and started from the rest state of each
+    profile (lbm_batch_rest_state) the network's columns need fewer steps in total than the
+    tanh columns, and both far fewer than the method's own equilibrium start from tanh. (From
+    equilibrium populations f_eq(rho, 0) no density profile, not even the converged one,
+    saves more than ~1.5 % of the steps: the transient of the missing forcing terms sets them.)"""
     import torch
 
     a, b, R = 0.25, 4.0, 1.0
@@ -342,7 +348,7 @@ def test_warm_start_gain_on_held_out_columns():
 
     p32 = lbm.make_params(4, 8, 0.8 * T_C_of(a, b, R), "fp32", a=a)
     p64 = lbm.make_params(4, 8, 0.8 * T_C_of(a, b, R), "fp64", a=a)
-    cols, rho = columns(512, 11)
+    cols, rho = columns(4096, 11)
     bt = lbm.lbm_batch_init(p32, cols, rho)
     lbm.lbm_batch_run(bt, 1e-7, 100000, 100)
     _, res, status = lbm.lbm_batch_results(bt, len(cols), check=False)
@@ -353,36 +359,49 @@ def test_warm_start_gain_on_held_out_columns():
     t = torch.empty(64 * len(cols), dtype=torch.float32, device="cuda")
     lbm.lbm_mlp_features(cols, 4, a, b, R, x, t=t, rho=rho_dev)
     keep = torch.from_numpy(np.repeat((res <= 1e-7) & (status == 0), 64)).cuda()
-    h = lbm.lbm_mlp_create(lbm.mlp_initial_params(3), 4096)
+    h = lbm.lbm_mlp_create(lbm.mlp_initial_params(3), 8192)
     try:
-        lbm.lbm_mlp_train(h, x[keep].contiguous(), t[keep].contiguous(), 4096, 1500, 1e-3, 5, record=False)
-        ev, rho0 = columns(128, 12)
+        xk, tk = x[keep].contiguous(), t[keep].contiguous()
+        for k, (iters, lr) in enumerate(((4000, 1e-3), (2400, 3e-4), (1600, 1e-4))):
+            lbm.lbm_mlp_train(h, xk, tk, 8192, iters, lr, 5 + k, record=False)
+        ev, rho0 = columns(256, 12)
         mean = rho0.reshape(len(ev), -1).mean(axis=1)
         warm = torch.empty(rho0.size, dtype=torch.float64, device="cuda")
         lbm.lbm_mlp_warm_start(h, ev, 4, a, b, R, mean, warm)
     finally:
         lbm.lbm_mlp_destroy(h)
-    finals = []
-    for start in (rho0, warm):
+    runs = {}
+    for name, start, rest in (("tanh", rho0, False), ("warm", warm, False), ("tanh_rest", rho0, True),
+                              ("warm_rest", warm, True)):
         bb = lbm.lbm_batch_init(p64, ev, start)
+        if rest:
+            lbm.lbm_batch_rest_state(bb)
         lbm.lbm_batch_run(bb, 1e-10, 200000, 100)
-        _, res, status = lbm.lbm_batch_results(bb, len(ev), check=False)
+        steps, res, status = lbm.lbm_batch_results(bb, len(ev), check=False)
         f = np.empty(rho0.size)
         lbm.lbm_batch_moments(bb, rho=f)
         lbm.lbm_batch_destroy(bb)
-        finals.append((f, (res <= 1e-10) & (status == 0)))
-    ok = finals[0][1] & finals[1][1]
+        runs[name] = (f, (res <= 1e-10) & (status == 0), steps)
+    ok = np.logical_and.reduce([r[1] for r in runs.values()])
     assert ok.sum() >= 0.8 * len(ev)
     per = lambda v: np.abs(v).reshape(len(ev), -1).max(axis=1)  # noqa: E731
-    err_tanh = per(rho0 - finals[0][0])[ok]
-    err_warm = per(warm.cpu().numpy() - finals[0][0])[ok]
+    ref = runs["tanh"][0]
+    err_tanh = per(rho0 - ref)[ok]
+    err_warm = per(warm.cpu().numpy() - ref)[ok]
     assert np.median(err_warm) < np.median(err_tanh)
     # a column's steady state need not be unique: a start can settle in another basin (a
     # "miss", which only the plain run reveals). Runs stopped at a per-step change of 1e-10
     # are within 1e-10 / (1 - r) of their fixed point, r the per-step decay factor of the
     # slowest mode (1 - r ~ 5e-4 here): same state = within 1e-5. Most columns agree.
-    same = per(finals[1][0] - finals[0][0])[ok] <= 1e-5
+    same = per(runs["warm_rest"][0] - ref)[ok] <= 1e-5
     assert np.mean(same) >= 0.9
+    total = {k: int(v[2][ok].sum()) for k, v in runs.items()}
+    per_col = runs["warm_rest"][2][ok] / runs["tanh_rest"][2][ok]
+    # measured: totals 0.958 (warm / tanh, rest-state starts) and 0.80 (against the plain
+    # method); per column median 0.945, 62 % of the columns faster
+    assert total["warm_rest"] < 0.97 * total["tanh_rest"], total
+    assert total["warm_rest"] < 0.85 * total["tanh"], total
+    assert np.median(per_col) < 0.99 and np.mean(per_col < 1.0) > 0.5
 
 
 def T_C_of(a, b, R):
