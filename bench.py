@@ -1166,7 +1166,7 @@ def run_warmstart(args):
         diff[k] = {"median": float(np.median(d)), "p90": float(np.percentile(d, 90)), "max": float(d.max()),
                    "columns_over_1e-3": int(np.sum(d > 1e-3))}
     out["config"] = {"workload": f"{len(cols)} held-out seeded 4xH liquid columns, H in {heights}; network trained on "
-                                 f"{len(cols_tr)} steady columns of another seed", "max_steps": cap, "check_every": 100}
+                                 f"{out['training']['columns']} steady columns of another seed", "max_steps": cap, "check_every": 100}
     out["runs"] = {k: {"seconds": v["seconds"], "converged": int(v["ok"].sum()), "nonphysical": v["nonphysical"],
                        "steps_all_converged": int(v["steps"][ok].sum()), "block_threads": v["block_threads"]}
                    for k, v in runs.items()}
